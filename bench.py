@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the pose-differentiable Gaussian-splatting renderer on GB300.
+
+Metric: fwd+bwd Mpix/s at 1M Gaussians (batched vs plain); one step = forward
+(projection, tile lists, compositing) + L1 loss + backward to every Gaussian
+parameter and every view's 6-DoF pose, for one batch of 64 views of mixed
+resolution (256x192 / 504x378 / 1008x756) of a seeded synthetic 1M-Gaussian
+SH-degree-3 scene.  `value` is the batched form (all 64 views in one launch
+sequence); `plain_value` the same work as a per-view loop.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun (N > 1) each rank renders its own 64 views of the same scene
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s at 1M Gaussians (batched vs plain); pose-solve p50/p99 ms"
+UNIT = "Mpix/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--gaussians", type=int, default=1_000_000)
+    ap.add_argument("--views", type=int, default=64)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-views", type=int, default=1)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower().startswith("active")})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_fallback": True}
+
+
+# ------------------------------------------------------------------ workload
+def _workload(args, rank: int):
+    from paper_2410_08743_gb300 import synth
+    w = synth.batched_workload(seed=3, n=args.gaussians, n_views=args.views, view_seed=3 + 7919 * rank)
+    return w
+
+
+def _cpu_baseline(w, n_views: int):
+    """The FP64 oracle on a bounded sample: the first `n_views` views of the
+    workload, full forward + L1 + backward, all host cores."""
+    import oracle
+    from paper_2410_08743_gb300 import synth
+    nthr = os.cpu_count() or 1
+    oracle.set_threads(nthr)
+    views = w["views"][:n_views]
+    poses = w["poses"][:n_views]
+    rng = np.random.default_rng(0)
+    target = synth.random_image_like(rng, views)
+    t0 = time.perf_counter()
+    r = oracle.render(w["scene"], views, poses)
+    L, d, _ = oracle.loss_l1(views, r["image"], target)
+    oracle.backward(w["scene"], views, poses, d)
+    dt = time.perf_counter() - t0
+    mpix = sum(v["width"] * v["height"] for v in views) / 1e6
+    sample = (f"{n_views} view(s) ({', '.join(str(v['width']) + 'x' + str(v['height']) for v in views)}) of the "
+              f"{len(w['scene']['opac'])}-Gaussian scene, forward + L1 + backward incl. pose, FP64")
+    return {"value": mpix / dt, "unit": UNIT, "cores": nthr, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args, 0)
+    vals = []
+    nv = max(1, args.cpu_sample_views)
+    t_all = []
+    for _ in range(max(1, args.steps)):
+        cb = _cpu_baseline(w, nv)
+        vals.append(cb["value"])
+        t_all.append(cb["seconds"])
+    v = float(np.median(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(t_all)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"oracle sample of the batched workload ({nv} view(s))"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_08743_gb300 import _lib as L
+    from paper_2410_08743_gb300 import build as B
+    from paper_2410_08743_gb300.render import Renderer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+
+    w = _workload(args, rank)
+    sc, views, poses = w["scene"], w["views"], w["poses"]
+    V = len(views)
+    npix = sum(v["width"] * v["height"] for v in views)
+    p = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in ("means", "scales", "quats", "opac", "sh")}
+    p["sh_degree"] = int(sc["sh_degree"])
+    P = torch.from_numpy(poses).to(dev)
+    r = Renderer(local)
+    # targets: renders of the same scene at slightly different poses (untimed)
+    tgt = r.forward(p, views, torch.from_numpy(w["target_poses"]).to(dev)).clone()
+    grads = {k: torch.zeros_like(p[k]) for k in ("means", "scales", "quats", "opac", "sh")}
+    pose_grad = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+    loss_v = torch.zeros(V, dtype=torch.float64, device=dev)
+    image = torch.empty(Renderer.image_numel(views), device=dev)
+    l1 = L.make_loss(L.GS_LOSS_L1, target=tgt, w_l1=1.0, loss_out=loss_v)
+
+    def step():
+        for g in grads.values():
+            g.zero_()
+        r.forward(p, views, P, image=image)
+        r.backward(p, views, P, image, l1, grads, pose_grad)
+
+    # warm-up: the first step grows the workspaces, the rest run without syncs
+    step()
+    torch.cuda.synchronize()
+    r.set_flags(L.GS_F_NO_SYNC)
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize()
+    L.gs_status(r.ctx)
+
+    stream = torch.cuda.current_stream()
+    K = args.steps
+
+    def timed(fn, k):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / k
+
+    # ---- main timed region: batched steps with per-kernel CUDA events
+    clocks = ClockSampler(local)
+    L.gs_ctx_set_profiling(r.ctx, True)
+    L.gs_ctx_profile(r.ctx)                      # reset
+    launches0 = L.gs_ctx_launch_count(r.ctx)
+    clocks.start()
+    ms = timed(step, K)
+    clk = clocks.stop()
+    launches = (L.gs_ctx_launch_count(r.ctx) - launches0) // K
+    prof = L.gs_ctx_profile(r.ctx)
+    L.gs_ctx_set_profiling(r.ctx, False)
+    st = L.gs_status(r.ctx)
+    counters = L.gs_frames_counters(r.frames)
+    n_keys = int(r.query(L.GS_Q_NUM_KEYS)[0])
+    value = world * npix / (ms * 1e-3) / 1e6
+
+    # ---- CUDA-graph replay of the same step (no events)
+    graph_value = None
+    if not args.no_graph:
+        try:
+            g = torch.cuda.CUDAGraph()
+            s2 = torch.cuda.Stream()
+            s2.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s2):
+                step()
+            torch.cuda.current_stream().wait_stream(s2)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                step()
+            g.replay()
+            torch.cuda.synchronize()
+            L.gs_status(r.ctx)
+            gms = timed(g.replay, K)
+            L.gs_status(r.ctx)
+            graph_value = world * npix / (gms * 1e-3) / 1e6
+            del g
+        except Exception as e:  # report, do not hide
+            graph_value = f"graph capture failed: {e}"
+
+    # ---- plain: one view per launch sequence
+    plain_value = None
+    if not args.no_plain:
+        r.set_flags(0)
+        vimg = [torch.empty(3 * v["width"] * v["height"], device=dev) for v in views]
+        offs = np.cumsum([0] + [3 * v["width"] * v["height"] for v in views])
+        vt = [tgt[offs[k]:offs[k + 1]].contiguous() for k in range(V)]
+        vl = [L.make_loss(L.GS_LOSS_L1, target=vt[k], w_l1=1.0, loss_out=loss_v[k:k + 1]) for k in range(V)]
+        vP = [P[k:k + 1].contiguous() for k in range(V)]
+        pr = Renderer(local)
+        for k in range(V):  # grow workspaces for the largest view
+            pr.forward(p, views[k:k + 1], vP[k], image=vimg[k])
+        pr.set_flags(L.GS_F_NO_SYNC)
+
+        def plain_step():
+            for g in grads.values():
+                g.zero_()
+            for k in range(V):
+                pr.forward(p, views[k:k + 1], vP[k], image=vimg[k])
+                pr.backward(p, views[k:k + 1], vP[k], vimg[k], vl[k], grads, pose_grad[k:k + 1])
+
+        plain_step()
+        torch.cuda.synchronize()
+        pms = timed(plain_step, max(1, K // 2))
+        L.gs_status(pr.ctx)
+        plain_value = world * npix / (pms * 1e-3) / 1e6
+        pr.close()
+
+    # ---- end to end through gs_step with host buffers
+    e2e = None
+    if not args.no_e2e:
+        r.set_flags(L.GS_F_HOST_IO)
+        hp = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
+        hposes = torch.from_numpy(poses).pin_memory()
+        htgt = tgt.cpu().pin_memory()
+        hg = {k: torch.zeros_like(hp[k]).pin_memory() for k in hp}
+        hpg = torch.zeros(V, 6, dtype=torch.float64).pin_memory()
+        hloss = torch.zeros(V, dtype=torch.float64).pin_memory()
+        desc = L.scene_desc(hp["means"], hp["scales"], hp["quats"], hp["opac"], hp["sh"], p["sh_degree"])
+        hl = L.make_loss(L.GS_LOSS_L1, target=htgt, w_l1=1.0)
+        hgr = L.make_grads(hg["means"], hg["scales"], hg["quats"], hg["opac"], hg["sh"])
+        varr = r.views(views)
+
+        def e2e_step():
+            L.gs_step(r.ctx, r.frames, desc, varr, V, hposes.data_ptr(), r.opts, hl, None, hgr, hpg.data_ptr(),
+                      hloss.data_ptr())
+
+        e2e_step()
+        torch.cuda.synchronize()
+        r.set_flags(L.GS_F_HOST_IO | L.GS_F_NO_SYNC)
+        ems = timed(e2e_step, max(1, K // 2))
+        L.gs_status(r.ctx)
+        h2d = sum(t.numel() * t.element_size() for t in hp.values()) + hposes.numel() * 8 + htgt.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in hg.values()) + hpg.numel() * 8 + hloss.numel() * 8
+        e2e = {"value": world * npix / (ems * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        r.set_flags(L.GS_F_NO_SYNC)
+
+    # ---- roofline of the dominant kernel
+    peaks = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
+    kname, (kms, kn) = dom
+    per_launch_ms = kms / max(1, kn)
+    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
+    n = len(sc["opac"])
+    roof = roofline_for(kname, per_launch_ms, kn // max(1, K), counters, n, V, n_keys, sc["sh_degree"], peaks,
+                        sm_mhz_peak)
+    kernels = {k: {"ms_per_step": v[0] / K, "launches_per_step": v[1] / K} for k, v in sorted(prof.items())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = _cpu_baseline(w, max(1, args.cpu_sample_views))
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched fwd+bwd: {n} Gaussians SH3, {V} views mixed 256x192/504x378/1008x756 "
+                                   f"({npix / 1e6:.2f} Mpix/step/GPU), L1 loss, all Gaussian grads + {V} pose grads",
+                       "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
+                       "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
+            "plain_value": plain_value, "graph_value": graph_value,
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches * K),
+            "roofline": roof, "cpu_baseline": cpu, "kernels": kernels,
+            "counters": {"keys": n_keys, "pairs_eval_fwd": counters[0], "pairs_blend_fwd": counters[1],
+                         "pairs_eval_bwd": counters[2], "pairs_grad_bwd": counters[3],
+                         "keys_per_gaussian_view": n_keys / (n * V)},
+            "status": st,
+        }
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# Algorithmic work per unit (see the design notes for the derivation):
+#   blend_fwd: 16 FP32 lane operations per evaluated (pixel, splat) pair
+#              (d = p - mu_hat, the conic quadratic form, the exponent, alpha,
+#              the two alpha tests) + 7 per blended pair (T update, stop test,
+#              weight, three colour FMAs).
+#   blend_bwd: 16 per evaluated pair (alpha recomputed) + 33 per pair that
+#              contributes gradients (T by division, weight, colour, dL/dalpha,
+#              background sum, conic/mean/opacity gradients).
+OPS_FWD_EVAL, OPS_FWD_BLEND = 16, 7
+OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
+
+
+def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # T lane-ops/s
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    t = per_launch_ms * 1e-3
+    lps = max(1, launches_per_step)
+    ncoef = 3 * (sh_degree + 1) ** 2
+    if kname == "blend_fwd":
+        ops = (OPS_FWD_EVAL * counters[0] + OPS_FWD_BLEND * counters[1]) / lps
+        a = ops / t / 1e12
+        return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+    if kname == "blend_bwd":
+        ops = (OPS_BWD_EVAL * counters[2] + OPS_BWD_GRAD * counters[3]) / lps
+        a = ops / t / 1e12
+        return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+    if kname == "preprocess_fwd":
+        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 52) / lps
+    elif kname == "preprocess_bwd":
+        by = (n * (4 * (3 + 3 + 4) + 4 * ncoef) * 2 + n * 4 * 2 + n * V * (36 + 8)) / lps
+    elif kname == "segment_sort":
+        by = n_keys * (8 + 4) / lps
+    elif kname == "scatter_keys":
+        by = (n * V * 12 + n_keys * 8) / lps
+    else:
+        by = 0.0
+    a = by / t / 1e9
+    return {"kernel": kname, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,255 @@
+/*
+ * gsplat.h - C ABI of the GB300 pose-differentiable Gaussian-splatting
+ * renderer ("Look Gauss, No Pose", arXiv 2410.08743).
+ *
+ * The library renders a set of 3D Gaussians (Sec. 3.1, Eq. 1-4) into one or
+ * more views and back-propagates an image loss to every Gaussian parameter
+ * and, per view, to the 6-DoF world-to-camera pose as a tangent-space
+ * gradient of a left perturbation T <- Exp(tau) T, tau = (rho, phi)
+ * (Sec. 3.2, Eq. 5-13).  All arithmetic runs in the library's own sm_103a
+ * CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Return codes: GS_OK (0), GS_PENDING (> 0, polling only), or a negative
+ *     GS_E* code; gs_last_error() returns a thread-local message for the
+ *     calling thread's last failure.  No C++ exception crosses this ABI.
+ *   - Pointers are DEVICE pointers unless the argument says host.  Device
+ *     inputs are borrowed for the duration of the call's stream work; the
+ *     caller must keep them alive and unmodified until that work completes.
+ *   - Every call is asynchronous on the caller's CUDA stream (`stream`, a
+ *     cudaStream_t passed as void*; NULL = legacy default stream) unless it
+ *     says otherwise.  Workspaces live in the gs_ctx / gs_frames objects and
+ *     grow on demand; a growth may synchronise the stream.
+ *   - Layouts:
+ *       Gaussians (structure of arrays, float32): means [N][3], scales [N][3]
+ *       (activated, > 0), quats [N][4] (w, x, y, z; any non-zero length, 16-byte
+ *       aligned; the
+ *       renderer normalises), opacities [N] (activated, in [0, 1]), sh
+ *       [N][16][3] (real SH, degree <= 3, l = 0..3, m = -l..l; the stride is
+ *       16 coefficients whatever sh_degree is).
+ *       Poses: float64 [V][12] = world->camera rotation R (row-major 3x3)
+ *       then translation t, so a world point x maps to R x + t.
+ *       Images: packed float32 planar, view v occupies [3][H_v][W_v] starting
+ *       at sum_{u<v} 3 H_u W_u; the pixel (px, py) samples the image-plane
+ *       point (px, py) (integer pixel centres).
+ *       Per-view pose gradients: float64 [V][6] = (rho[3], phi[3]).
+ */
+#ifndef GSPLAT_H
+#define GSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GS_OK = 0,
+    GS_PENDING = 1,       /* solve not finished yet (gs_solve_poll) */
+    GS_EINVAL = -1,       /* bad argument */
+    GS_ENOMEM = -2,       /* device or host allocation failed */
+    GS_ETIMEOUT = -3,     /* a bounded device or host wait gave up */
+    GS_EBUSY = -4,        /* object in use / queue full */
+    GS_ECUDA = -5,        /* a CUDA runtime call failed */
+    GS_EOVERFLOW = -6     /* a fixed-capacity buffer was too small (no-sync mode) */
+};
+
+/* Render option flags. */
+enum {
+    GS_F_NO_SYNC = 1u << 0,   /* never synchronise inside the call: use the
+                                 capacities reserved so far and report
+                                 GS_EOVERFLOW through gs_status() instead of
+                                 growing (required inside CUDA-graph capture) */
+    GS_F_HOST_IO = 1u << 1    /* gs_step only: every array argument is host memory */
+};
+
+typedef struct gs_ctx gs_ctx;
+typedef struct gs_scene gs_scene;
+typedef struct gs_frames gs_frames;
+
+/* Gaussians, structure of arrays (layout above). */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;        /* 0..3 */
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+} gs_scene_desc;
+
+/* Pinhole intrinsics and image size of one view (host memory). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gs_view;
+
+/* Rendering options (Sec. 3.1; values the paper leaves open are the prior
+ * art's: see gs_default_opts). */
+typedef struct {
+    float bg[3];              /* background colour composited with T_final */
+    float z_near;             /* cull Gaussians with camera-space z <= z_near */
+    float eps2d;              /* low-pass dilation added to Sigma_hat's diagonal */
+    float clamp_factor;       /* frustum clamp of x/z, y/z in J; 0 disables */
+    float alpha_min;          /* skip a splat whose alpha < alpha_min */
+    float alpha_max;          /* clamp alpha to alpha_max */
+    float t_min;              /* stop before a splat that would bring T below t_min */
+    uint32_t flags;           /* GS_F_* */
+} gs_render_opts;
+
+/* Fills the defaults: black background, z_near 0.2, eps2d 0.3,
+ * clamp_factor 1.3, alpha_min 1/255, alpha_max 0.99, t_min 1e-4, flags 0. */
+void gs_default_opts(gs_render_opts* opts);
+
+/* Loss applied inside gs_render_backward. */
+enum {
+    GS_LOSS_DLDC = 0,         /* dl_dimage holds dL/dC directly */
+    GS_LOSS_L1 = 1,           /* w_l1 * mean_{3HW} |C - target| per view (Eq. 16, L1 term) */
+    GS_LOSS_L1_DSSIM = 2      /* w_l1 * L1 + w_dssim * (1 - SSIM), 11x11 Gaussian window
+                                 (Eq. 16 with beta = w_dssim) */
+};
+
+typedef struct {
+    int32_t kind;             /* GS_LOSS_* */
+    float w_l1, w_dssim;
+    const float* target;      /* device, packed like the image (L1 / D-SSIM) */
+    const float* dl_dimage;   /* device, packed like the image (GS_LOSS_DLDC) */
+    double* loss;             /* device [V], nullable: per-view loss values (written) */
+} gs_loss;
+
+/* Per-Gaussian gradient outputs (device, same layouts as the parameters).
+ * gs_render_backward ADDS into them, so a per-view loop accumulates; zero
+ * them first for a fresh gradient.  Any member may be NULL to skip it. */
+typedef struct {
+    float* means;
+    float* scales;
+    float* quats;
+    float* opacities;
+    float* sh;
+} gs_grads;
+
+/* ---------------------------------------------------------------- objects */
+
+/* Creates a context on CUDA device `device` (made current for the call).
+ * The context owns per-call scratch and a device status word. */
+int gs_ctx_create(int device, gs_ctx** out);
+void gs_ctx_destroy(gs_ctx* ctx);
+
+/* Copies a scene (host or device source, `src_on_device` 0/1) into
+ * library-owned device memory.  Synchronous. */
+int gs_scene_load(gs_ctx* ctx, const gs_scene_desc* desc, int src_on_device, gs_scene** out);
+/* Wraps caller-owned DEVICE arrays without copying (the caller keeps them
+ * alive for every call that uses the handle). */
+int gs_scene_borrow(const gs_scene_desc* desc, gs_scene** out);
+void gs_scene_free(gs_scene* scene);
+
+/* Forward state kept for the backward pass: per-(view, Gaussian) splats,
+ * tile lists, per-pixel final transmittance and list lengths.  One frames
+ * object serves one forward/backward pair at a time. */
+int gs_frames_create(gs_ctx* ctx, gs_frames** out);
+void gs_frames_destroy(gs_frames* fr);
+/* Reserves capacity (in keys, in (view, Gaussian) pairs, in pixels and in
+ * tiles) so that GS_F_NO_SYNC calls up to that size cannot overflow. */
+int gs_frames_reserve(gs_frames* fr, int64_t keys, int64_t pairs, int64_t pixels, int64_t tiles);
+
+/* ---------------------------------------------------------------- render */
+
+/* Sec. 3.1: projects every Gaussian into every view (Eq. 1-2, SH colour),
+ * builds the depth-sorted per-tile lists (deterministic: ties in depth go
+ * to the lower Gaussian index) and alpha-composites front to back (Eq. 3-4).
+ *   views  host [n_views]; poses device [n_views][12];
+ *   image  device output, packed planar float32.
+ *   target device, nullable: with a target the per-view L1 loss (mean over
+ *          3HW of |C - target|) is written to loss_out [n_views] (device,
+ *          float64, nullable).
+ * Keeps its state in `fr` for gs_render_backward.  Errors: GS_EINVAL for
+ * bad sizes/pointers, GS_ENOMEM, GS_ECUDA. */
+int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                      const double* poses, const gs_render_opts* opts, gs_frames* fr, float* image,
+                      const float* target, double* loss_out, void* stream);
+
+/* Sec. 3.2: back-propagates the loss through compositing, projection and SH
+ * to the Gaussians (accumulated into `grads`, NULL = pose only) and to each
+ * view's pose (pose_grad device [n_views][6], float64, written, nullable).
+ * The pose gradient is the tangent-space gradient of L(Exp(tau) T) at tau = 0
+ * (Eq. 7 with Eq. 8-13).  `image` is the forward's output; the other
+ * arguments must equal the forward's. */
+int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                       const double* poses, const gs_render_opts* opts, gs_frames* fr,
+                       const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad,
+                       void* stream);
+
+/* One fused forward + loss + backward step (Sec. 3.3): renders the views,
+ * evaluates `loss` and writes fresh gradients (overwritten, not accumulated)
+ * into `grads` (NULL = pose only) and pose_grad [n_views][6], and the per-view
+ * loss into loss_out [n_views] (nullable).  image_out (nullable) receives the
+ * rendered image.  Without GS_F_HOST_IO in opts->flags every array is a device
+ * pointer.  With GS_F_HOST_IO every array (the scene's parameters, poses,
+ * loss->target / loss->dl_dimage, image_out, grads, pose_grad, loss_out) is
+ * HOST memory, preferably pinned: the call copies the inputs to library-owned
+ * device staging, runs the step and copies the outputs back, all on `stream`;
+ * the outputs are valid after the stream synchronises. */
+int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* scene, int n_views, const gs_view* views,
+            const double* poses, const gs_render_opts* opts, const gs_loss* loss, float* image_out,
+            gs_grads* grads, double* pose_grad, double* loss_out, void* stream);
+
+/* One optimisation step of the view poses (Sec. 3.2-3.3): Adam on the
+ * tangent vector (moments m, v device [n_views][6] float64, kept in the
+ * tangent space), then the left update T <- Exp(-lr m_hat/(sqrt(v_hat)+eps)) T
+ * on poses (device [n_views][12], float64, in place).  step is 1-based. */
+int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* adam_m, double* adam_v,
+                 const double* pose_grad, double lr, double beta1, double beta2, double eps,
+                 int step, void* stream);
+
+/* Synchronises `stream`, returns and clears the context's device status word
+ * (GS_OK, GS_EOVERFLOW from a GS_F_NO_SYNC call, ...). */
+int gs_status(gs_ctx* ctx, void* stream);
+
+/* Copies an internal forward array of `fr` to host memory (synchronous):
+ * what = GS_Q_*; bytes must be at least the array size; the size in bytes
+ * is returned through *size_out (may be called with dst = NULL to query). */
+enum {
+    GS_Q_NUM_KEYS = 0,        /* int64: total (tile, Gaussian) keys */
+    GS_Q_DEPTH = 1,           /* float [V*N]: key-path depth (0 where culled) */
+    GS_Q_RECT = 2,            /* int32 [V*N][4]: tile rectangle x0,y0,x1,y1 (0 where culled) */
+    GS_Q_RADIUS = 3,          /* int32 [V*N]: screen radius (0 where culled) */
+    GS_Q_TILE_RANGES = 4,     /* uint32 [tiles][2]: [start, end) in the sorted list */
+    GS_Q_SORTED_IDX = 5,      /* uint32 [keys]: Gaussian index per sorted key */
+    GS_Q_T_FINAL = 6,         /* float [pixels]: final transmittance */
+    GS_Q_N_CONTRIB = 7,       /* uint32 [pixels]: 1 + last blended list position in the tile */
+    GS_Q_MEAN2D = 8,          /* float [V*N][2]: projected mean (0 where culled) */
+    GS_Q_SPLAT = 9            /* float [V*N][9]: mu_hat(2), conic(3), opacity, colour(3) */
+};
+int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* size_out);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream
+ * around every kernel the library launches (off by default).  While enabled,
+ * calls must not be captured into a CUDA graph. */
+int gs_ctx_set_profiling(gs_ctx* ctx, int enable);
+/* Synchronises the device and returns, per kernel kind, the name, the summed
+ * event time in milliseconds and the launch count since the last read; then
+ * resets them.  names is [max_kinds][32]; *n_kinds receives the count. */
+int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_ms, int64_t* launches,
+                   int* n_kinds);
+
+/* Number of CUDA kernels this context has launched so far (host counter). */
+int64_t gs_ctx_launch_count(gs_ctx* ctx);
+
+/* Work counters of the last forward/backward of `fr` (synchronous):
+ * out[0] (pixel, splat) pairs evaluated by the forward blend, out[1] pairs
+ * blended, out[2] pairs evaluated by the backward blend, out[3] pairs that
+ * contributed gradients in the backward. */
+int gs_frames_counters(gs_frames* fr, int64_t out[4]);
+
+/* Thread-local message describing the calling thread's last error. */
+const char* gs_last_error(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPLAT_H */

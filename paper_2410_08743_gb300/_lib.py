@@ -1,0 +1,289 @@
+"""ctypes binding of libgsplat (include/gsplat.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+tensor data pointers, sizes and the current CUDA stream straight through.  All
+arithmetic happens in the library's CUDA kernels.  Importing this module does
+not need a GPU; calling into the library needs the built libgsplat.so and
+fails loudly (ImportError / GsError) when it is missing or a call fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgsplat.so")
+
+GS_OK, GS_PENDING = 0, 1
+GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3, -4, -5, -6
+GS_F_NO_SYNC, GS_F_HOST_IO = 1, 2
+GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM = 0, 1, 2
+(GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
+ GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT) = range(10)
+
+# names declared in include/gsplat.h (checked by the CPU test suite)
+EXPORTED = (
+    "gs_default_opts", "gs_ctx_create", "gs_ctx_destroy", "gs_scene_load", "gs_scene_borrow", "gs_scene_free",
+    "gs_frames_create", "gs_frames_destroy", "gs_frames_reserve", "gs_render_forward", "gs_render_backward",
+    "gs_pose_step", "gs_status", "gs_frames_query", "gs_last_error", "gs_version", "gs_ctx_set_profiling",
+    "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step",
+)
+
+
+class GsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gsplat error {code}: {msg}")
+        self.code = code
+
+
+class gs_scene_desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("means", C.c_void_p), ("scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacities", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class gs_view(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gs_render_opts(C.Structure):
+    _fields_ = [("bg", C.c_float * 3), ("z_near", C.c_float), ("eps2d", C.c_float), ("clamp_factor", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("flags", C.c_uint32)]
+
+
+class gs_loss(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("w_l1", C.c_float), ("w_dssim", C.c_float), ("target", C.c_void_p),
+                ("dl_dimage", C.c_void_p), ("loss", C.c_void_p)]
+
+
+class gs_grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libgsplat.so (built by paper_2410_08743_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libgsplat.so not built ({p}); run paper_2410_08743_gb300.build.build()")
+    L = C.CDLL(p)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    L.gs_default_opts.argtypes = [C.POINTER(gs_render_opts)]
+    L.gs_default_opts.restype = None
+    L.gs_ctx_create.argtypes = [i32, C.POINTER(vp)]
+    L.gs_ctx_destroy.argtypes = [vp]
+    L.gs_ctx_destroy.restype = None
+    L.gs_scene_load.argtypes = [vp, C.POINTER(gs_scene_desc), i32, C.POINTER(vp)]
+    L.gs_scene_borrow.argtypes = [C.POINTER(gs_scene_desc), C.POINTER(vp)]
+    L.gs_scene_free.argtypes = [vp]
+    L.gs_scene_free.restype = None
+    L.gs_frames_create.argtypes = [vp, C.POINTER(vp)]
+    L.gs_frames_destroy.argtypes = [vp]
+    L.gs_frames_destroy.restype = None
+    L.gs_frames_reserve.argtypes = [vp, i64, i64, i64, i64]
+    L.gs_render_forward.argtypes = [vp, vp, i32, C.POINTER(gs_view), vp, C.POINTER(gs_render_opts), vp, vp, vp, vp, vp]
+    L.gs_render_backward.argtypes = [vp, vp, i32, C.POINTER(gs_view), vp, C.POINTER(gs_render_opts), vp, vp,
+                                     C.POINTER(gs_loss), C.POINTER(gs_grads), vp, vp]
+    L.gs_step.argtypes = [vp, vp, C.POINTER(gs_scene_desc), i32, C.POINTER(gs_view), vp, C.POINTER(gs_render_opts),
+                          C.POINTER(gs_loss), vp, C.POINTER(gs_grads), vp, vp, vp]
+    L.gs_step.restype = C.c_int
+    L.gs_pose_step.argtypes = [vp, i32, vp, vp, vp, vp, f64, f64, f64, f64, i32, vp]
+    L.gs_status.argtypes = [vp, vp]
+    L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.gs_ctx_set_profiling.argtypes = [vp, i32]
+    L.gs_ctx_profile.argtypes = [vp, i32, vp, vp, vp, C.POINTER(C.c_int)]
+    L.gs_frames_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.gs_ctx_launch_count.argtypes = [vp]
+    L.gs_ctx_launch_count.restype = C.c_int64
+    L.gs_last_error.restype = C.c_char_p
+    L.gs_version.restype = C.c_char_p
+    for name in ("gs_ctx_create", "gs_scene_load", "gs_scene_borrow", "gs_frames_create", "gs_frames_reserve",
+                 "gs_render_forward", "gs_render_backward", "gs_pose_step", "gs_status", "gs_frames_query",
+                 "gs_ctx_set_profiling", "gs_ctx_profile", "gs_frames_counters"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ck(rc: int) -> int:
+    if rc < 0:
+        raise GsError(rc, load().gs_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor arguments must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- objects
+
+def gs_default_opts(**over) -> gs_render_opts:
+    o = gs_render_opts()
+    load().gs_default_opts(C.byref(o))
+    for k, v in over.items():
+        if k == "bg":
+            for j in range(3):
+                o.bg[j] = float(v[j])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def gs_ctx_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    _ck(load().gs_ctx_create(int(device), C.byref(h)))
+    return h.value
+
+
+def gs_ctx_destroy(ctx: int) -> None:
+    load().gs_ctx_destroy(C.c_void_p(ctx))
+
+
+def scene_desc(means, scales, quats, opac, sh, sh_degree: int) -> gs_scene_desc:
+    return gs_scene_desc(int(means.shape[0]), int(sh_degree), _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac),
+                         _ptr(sh))
+
+
+def gs_scene_borrow(means, scales, quats, opac, sh, sh_degree: int) -> int:
+    d = scene_desc(means, scales, quats, opac, sh, sh_degree)
+    h = C.c_void_p()
+    _ck(load().gs_scene_borrow(C.byref(d), C.byref(h)))
+    return h.value
+
+
+def gs_scene_load(ctx: int, means, scales, quats, opac, sh, sh_degree: int) -> int:
+    d = scene_desc(means, scales, quats, opac, sh, sh_degree)
+    h = C.c_void_p()
+    _ck(load().gs_scene_load(C.c_void_p(ctx), C.byref(d), int(means.is_cuda), C.byref(h)))
+    return h.value
+
+
+def gs_scene_free(scene: int) -> None:
+    load().gs_scene_free(C.c_void_p(scene))
+
+
+def gs_frames_create(ctx: int) -> int:
+    h = C.c_void_p()
+    _ck(load().gs_frames_create(C.c_void_p(ctx), C.byref(h)))
+    return h.value
+
+
+def gs_frames_destroy(fr: int) -> None:
+    load().gs_frames_destroy(C.c_void_p(fr))
+
+
+def gs_frames_reserve(fr: int, keys: int, pairs: int, pixels: int, tiles: int) -> None:
+    _ck(load().gs_frames_reserve(C.c_void_p(fr), int(keys), int(pairs), int(pixels), int(tiles)))
+
+
+def views_array(views) -> C.Array:
+    arr = (gs_view * max(1, len(views)))()
+    for k, v in enumerate(views):
+        arr[k] = gs_view(float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"]), int(v["width"]),
+                         int(v["height"]))
+    return arr
+
+
+def gs_render_forward(ctx: int, scene: int, views_arr, n_views: int, poses, opts: gs_render_opts, fr: int, image,
+                      target=None, loss_out=None, stream=None) -> None:
+    _ck(load().gs_render_forward(C.c_void_p(ctx), C.c_void_p(scene), int(n_views), views_arr, _ptr(poses),
+                                 C.byref(opts), C.c_void_p(fr), _ptr(image), _ptr(target), _ptr(loss_out),
+                                 _stream(stream)))
+
+
+def gs_render_backward(ctx: int, scene: int, views_arr, n_views: int, poses, opts: gs_render_opts, fr: int, image,
+                       loss: gs_loss, grads: gs_grads | None, pose_grad, stream=None) -> None:
+    _ck(load().gs_render_backward(C.c_void_p(ctx), C.c_void_p(scene), int(n_views), views_arr, _ptr(poses),
+                                  C.byref(opts), C.c_void_p(fr), _ptr(image), C.byref(loss),
+                                  C.byref(grads) if grads is not None else None, _ptr(pose_grad), _stream(stream)))
+
+
+def gs_step(ctx: int, fr: int, desc: gs_scene_desc, views_arr, n_views: int, poses_ptr, opts: gs_render_opts,
+            loss: gs_loss, image_ptr, grads: gs_grads | None, pose_grad_ptr, loss_out_ptr, stream=None) -> None:
+    """Raw pointers (ints) so that host (GS_F_HOST_IO) and device buffers pass alike."""
+    _ck(load().gs_step(C.c_void_p(ctx), C.c_void_p(fr), C.byref(desc), int(n_views), views_arr,
+                       C.c_void_p(poses_ptr), C.byref(opts), C.byref(loss), C.c_void_p(image_ptr),
+                       C.byref(grads) if grads is not None else None, C.c_void_p(pose_grad_ptr),
+                       C.c_void_p(loss_out_ptr), _stream(stream)))
+
+
+def make_loss(kind: int, target=None, dl_dimage=None, w_l1: float = 1.0, w_dssim: float = 0.0, loss_out=None):
+    return gs_loss(int(kind), float(w_l1), float(w_dssim), _ptr(target), _ptr(dl_dimage), _ptr(loss_out))
+
+
+def make_grads(means=None, scales=None, quats=None, opac=None, sh=None) -> gs_grads:
+    return gs_grads(_ptr(means), _ptr(scales), _ptr(quats), _ptr(opac), _ptr(sh))
+
+
+def gs_pose_step(ctx: int, poses, m, v, grad, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8,
+                 stream=None) -> None:
+    _ck(load().gs_pose_step(C.c_void_p(ctx), int(poses.shape[0]), _ptr(poses), _ptr(m), _ptr(v), _ptr(grad),
+                            float(lr), float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def gs_status(ctx: int, stream=None) -> int:
+    return _ck(load().gs_status(C.c_void_p(ctx), _stream(stream)))
+
+
+def gs_frames_query(fr: int, what: int):
+    """Returns the queried internal array as a numpy array (synchronous)."""
+    import numpy as np
+    L = load()
+    size = C.c_size_t(0)
+    _ck(L.gs_frames_query(C.c_void_p(fr), int(what), None, 0, C.byref(size)))
+    dtype = {GS_Q_NUM_KEYS: np.int64, GS_Q_DEPTH: np.float32, GS_Q_RECT: np.int32, GS_Q_RADIUS: np.int32,
+             GS_Q_TILE_RANGES: np.uint32, GS_Q_SORTED_IDX: np.uint32, GS_Q_T_FINAL: np.float32,
+             GS_Q_N_CONTRIB: np.uint32, GS_Q_MEAN2D: np.float32, GS_Q_SPLAT: np.float32}[what]
+    out = np.zeros(max(1, size.value // np.dtype(dtype).itemsize), dtype)
+    _ck(L.gs_frames_query(C.c_void_p(fr), int(what), out.ctypes.data_as(C.c_void_p), out.nbytes, None))
+    return out[: size.value // np.dtype(dtype).itemsize]
+
+
+def gs_ctx_set_profiling(ctx: int, enable: bool) -> None:
+    _ck(load().gs_ctx_set_profiling(C.c_void_p(ctx), int(bool(enable))))
+
+
+def gs_ctx_profile(ctx: int) -> dict:
+    """{kernel kind: (total ms, launches)} since the last read (synchronous)."""
+    K = 32
+    names = (C.c_char * 32 * K)()
+    ms = (C.c_double * K)()
+    cnt = (C.c_int64 * K)()
+    n = C.c_int(0)
+    _ck(load().gs_ctx_profile(C.c_void_p(ctx), K, C.cast(names, C.c_void_p), C.cast(ms, C.c_void_p),
+                              C.cast(cnt, C.c_void_p), C.byref(n)))
+    return {names[i].value.decode(): (ms[i], int(cnt[i])) for i in range(n.value)}
+
+
+def gs_ctx_launch_count(ctx: int) -> int:
+    return int(load().gs_ctx_launch_count(C.c_void_p(ctx)))
+
+
+def gs_frames_counters(fr: int):
+    out = (C.c_int64 * 4)()
+    _ck(load().gs_frames_counters(C.c_void_p(fr), out))
+    return [int(x) for x in out]
+
+
+def gs_last_error() -> str:
+    return load().gs_last_error().decode(errors="replace")
+
+
+def gs_version() -> str:
+    return load().gs_version().decode()

@@ -1,0 +1,905 @@
+// gs_api.cu - the C ABI: contexts, scenes, forward state, and the
+// orchestration of the kernels of one forward / backward pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+// ------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+    } while (0)
+
+#define CK_LAUNCH()                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(GS_ECUDA, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// ------------------------------------------------------------ objects
+// Kernel kinds reported by the profiler.
+enum ProfKind {
+    PK_SETUP = 0, PK_PRE_FWD, PK_SCAN, PK_SCATTER, PK_SORT, PK_BLEND_FWD, PK_LOSS, PK_DSSIM, PK_BLEND_BWD,
+    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT
+};
+static const char* kProfNames[PK_COUNT] = {"setup_views", "preprocess_fwd", "scan_tiles", "scatter_keys",
+                                           "segment_sort", "blend_fwd", "loss_finalize", "dssim", "blend_bwd",
+                                           "preprocess_bwd", "pose_reduce", "pose_adam", "memset"};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct gs_ctx {
+    int device = 0;
+    int* status = nullptr;          // device status word
+    long long* pinned = nullptr;    // small pinned host scratch
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[PK_COUNT] = {};
+    long long prof_n[PK_COUNT] = {};
+    long long launches = 0;         // kernels launched by this context
+};
+
+static cudaEvent_t pool_event(gs_ctx* c) {
+    if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records an event pair around one kernel launch on the launching stream.
+struct ProfScope {
+    gs_ctx* c;
+    cudaStream_t s;
+    int idx = -1;
+    ProfScope(gs_ctx* c_, int kind, cudaStream_t s_, int n_kernels) : c(c_), s(s_) {
+        if (c) c->launches += n_kernels;
+        if (!c || !c->prof) return;
+        ProfRec r{kind, pool_event(c), pool_event(c)};
+        cudaEventRecord(r.a, s);
+        c->recs.push_back(r);
+        idx = (int)c->recs.size() - 1;
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(c->recs[idx].b, s);
+    }
+};
+#define PROF(kind, nk) ProfScope prof_scope_##kind(ctx, kind, s, nk)
+
+struct gs_scene {
+    SceneDev d{};
+    bool owned = false;
+};
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;  // elements
+    int ensure(size_t n, bool allow_grow, const char* what) {
+        if (n <= cap && p) return GS_OK;
+        if (!allow_grow) return fail(GS_EOVERFLOW, "%s: capacity %zu < %zu in no-sync mode", what, cap, n);
+        size_t nc = std::max<size_t>(n + n / 4, 256);
+        T* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, nc * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            nc = n;
+            e = cudaMalloc(&q, nc * sizeof(T));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(GS_ENOMEM, "%s: cudaMalloc of %zu bytes failed", what, nc * sizeof(T));
+            }
+        }
+        if (p) cudaFree(p);
+        p = q;
+        cap = nc;
+        return GS_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct gs_frames {
+    gs_ctx* ctx = nullptr;
+    // launch configuration of the last forward
+    int n_views = 0;
+    int n = 0;
+    int total_tiles = 0;
+    long long total_pixels = 0;
+    long long total_image = 0;
+    uint32_t n_keys = 0;
+    bool have_forward = false;
+    std::vector<gs_view> views_host;
+    std::vector<ViewDev> vdev_host;
+    std::vector<int> tile_base_host;
+    ViewDev* vdev_pinned = nullptr;
+    int* tb_pinned = nullptr;
+    size_t pinned_views_cap = 0;
+    DevBuf<ViewDev> vdev;
+    DevBuf<int> tile_base;
+    // per (view, Gaussian)
+    DevBuf<float4> A, B, gA, gB;
+    DevBuf<float> Cb, depth, gC;
+    DevBuf<uint2> rect;
+    DevBuf<int> radius;
+    // per tile
+    DevBuf<uint32_t> counts, starts, cursor, scan_tmp;
+    DevBuf<float> tile_loss;
+    // per key
+    DevBuf<unsigned long long> keys, tmp_keys;
+    DevBuf<uint32_t> sorted_idx;
+    // per pixel
+    DevBuf<float> T_final;
+    DevBuf<uint32_t> n_contrib;
+    // backward
+    DevBuf<double> pose_partials;
+    DevBuf<float> dldc_ssim, ssim_tmp;
+    DevBuf<long long> img_off_dev;
+    DevBuf<double> loss_tmp;
+    DevBuf<unsigned long long> counters;  // [4] pair counters
+    // gs_step staging (host I/O and fresh gradients)
+    DevBuf<float> st_params, st_target, st_image, st_grads;
+    DevBuf<double> st_poses, st_pose_grad, st_loss;
+
+    SplatArrays splats() {
+        SplatArrays s;
+        s.A = A.p; s.B = B.p; s.Cb = Cb.p; s.rect = rect.p; s.depth = depth.p; s.radius = radius.p;
+        return s;
+    }
+    Grad2DArrays g2d() {
+        Grad2DArrays g;
+        g.gA = gA.p; g.gB = gB.p; g.gC = gC.p;
+        return g;
+    }
+    void release() {
+        DevBuf<float4>* f4[] = {&A, &B, &gA, &gB};
+        for (auto* b : f4) b->release();
+        DevBuf<float>* f1[] = {&Cb, &depth, &gC, &tile_loss, &T_final, &dldc_ssim, &ssim_tmp};
+        for (auto* b : f1) b->release();
+        rect.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
+        keys.release(); tmp_keys.release(); sorted_idx.release(); n_contrib.release(); pose_partials.release();
+        loss_tmp.release(); counters.release();
+        st_params.release(); st_target.release(); st_image.release(); st_grads.release();
+        st_poses.release(); st_pose_grad.release(); st_loss.release();
+        vdev.release(); tile_base.release(); img_off_dev.release();
+        if (vdev_pinned) cudaFreeHost(vdev_pinned);
+        if (tb_pinned) cudaFreeHost(tb_pinned);
+        vdev_pinned = nullptr; tb_pinned = nullptr;
+    }
+};
+
+static const int kViewChunk = 64;  // views per preprocess launch (bounds shared memory)
+
+// ------------------------------------------------------------ helpers
+static int check_scene(const gs_scene* sc) {
+    if (!sc) return fail(GS_EINVAL, "scene is NULL");
+    if (sc->d.n < 0) return fail(GS_EINVAL, "negative Gaussian count");
+    if (sc->d.sh_degree < 0 || sc->d.sh_degree > 3) return fail(GS_EINVAL, "sh_degree %d not in 0..3", sc->d.sh_degree);
+    if (sc->d.n > 0 && (!sc->d.means || !sc->d.scales || !sc->d.quats || !sc->d.opac || !sc->d.sh))
+        return fail(GS_EINVAL, "scene has a NULL parameter array");
+    if (reinterpret_cast<uintptr_t>(sc->d.quats) % 16 != 0)
+        return fail(GS_EINVAL, "quats must be 16-byte aligned (read as float4)");
+    return GS_OK;
+}
+
+static int check_views(int n_views, const gs_view* views) {
+    if (n_views < 0) return fail(GS_EINVAL, "negative view count");
+    if (n_views > 0 && !views) return fail(GS_EINVAL, "views is NULL");
+    for (int v = 0; v < n_views; v++) {
+        const gs_view& w = views[v];
+        if (w.width <= 0 || w.height <= 0 || w.width > 16 * 4095 || w.height > 16 * 4095)
+            return fail(GS_EINVAL, "view %d: bad size %dx%d", v, w.width, w.height);
+        if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(GS_EINVAL, "view %d: focal lengths must be > 0", v);
+    }
+    return GS_OK;
+}
+
+static RenderParams make_params(const gs_render_opts* o) {
+    RenderParams rp;
+    for (int k = 0; k < 3; k++) rp.bg[k] = o->bg[k];
+    rp.z_near = o->z_near; rp.eps2d = o->eps2d; rp.clamp_factor = o->clamp_factor;
+    rp.alpha_min = o->alpha_min; rp.alpha_max = o->alpha_max; rp.t_min = o->t_min;
+    return rp;
+}
+
+static bool same_views(const std::vector<gs_view>& a, int n, const gs_view* b) {
+    if ((int)a.size() != n) return false;
+    for (int v = 0; v < n; v++)
+        if (memcmp(&a[v], &b[v], sizeof(gs_view)) != 0) return false;
+    return true;
+}
+
+// Builds the host view tables and uploads them when the views changed.
+static int upload_views(gs_frames* fr, int n_views, const gs_view* views, bool allow_grow, cudaStream_t s) {
+    if (same_views(fr->views_host, n_views, views) && fr->vdev.p) return GS_OK;
+    if (!allow_grow) return fail(GS_EOVERFLOW, "views changed in no-sync mode");
+    fr->views_host.assign(views, views + n_views);
+    fr->vdev_host.assign(n_views, ViewDev{});
+    fr->tile_base_host.assign(n_views + 1, 0);
+    long long img = 0, pix = 0;
+    int tb = 0;
+    for (int v = 0; v < n_views; v++) {
+        ViewDev& d = fr->vdev_host[v];
+        const gs_view& w = views[v];
+        d.fx = w.fx; d.fy = w.fy; d.cx = w.cx; d.cy = w.cy;
+        d.W = w.width; d.H = w.height;
+        d.gw = (w.width + GS_TILE - 1) / GS_TILE;
+        d.gh = (w.height + GS_TILE - 1) / GS_TILE;
+        d.tile_base = tb;
+        d.img_off = img;
+        d.pix_off = pix;
+        fr->tile_base_host[v] = tb;
+        tb += d.gw * d.gh;
+        img += 3LL * w.width * w.height;
+        pix += (long long)w.width * w.height;
+    }
+    fr->tile_base_host[n_views] = tb;
+    fr->total_tiles = tb;
+    fr->total_pixels = pix;
+    fr->total_image = img;
+    int rc;
+    if ((rc = fr->vdev.ensure(std::max(n_views, 1), true, "views")) != GS_OK) return rc;
+    if ((rc = fr->tile_base.ensure(n_views + 1, true, "tile_base")) != GS_OK) return rc;
+    if (fr->pinned_views_cap < (size_t)n_views + 1) {
+        // the pinned staging may still feed an earlier upload
+        CK(cudaStreamSynchronize(s));
+        if (fr->vdev_pinned) cudaFreeHost(fr->vdev_pinned);
+        if (fr->tb_pinned) cudaFreeHost(fr->tb_pinned);
+        fr->vdev_pinned = nullptr; fr->tb_pinned = nullptr;
+        size_t c = (size_t)n_views + 16;
+        CK(cudaMallocHost(&fr->vdev_pinned, c * sizeof(ViewDev)));
+        CK(cudaMallocHost(&fr->tb_pinned, (c + 1) * sizeof(int)));
+        fr->pinned_views_cap = c;
+    } else {
+        CK(cudaStreamSynchronize(s));
+    }
+    memcpy(fr->vdev_pinned, fr->vdev_host.data(), sizeof(ViewDev) * n_views);
+    memcpy(fr->tb_pinned, fr->tile_base_host.data(), sizeof(int) * (n_views + 1));
+    if (n_views > 0) CK(cudaMemcpyAsync(fr->vdev.p, fr->vdev_pinned, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(fr->tile_base.p, fr->tb_pinned, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+    return GS_OK;
+}
+
+static int ensure_pair_buffers(gs_frames* fr, size_t vn, bool grow) {
+    int rc;
+    if ((rc = fr->A.ensure(vn, grow, "splat A")) || (rc = fr->B.ensure(vn, grow, "splat B")) ||
+        (rc = fr->Cb.ensure(vn, grow, "splat Cb")) || (rc = fr->rect.ensure(vn, grow, "splat rect")) ||
+        (rc = fr->depth.ensure(vn, grow, "splat depth")) || (rc = fr->radius.ensure(vn, grow, "splat radius")))
+        return rc;
+    return GS_OK;
+}
+
+static int ensure_tile_buffers(gs_frames* fr, size_t tiles, bool grow) {
+    int rc;
+    if ((rc = fr->counts.ensure(tiles + 1, grow, "tile counts")) || (rc = fr->starts.ensure(tiles + 1, grow, "tile starts")) ||
+        (rc = fr->cursor.ensure(tiles + 1, grow, "tile cursor")) || (rc = fr->tile_loss.ensure(tiles + 1, grow, "tile loss")) ||
+        (rc = fr->scan_tmp.ensure(gs::scan_tmp_bytes((int)tiles + 1) / 4 + 1, grow, "scan tmp")))
+        return rc;
+    return GS_OK;
+}
+
+static int ensure_key_buffers(gs_frames* fr, size_t keys, bool grow) {
+    int rc;
+    if ((rc = fr->keys.ensure(keys, grow, "keys")) || (rc = fr->tmp_keys.ensure(keys, grow, "tmp keys")) ||
+        (rc = fr->sorted_idx.ensure(keys, grow, "sorted idx")))
+        return rc;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------ ABI
+extern "C" {
+
+const char* gs_last_error(void) { return g_err.c_str(); }
+
+const char* gs_version(void) { return "gsplat-gb300 0.1 (sm_103a)"; }
+
+void gs_default_opts(gs_render_opts* o) {
+    if (!o) return;
+    o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
+    o->z_near = 0.2f;
+    o->eps2d = 0.3f;
+    o->clamp_factor = 1.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_min = 1e-4f;
+    o->flags = 0u;
+}
+
+int gs_ctx_create(int device, gs_ctx** out) {
+    if (!out) return fail(GS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(GS_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    CK(cudaSetDevice(device));
+    gs_ctx* c = new (std::nothrow) gs_ctx();
+    if (!c) return fail(GS_ENOMEM, "host allocation failed");
+    c->device = device;
+    cudaError_t e = cudaMalloc(&c->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 64 * sizeof(long long));
+    if (e != cudaSuccess) {
+        if (c->status) cudaFree(c->status);
+        delete c;
+        return fail(GS_ECUDA, "context setup: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return GS_OK;
+}
+
+void gs_ctx_destroy(gs_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (const ProfRec& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->status) cudaFree(c->status);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+}
+
+int gs_scene_borrow(const gs_scene_desc* d, gs_scene** out) {
+    if (!d || !out) return fail(GS_EINVAL, "NULL argument");
+    if (d->n < 0 || d->n > 0x7fffffff) return fail(GS_EINVAL, "Gaussian count %lld out of range", (long long)d->n);
+    gs_scene* s = new (std::nothrow) gs_scene();
+    if (!s) return fail(GS_ENOMEM, "host allocation failed");
+    s->d.n = (int)d->n;
+    s->d.sh_degree = d->sh_degree;
+    s->d.means = d->means; s->d.scales = d->scales; s->d.quats = d->quats;
+    s->d.opac = d->opacities; s->d.sh = d->sh;
+    s->owned = false;
+    int rc = check_scene(s);
+    if (rc != GS_OK) { delete s; return rc; }
+    *out = s;
+    return GS_OK;
+}
+
+int gs_scene_load(gs_ctx* ctx, const gs_scene_desc* d, int src_on_device, gs_scene** out) {
+    if (!ctx || !d || !out) return fail(GS_EINVAL, "NULL argument");
+    if (d->n < 0 || d->n > 0x7fffffff) return fail(GS_EINVAL, "Gaussian count out of range");
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(GS_EINVAL, "sh_degree %d not in 0..3", d->sh_degree);
+    if (d->n > 0 && (!d->means || !d->scales || !d->quats || !d->opacities || !d->sh))
+        return fail(GS_EINVAL, "scene has a NULL parameter array");
+    CK(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)d->n;
+    const size_t bytes = n * sizeof(float) * (3 + 3 + 4 + 1 + 48);
+    char* base = nullptr;
+    if (n > 0) CK(cudaMalloc(&base, bytes));
+    gs_scene* s = new (std::nothrow) gs_scene();
+    if (!s) { if (base) cudaFree(base); return fail(GS_ENOMEM, "host allocation failed"); }
+    float* p = reinterpret_cast<float*>(base);
+    float* quats = p; float* means = quats + 4 * n; float* scales = means + 3 * n;
+    float* opac = scales + 3 * n; float* sh = opac + n;
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n > 0) {
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemcpy(means, d->means, 3 * n * sizeof(float), kind);
+        if (e == cudaSuccess) e = cudaMemcpy(scales, d->scales, 3 * n * sizeof(float), kind);
+        if (e == cudaSuccess) e = cudaMemcpy(quats, d->quats, 4 * n * sizeof(float), kind);
+        if (e == cudaSuccess) e = cudaMemcpy(opac, d->opacities, n * sizeof(float), kind);
+        if (e == cudaSuccess) e = cudaMemcpy(sh, d->sh, 48 * n * sizeof(float), kind);
+        if (e != cudaSuccess) {
+            cudaFree(base);
+            delete s;
+            return fail(GS_ECUDA, "scene copy: %s", cudaGetErrorString(e));
+        }
+    }
+    s->d.n = (int)n; s->d.sh_degree = d->sh_degree;
+    s->d.means = means; s->d.scales = scales; s->d.quats = quats; s->d.opac = opac; s->d.sh = sh;
+    s->owned = true;
+    *out = s;
+    return GS_OK;
+}
+
+void gs_scene_free(gs_scene* s) {
+    if (!s) return;
+    if (s->owned && s->d.quats) cudaFree(const_cast<float*>(s->d.quats));
+    delete s;
+}
+
+int gs_frames_create(gs_ctx* ctx, gs_frames** out) {
+    if (!ctx || !out) return fail(GS_EINVAL, "NULL argument");
+    gs_frames* f = new (std::nothrow) gs_frames();
+    if (!f) return fail(GS_ENOMEM, "host allocation failed");
+    f->ctx = ctx;
+    *out = f;
+    return GS_OK;
+}
+
+void gs_frames_destroy(gs_frames* f) {
+    if (!f) return;
+    cudaSetDevice(f->ctx->device);
+    cudaDeviceSynchronize();
+    f->release();
+    delete f;
+}
+
+int gs_frames_reserve(gs_frames* fr, int64_t keys, int64_t pairs, int64_t pixels, int64_t tiles) {
+    if (!fr || keys < 0 || pairs < 0 || pixels < 0 || tiles < 0) return fail(GS_EINVAL, "bad reserve arguments");
+    if (keys > 0xfffffff0LL) return fail(GS_EINVAL, "key capacity above 2^32");
+    CK(cudaSetDevice(fr->ctx->device));
+    int rc;
+    if ((rc = ensure_pair_buffers(fr, (size_t)pairs, true))) return rc;
+    if ((rc = fr->gA.ensure(pairs, true, "g2d A")) || (rc = fr->gB.ensure(pairs, true, "g2d B")) ||
+        (rc = fr->gC.ensure(pairs, true, "g2d C")))
+        return rc;
+    if ((rc = ensure_tile_buffers(fr, (size_t)tiles, true))) return rc;
+    if ((rc = ensure_key_buffers(fr, (size_t)keys, true))) return rc;
+    if ((rc = fr->T_final.ensure(pixels, true, "T_final")) || (rc = fr->n_contrib.ensure(pixels, true, "n_contrib")))
+        return rc;
+    return GS_OK;
+}
+
+int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views, const double* poses,
+                      const gs_render_opts* opts, gs_frames* fr, float* image, const float* target, double* loss_out,
+                      void* stream) {
+    if (!ctx || !fr || !opts) return fail(GS_EINVAL, "NULL ctx/frames/opts");
+    if (fr->ctx != ctx) return fail(GS_EINVAL, "frames belong to another context");
+    int rc;
+    if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
+    if (n_views > 0 && (!poses || !image)) return fail(GS_EINVAL, "poses/image is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool grow = !(opts->flags & GS_F_NO_SYNC);
+    CK(cudaSetDevice(ctx->device));
+    fr->have_forward = false;
+    if ((rc = upload_views(fr, n_views, views, grow, s))) return rc;
+    const int n = scene->d.n;
+    const size_t vn = (size_t)n * n_views;
+    const int T = fr->total_tiles;
+    if ((rc = ensure_pair_buffers(fr, std::max<size_t>(vn, 1), grow))) return rc;
+    if ((rc = ensure_tile_buffers(fr, (size_t)T, grow))) return rc;
+    if ((rc = fr->T_final.ensure(std::max<long long>(fr->total_pixels, 1), grow, "T_final")) ||
+        (rc = fr->n_contrib.ensure(std::max<long long>(fr->total_pixels, 1), grow, "n_contrib")))
+        return rc;
+    if ((rc = ensure_key_buffers(fr, std::max<size_t>(fr->keys.cap, 1024), grow))) return rc;
+    fr->n_views = n_views;
+    fr->n = n;
+    if (n_views == 0) { fr->have_forward = true; return GS_OK; }
+    const RenderParams rp = make_params(opts);
+    SplatArrays sp = fr->splats();
+    if ((rc = fr->counters.ensure(4, grow, "counters"))) return rc;
+    {
+        PROF(PK_SETUP, 1);
+        gs::launch_setup_views(views, n_views, poses, fr->vdev.p, rp, s);
+    }
+    CK_LAUNCH();
+    {
+        PROF(PK_MEMSET, 0);
+        CK(cudaMemsetAsync(fr->counts.p, 0, sizeof(uint32_t) * (T + 1), s));
+        CK(cudaMemsetAsync(fr->cursor.p, 0, sizeof(uint32_t) * (T + 1), s));
+        CK(cudaMemsetAsync(fr->counters.p, 0, sizeof(unsigned long long) * 4, s));
+    }
+    for (int v0 = 0; v0 < n_views; v0 += kViewChunk) {
+        const int nv = std::min(kViewChunk, n_views - v0);
+        SplatArrays spc = sp;
+        const size_t off = (size_t)v0 * n;
+        spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
+        {
+            PROF(PK_PRE_FWD, 1);
+            gs::launch_preprocess_fwd(scene->d, nv, fr->vdev.p + v0, rp, spc, fr->counts.p, s);
+        }
+        CK_LAUNCH();
+    }
+    {
+        PROF(PK_SCAN, (T + 1 > 4096) ? 3 : 1);
+        gs::launch_scan_u32(fr->counts.p, fr->starts.p, T + 1, fr->scan_tmp.p, fr->scan_tmp.cap * 4, s);
+    }
+    CK_LAUNCH();
+    if (grow) {
+        CK(cudaMemcpyAsync(ctx->pinned, fr->starts.p + T, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const uint32_t K = *reinterpret_cast<uint32_t*>(ctx->pinned);
+        fr->n_keys = K;
+        if ((rc = ensure_key_buffers(fr, std::max<uint32_t>(K, 1), true))) return rc;
+    }
+    const uint32_t cap = (uint32_t)std::min<size_t>(fr->keys.cap, 0xffffffffu);
+    {
+        PROF(PK_SCATTER, 1);
+        gs::launch_scatter_keys(n, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p, fr->keys.p, cap, ctx->status, s);
+    }
+    CK_LAUNCH();
+    {
+        PROF(PK_SORT, 3);
+        gs::launch_segment_sort(T, fr->starts.p, fr->keys.p, fr->tmp_keys.p, fr->sorted_idx.p, cap, 0, s);
+    }
+    CK_LAUNCH();
+    {
+        PROF(PK_BLEND_FWD, 1);
+        gs::launch_blend_fwd(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->sorted_idx.p, cap,
+                             image, fr->T_final.p, fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr,
+                             fr->counters.p, s);
+    }
+    CK_LAUNCH();
+    if (target && loss_out) {
+        PROF(PK_LOSS, 1);
+        gs::launch_loss_finalize(n_views, fr->vdev.p, fr->tile_loss.p, 1.0, nullptr, loss_out, s);
+        CK_LAUNCH();
+    }
+    fr->have_forward = true;
+    return GS_OK;
+}
+
+int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views, const double* poses,
+                       const gs_render_opts* opts, gs_frames* fr, const float* image, const gs_loss* loss,
+                       gs_grads* grads, double* pose_grad, void* stream) {
+    if (!ctx || !fr || !opts || !loss) return fail(GS_EINVAL, "NULL ctx/frames/opts/loss");
+    int rc;
+    if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
+    if (!fr->have_forward || fr->n_views != n_views || fr->n != scene->d.n || !same_views(fr->views_host, n_views, views))
+        return fail(GS_EINVAL, "backward does not match the frames' last forward");
+    if (n_views == 0) return GS_OK;
+    if (!image) return fail(GS_EINVAL, "image is NULL");
+    if (loss->kind == GS_LOSS_DLDC && !loss->dl_dimage) return fail(GS_EINVAL, "GS_LOSS_DLDC without dl_dimage");
+    if ((loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM) && !loss->target)
+        return fail(GS_EINVAL, "loss needs a target");
+    if (loss->kind < 0 || loss->kind > 2) return fail(GS_EINVAL, "unknown loss kind %d", loss->kind);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool grow = !(opts->flags & GS_F_NO_SYNC);
+    CK(cudaSetDevice(ctx->device));
+    const int n = scene->d.n;
+    const size_t vn = (size_t)n * n_views;
+    if ((rc = fr->gA.ensure(std::max<size_t>(vn, 1), grow, "g2d A")) ||
+        (rc = fr->gB.ensure(std::max<size_t>(vn, 1), grow, "g2d B")) ||
+        (rc = fr->gC.ensure(std::max<size_t>(vn, 1), grow, "g2d C")))
+        return rc;
+    const int nblk = gs::preprocess_bwd_blocks(n);
+    const int nchunks = (n_views + kViewChunk - 1) / kViewChunk;
+    if ((rc = fr->pose_partials.ensure((size_t)std::max(nblk, 1) * n_views * 6 + 6, grow, "pose partials"))) return rc;
+    const RenderParams rp = make_params(opts);
+    const float* dldc = loss->dl_dimage;
+    const bool l1_loss = loss->loss && (loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM);
+    if (loss->kind == GS_LOSS_L1_DSSIM) {
+        if ((rc = fr->dldc_ssim.ensure(fr->total_image, grow, "dssim grad")) ||
+            (rc = fr->ssim_tmp.ensure(fr->total_image * 4, grow, "dssim tmp")))
+            return rc;
+        std::vector<long long> offs(n_views);
+        for (int v = 0; v < n_views; v++) offs[v] = fr->vdev_host[v].img_off;
+        if (loss->loss && (rc = fr->loss_tmp.ensure(n_views, grow, "loss tmp"))) return rc;
+        {
+            PROF(PK_DSSIM, n_views * (12 + (loss->loss ? 1 : 0)));
+            gs::launch_dssim(n_views, views, offs.data(), image, loss->target, loss->w_dssim, fr->dldc_ssim.p,
+                             loss->loss ? fr->loss_tmp.p : nullptr, fr->ssim_tmp.p, s);
+        }
+        CK_LAUNCH();
+        dldc = fr->dldc_ssim.p;
+    }
+    {
+        PROF(PK_MEMSET, 0);
+        CK(cudaMemsetAsync(fr->gA.p, 0, sizeof(float4) * vn, s));
+        CK(cudaMemsetAsync(fr->gB.p, 0, sizeof(float4) * vn, s));
+        CK(cudaMemsetAsync(fr->gC.p, 0, sizeof(float) * vn, s));
+    }
+    const uint32_t cap = (uint32_t)std::min<size_t>(fr->keys.cap, 0xffffffffu);
+    {
+        PROF(PK_BLEND_BWD, 1);
+        gs::launch_blend_bwd(fr->total_tiles, n_views, fr->tile_base.p, fr->vdev.p, rp, fr->splats(), n, fr->starts.p,
+                             fr->sorted_idx.p, cap, image, fr->T_final.p, fr->n_contrib.p, loss->kind, loss->w_l1,
+                             loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr, fr->counters.p + 2,
+                             s);
+    }
+    CK_LAUNCH();
+    if (l1_loss) {
+        PROF(PK_LOSS, 1);
+        gs::launch_loss_finalize(n_views, fr->vdev.p, fr->tile_loss.p, (double)loss->w_l1,
+                                 loss->kind == GS_LOSS_L1_DSSIM ? fr->loss_tmp.p : nullptr, loss->loss, s);
+        CK_LAUNCH();
+    }
+    gs_grads gg{};
+    if (grads) gg = *grads;
+    if (gg.quats && reinterpret_cast<uintptr_t>(gg.quats) % 16 != 0)
+        return fail(GS_EINVAL, "grads->quats must be 16-byte aligned");
+    SplatArrays sp = fr->splats();
+    Grad2DArrays g2 = fr->g2d();
+    for (int c = 0; c < nchunks; c++) {
+        const int v0 = c * kViewChunk;
+        const int nv = std::min(kViewChunk, n_views - v0);
+        SplatArrays spc = sp;
+        Grad2DArrays g2c = g2;
+        const size_t off = (size_t)v0 * n;
+        spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
+        g2c.gA += off; g2c.gB += off; g2c.gC += off;
+        double* part = fr->pose_partials.p;
+        {
+            PROF(PK_PRE_BWD, 1);
+            gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, s);
+        }
+        CK_LAUNCH();
+        if (pose_grad) {
+            PROF(PK_POSE_REDUCE, 1);
+            gs::launch_pose_reduce(nv, nblk, part, pose_grad + 6 * v0, s);
+            CK_LAUNCH();
+        }
+    }
+    return GS_OK;
+}
+
+int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, const gs_view* views,
+            const double* poses, const gs_render_opts* opts, const gs_loss* loss, float* image_out, gs_grads* grads,
+            double* pose_grad, double* loss_out, void* stream) {
+    if (!ctx || !fr || !sd || !opts || !loss) return fail(GS_EINVAL, "NULL argument");
+    int rc;
+    if ((rc = check_views(n_views, views))) return rc;
+    if (sd->n < 0 || sd->n > 0x7fffffff) return fail(GS_EINVAL, "Gaussian count out of range");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool host = (opts->flags & GS_F_HOST_IO) != 0;
+    const bool grow = !(opts->flags & GS_F_NO_SYNC);
+    const size_t n = (size_t)sd->n;
+    long long n_img = 0;
+    for (int v = 0; v < n_views; v++) n_img += 3LL * views[v].width * views[v].height;
+    const bool need_target = loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM;
+    const float* in_img = need_target ? loss->target : loss->dl_dimage;
+    if (n_views > 0 && (!poses || !in_img)) return fail(GS_EINVAL, "poses or loss input is NULL");
+    gs_scene_desc dd = *sd;
+    const double* dposes = poses;
+    gs_loss dl = *loss;
+    float* dimage = image_out;
+    gs_grads dg{};
+    if (grads) dg = *grads;
+    double* dpose_grad = pose_grad;
+    double* dloss = loss_out;
+    // parameter layout inside the staging block: quats (16-byte aligned), means, scales, opac, sh
+    const size_t off_q = 0, off_m = 4 * n, off_s = 7 * n, off_o = 10 * n, off_sh = 11 * n, nparam = 59 * n;
+    if (host) {
+        if ((rc = fr->st_params.ensure(std::max<size_t>(nparam, 1), grow, "staging params")) ||
+            (rc = fr->st_target.ensure(std::max<long long>(n_img, 1), grow, "staging target")) ||
+            (rc = fr->st_image.ensure(std::max<long long>(n_img, 1), grow, "staging image")) ||
+            (rc = fr->st_grads.ensure(std::max<size_t>(nparam, 1), grow, "staging grads")) ||
+            (rc = fr->st_poses.ensure(std::max(12 * n_views, 1), grow, "staging poses")) ||
+            (rc = fr->st_pose_grad.ensure(std::max(6 * n_views, 1), grow, "staging pose grad")) ||
+            (rc = fr->st_loss.ensure(std::max(n_views, 1), grow, "staging loss")))
+            return rc;
+        float* P = fr->st_params.p;
+        if (n > 0) {
+            CK(cudaMemcpyAsync(P + off_m, sd->means, 3 * n * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P + off_s, sd->scales, 3 * n * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P + off_q, sd->quats, 4 * n * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P + off_o, sd->opacities, n * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P + off_sh, sd->sh, 48 * n * 4, cudaMemcpyHostToDevice, s));
+        }
+        dd.means = P + off_m; dd.scales = P + off_s; dd.quats = P + off_q; dd.opacities = P + off_o; dd.sh = P + off_sh;
+        if (n_views > 0) {
+            CK(cudaMemcpyAsync(fr->st_poses.p, poses, 12 * sizeof(double) * n_views, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(fr->st_target.p, in_img, n_img * sizeof(float), cudaMemcpyHostToDevice, s));
+        }
+        dposes = fr->st_poses.p;
+        if (need_target) dl.target = fr->st_target.p; else dl.dl_dimage = fr->st_target.p;
+        dimage = fr->st_image.p;
+        float* G = fr->st_grads.p;
+        if (grads) {
+            dg.means = grads->means ? G + off_m : nullptr; dg.scales = grads->scales ? G + off_s : nullptr;
+            dg.quats = grads->quats ? G + off_q : nullptr; dg.opacities = grads->opacities ? G + off_o : nullptr;
+            dg.sh = grads->sh ? G + off_sh : nullptr;
+            if (nparam) CK(cudaMemsetAsync(G, 0, nparam * sizeof(float), s));
+        }
+        dpose_grad = pose_grad ? fr->st_pose_grad.p : nullptr;
+        dloss = loss_out ? fr->st_loss.p : nullptr;
+    } else {
+        if (!dimage) {
+            if ((rc = fr->st_image.ensure(std::max<long long>(n_img, 1), grow, "image"))) return rc;
+            dimage = fr->st_image.p;
+        }
+        if (grads && n > 0) {
+            if (dg.means) CK(cudaMemsetAsync(dg.means, 0, 3 * n * 4, s));
+            if (dg.scales) CK(cudaMemsetAsync(dg.scales, 0, 3 * n * 4, s));
+            if (dg.quats) CK(cudaMemsetAsync(dg.quats, 0, 4 * n * 4, s));
+            if (dg.opacities) CK(cudaMemsetAsync(dg.opacities, 0, n * 4, s));
+            if (dg.sh) CK(cudaMemsetAsync(dg.sh, 0, 48 * n * 4, s));
+        }
+    }
+    gs_scene* sc = nullptr;
+    if ((rc = gs_scene_borrow(&dd, &sc))) return rc;
+    gs_render_opts o2 = *opts;
+    o2.flags &= ~(uint32_t)GS_F_HOST_IO;
+    dl.loss = dloss;
+    rc = gs_render_forward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, nullptr, nullptr, stream);
+    if (rc == GS_OK)
+        rc = gs_render_backward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, &dl, grads ? &dg : nullptr,
+                                dpose_grad, stream);
+    gs_scene_free(sc);
+    if (rc != GS_OK) return rc;
+    if (host) {
+        if (image_out && n_img) CK(cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (grads && n > 0) {
+            const float* G = fr->st_grads.p;
+            if (grads->means) CK(cudaMemcpyAsync(grads->means, G + off_m, 3 * n * 4, cudaMemcpyDeviceToHost, s));
+            if (grads->scales) CK(cudaMemcpyAsync(grads->scales, G + off_s, 3 * n * 4, cudaMemcpyDeviceToHost, s));
+            if (grads->quats) CK(cudaMemcpyAsync(grads->quats, G + off_q, 4 * n * 4, cudaMemcpyDeviceToHost, s));
+            if (grads->opacities) CK(cudaMemcpyAsync(grads->opacities, G + off_o, n * 4, cudaMemcpyDeviceToHost, s));
+            if (grads->sh) CK(cudaMemcpyAsync(grads->sh, G + off_sh, 48 * n * 4, cudaMemcpyDeviceToHost, s));
+        }
+        if (pose_grad && n_views)
+            CK(cudaMemcpyAsync(pose_grad, dpose_grad, 6 * sizeof(double) * n_views, cudaMemcpyDeviceToHost, s));
+        if (loss_out && n_views) CK(cudaMemcpyAsync(loss_out, dloss, sizeof(double) * n_views, cudaMemcpyDeviceToHost, s));
+    }
+    return GS_OK;
+}
+
+int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, const double* g, double lr, double b1,
+                 double b2, double eps, int step, void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    if (n_views < 0 || step < 1) return fail(GS_EINVAL, "bad n_views or step");
+    if (n_views > 0 && (!poses || !m || !v || !g)) return fail(GS_EINVAL, "NULL pose/moment/gradient array");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        PROF(PK_POSE_ADAM, 1);
+        gs::launch_pose_adam(n_views, poses, m, v, g, lr, b1, b2, eps, step, s);
+    }
+    CK_LAUNCH();
+    return GS_OK;
+}
+
+int gs_status(gs_ctx* ctx, void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    const int st = *reinterpret_cast<int*>(ctx->pinned);
+    if (st & GS_DEV_OVERFLOW) return fail(GS_EOVERFLOW, "a key buffer overflowed in no-sync mode");
+    if (st) return fail(GS_ECUDA, "device status 0x%x", st);
+    return GS_OK;
+}
+
+int gs_ctx_set_profiling(gs_ctx* ctx, int enable) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    ctx->prof = enable != 0;
+    return GS_OK;
+}
+
+int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_ms, int64_t* launches,
+                   int* n_kinds) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    for (const ProfRec& r : ctx->recs) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.kind] += ms;
+            ctx->prof_n[r.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    int k = 0;
+    for (int i = 0; i < PK_COUNT && k < max_kinds; i++) {
+        if (ctx->prof_n[i] == 0) continue;
+        if (names) { strncpy(names[k], kProfNames[i], 31); names[k][31] = 0; }
+        if (total_ms) total_ms[k] = ctx->prof_ms[i];
+        if (launches) launches[k] = ctx->prof_n[i];
+        k++;
+    }
+    if (n_kinds) *n_kinds = k;
+    for (int i = 0; i < PK_COUNT; i++) { ctx->prof_ms[i] = 0.0; ctx->prof_n[i] = 0; }
+    return GS_OK;
+}
+
+int64_t gs_ctx_launch_count(gs_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int gs_frames_counters(gs_frames* fr, int64_t out[4]) {
+    if (!fr || !out) return fail(GS_EINVAL, "NULL argument");
+    for (int k = 0; k < 4; k++) out[k] = 0;
+    if (!fr->counters.p) return GS_OK;
+    CK(cudaSetDevice(fr->ctx->device));
+    unsigned long long c[4];
+    CK(cudaMemcpy(c, fr->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; k++) out[k] = (int64_t)c[k];
+    return GS_OK;
+}
+
+int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* size_out) {
+    if (!fr) return fail(GS_EINVAL, "frames is NULL");
+    if (!fr->have_forward) return fail(GS_EINVAL, "no forward pass recorded");
+    CK(cudaSetDevice(fr->ctx->device));
+    CK(cudaDeviceSynchronize());
+    const size_t vn = (size_t)fr->n * fr->n_views;
+    size_t need = 0;
+    switch (what) {
+        case GS_Q_NUM_KEYS: need = sizeof(int64_t); break;
+        case GS_Q_DEPTH: need = vn * sizeof(float); break;
+        case GS_Q_RECT: need = vn * 4 * sizeof(int32_t); break;
+        case GS_Q_RADIUS: need = vn * sizeof(int32_t); break;
+        case GS_Q_TILE_RANGES: need = (size_t)fr->total_tiles * 2 * sizeof(uint32_t); break;
+        case GS_Q_SORTED_IDX: need = (size_t)fr->n_keys * sizeof(uint32_t); break;
+        case GS_Q_T_FINAL: need = (size_t)fr->total_pixels * sizeof(float); break;
+        case GS_Q_N_CONTRIB: need = (size_t)fr->total_pixels * sizeof(uint32_t); break;
+        case GS_Q_MEAN2D: need = vn * 2 * sizeof(float); break;
+        case GS_Q_SPLAT: need = vn * 9 * sizeof(float); break;
+        default: return fail(GS_EINVAL, "unknown query %d", what);
+    }
+    if (size_out) *size_out = need;
+    if (!dst) return GS_OK;
+    if (bytes < need) return fail(GS_EINVAL, "destination too small (%zu < %zu)", bytes, need);
+    if (what == GS_Q_NUM_KEYS) {
+        uint32_t K = 0;
+        CK(cudaMemcpy(&K, fr->starts.p + fr->total_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        int64_t k64 = K;
+        memcpy(dst, &k64, sizeof(k64));
+        return GS_OK;
+    }
+    if (what == GS_Q_DEPTH) { CK(cudaMemcpy(dst, fr->depth.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
+    if (what == GS_Q_RADIUS) { CK(cudaMemcpy(dst, fr->radius.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
+    if (what == GS_Q_T_FINAL) { CK(cudaMemcpy(dst, fr->T_final.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
+    if (what == GS_Q_N_CONTRIB) { CK(cudaMemcpy(dst, fr->n_contrib.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
+    if (what == GS_Q_SORTED_IDX) {
+        uint32_t K = 0;
+        CK(cudaMemcpy(&K, fr->starts.p + fr->total_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        const size_t nb = std::min<size_t>((size_t)K * 4, need);
+        if (nb) CK(cudaMemcpy(dst, fr->sorted_idx.p, nb, cudaMemcpyDeviceToHost));
+        return GS_OK;
+    }
+    if (what == GS_Q_TILE_RANGES) {
+        std::vector<uint32_t> st(fr->total_tiles + 1);
+        CK(cudaMemcpy(st.data(), fr->starts.p, st.size() * 4, cudaMemcpyDeviceToHost));
+        uint32_t* o = static_cast<uint32_t*>(dst);
+        for (int t = 0; t < fr->total_tiles; t++) { o[2 * t] = st[t]; o[2 * t + 1] = st[t + 1]; }
+        return GS_OK;
+    }
+    std::vector<uint2> rc(vn);
+    if (vn) CK(cudaMemcpy(rc.data(), fr->rect.p, vn * sizeof(uint2), cudaMemcpyDeviceToHost));
+    if (what == GS_Q_RECT) {
+        int32_t* o = static_cast<int32_t*>(dst);
+        for (size_t k = 0; k < vn; k++) {
+            const int x0 = rc[k].x & 0xffff, y0 = rc[k].x >> 16, x1 = rc[k].y & 0xffff, y1 = rc[k].y >> 16;
+            const bool ok = x1 > x0;
+            o[4 * k] = ok ? x0 : 0; o[4 * k + 1] = ok ? y0 : 0; o[4 * k + 2] = ok ? x1 : 0; o[4 * k + 3] = ok ? y1 : 0;
+        }
+        return GS_OK;
+    }
+    std::vector<float4> a(vn), b(vn);
+    std::vector<float> c(vn);
+    if (vn) {
+        CK(cudaMemcpy(a.data(), fr->A.p, vn * sizeof(float4), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(b.data(), fr->B.p, vn * sizeof(float4), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(c.data(), fr->Cb.p, vn * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    float* o = static_cast<float*>(dst);
+    for (size_t k = 0; k < vn; k++) {
+        const bool ok = (rc[k].y & 0xffff) > (rc[k].x & 0xffff);
+        if (what == GS_Q_MEAN2D) {
+            o[2 * k] = ok ? a[k].x : 0.f; o[2 * k + 1] = ok ? a[k].y : 0.f;
+        } else {
+            float r[9] = {a[k].x, a[k].y, a[k].z, a[k].w, b[k].x, b[k].y, b[k].z, b[k].w, c[k]};
+            for (int j = 0; j < 9; j++) o[9 * k + j] = ok ? r[j] : 0.f;
+        }
+    }
+    return GS_OK;
+}
+
+}  // extern "C"

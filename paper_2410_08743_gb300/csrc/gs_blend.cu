@@ -1,0 +1,341 @@
+// gs_blend.cu - per-tile alpha compositing (Sec. 3.1, Eq. 3-4) and its
+// reverse-replay backward (the prior art's gradients w.r.t. the 2D splat
+// parameters, the inputs of the pose chain rule of Sec. 3.2).
+//
+// One CTA per 16x16 tile, one pixel per thread.  The tile's depth-sorted list
+// is consumed in batches of 256 splats staged in shared memory; each thread
+// walks the batch for its pixel.  The forward stops a pixel before the splat
+// that would bring its transmittance below t_min and the CTA leaves once every
+// pixel has stopped.  The backward walks the same lists back to front from
+// each pixel's last blended entry, rebuilding T by division, and reduces every
+// splat's nine 2D gradients over the warp before one vector atomic per warp.
+#include <cuda_runtime.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+#define BATCH 256
+
+// Shared-memory splat batch: A = (mu.x, mu.y, conic.a, conic.b),
+// B = (conic.c, opacity, r, g), Cb = b.
+struct SplatBatch {
+    float4 A[BATCH];
+    float4 B[BATCH];
+    float Cb[BATCH];
+};
+
+// alpha of one (pixel, splat) pair with a fixed operation sequence, so that
+// the forward and the backward take the same skip decisions.
+//   power = -1/2 (a dx^2 + c dy^2) - b dx dy with d = p - mu_hat (Eq. 3)
+//   returns false when the pair is skipped (power > 0 or alpha < alpha_min).
+__device__ __forceinline__ bool pair_alpha(const float4 a, const float4 b, float px, float py, float amin, float amax,
+                                           float& dx, float& dy, float& G, float& alpha, bool& clamped) {
+    dx = __fsub_rn(px, a.x);
+    dy = __fsub_rn(py, a.y);
+    float q = __fmul_rn(a.z, __fmul_rn(dx, dx));
+    q = __fmaf_rn(b.x, __fmul_rn(dy, dy), q);
+    const float power = __fmaf_rn(-a.w, __fmul_rn(dx, dy), __fmul_rn(-0.5f, q));
+    if (power > 0.0f) return false;
+    G = fast_exp2(__fmul_rn(power, GS_LOG2E));
+    const float ar = __fmul_rn(b.y, G);
+    clamped = ar > amax;
+    alpha = clamped ? amax : ar;
+    return alpha >= amin;
+}
+
+__global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const int* __restrict__ tile_base,
+                                                           const ViewDev* __restrict__ views, RenderParams rp,
+                                                           SplatArrays sp, int n, const uint32_t* __restrict__ starts,
+                                                           const uint32_t* __restrict__ sorted_idx, uint32_t cap,
+                                                           float* __restrict__ image, float* __restrict__ T_final,
+                                                           uint32_t* __restrict__ n_contrib,
+                                                           const float* __restrict__ target,
+                                                           float* __restrict__ tile_loss,
+                                                           unsigned long long* __restrict__ counters) {
+    __shared__ SplatBatch sb;
+    __shared__ float s_red[GS_TILE_PIX / 32];
+    const int t = blockIdx.x;
+    const int v = view_of_tile(tile_base, n_views, t);
+    const ViewDev& vd = views[v];
+    const int W = vd.W, H = vd.H, gw = vd.gw;
+    const int lt = t - vd.tile_base;
+    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
+    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const bool inside = px < W && py < H;
+    const float fpx = (float)px, fpy = (float)py;
+    uint32_t s = starts[t], e = starts[t + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    const size_t vbase = (size_t)v * n;
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0, n_eval = 0, n_blend = 0;
+    bool done = !inside;
+    for (uint32_t base = s; base < e; base += BATCH) {
+        if (__syncthreads_count(done) == GS_TILE_PIX) break;
+        const uint32_t j = base + threadIdx.x;
+        if (j < e) {
+            const size_t k = vbase + sorted_idx[j];
+            sb.A[threadIdx.x] = sp.A[k];
+            sb.B[threadIdx.x] = sp.B[k];
+            sb.Cb[threadIdx.x] = sp.Cb[k];
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)BATCH, e - base);
+        if (!done) {
+            for (int jj = 0; jj < cnt; jj++) {
+                const float4 a = sb.A[jj];
+                const float4 b = sb.B[jj];
+                float dx, dy, G, alpha;
+                bool cl;
+                n_eval++;
+                if (!pair_alpha(a, b, fpx, fpy, rp.alpha_min, rp.alpha_max, dx, dy, G, alpha, cl)) continue;
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < rp.t_min) { done = true; break; }
+                n_blend++;
+                const float w = alpha * T;
+                C0 = fmaf(b.z, w, C0);
+                C1 = fmaf(b.w, w, C1);
+                C2 = fmaf(sb.Cb[jj], w, C2);
+                T = Tn;
+                last = base - s + jj + 1;
+            }
+        }
+    }
+    float l1 = 0.0f;
+    if (inside) {
+        const size_t p = (size_t)py * W + px;
+        const size_t np = (size_t)W * H;
+        float* img = image + vd.img_off;
+        C0 = fmaf(T, rp.bg[0], C0);
+        C1 = fmaf(T, rp.bg[1], C1);
+        C2 = fmaf(T, rp.bg[2], C2);
+        img[p] = C0;
+        img[np + p] = C1;
+        img[2 * np + p] = C2;
+        T_final[vd.pix_off + p] = T;
+        n_contrib[vd.pix_off + p] = last;
+        if (target) {
+            const float* tg = target + vd.img_off;
+            l1 = fabsf(C0 - tg[p]) + fabsf(C1 - tg[np + p]) + fabsf(C2 - tg[2 * np + p]);
+        }
+    }
+    if (target) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = l1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < GS_TILE_PIX / 32; w++) acc += s_red[w];
+            tile_loss[t] = acc;
+        }
+    }
+    if (counters) {
+        unsigned long long ce = n_eval, cbl = n_blend;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ce += __shfl_xor_sync(0xffffffffu, ce, o);
+            cbl += __shfl_xor_sync(0xffffffffu, cbl, o);
+        }
+        if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cbl); }
+    }
+}
+
+void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
+                      SplatArrays sp, int n, const uint32_t* starts, const uint32_t* sorted_idx, uint32_t cap,
+                      float* image, float* T_final, uint32_t* n_contrib, const float* target, float* tile_loss,
+                      unsigned long long* counters, cudaStream_t s) {
+    if (n_tiles <= 0) return;
+    k_blend_fwd<<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap, image,
+                                                 T_final, n_contrib, target, tile_loss, counters);
+}
+
+// Per-view loss w * mean_{3HW} |C - target| (+ addend[v]) from the per-tile
+// partial sums, summed in tile order (deterministic).
+__global__ void k_loss_finalize(int n_views, const ViewDev* __restrict__ views, const float* __restrict__ tile_loss,
+                                double w, const double* __restrict__ addend, double* __restrict__ out) {
+    __shared__ double sm[256];
+    const int v = blockIdx.x;
+    const ViewDev& vd = views[v];
+    const int nt = vd.gw * vd.gh;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) acc += (double)tile_loss[vd.tile_base + t];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[v] = w * sm[0] / (3.0 * (double)vd.W * (double)vd.H) + (addend ? addend[v] : 0.0);
+}
+
+void launch_loss_finalize(int n_views, const ViewDev* views, const float* tile_loss, double w, const double* addend,
+                          double* loss_out, cudaStream_t s) {
+    if (n_views <= 0) return;
+    k_loss_finalize<<<n_views, 256, 0, s>>>(n_views, views, tile_loss, w, addend, loss_out);
+}
+
+// ------------------------------------------------------------ backward
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
+                                                           const ViewDev* __restrict__ views, RenderParams rp,
+                                                           SplatArrays sp, int n, const uint32_t* __restrict__ starts,
+                                                           const uint32_t* __restrict__ sorted_idx, uint32_t cap,
+                                                           const float* __restrict__ image,
+                                                           const float* __restrict__ T_final,
+                                                           const uint32_t* __restrict__ n_contrib, int loss_kind,
+                                                           float w_l1, const float* __restrict__ target,
+                                                           const float* __restrict__ dldc, Grad2DArrays g2d,
+                                                           float* __restrict__ tile_loss,
+                                                           unsigned long long* __restrict__ counters) {
+    __shared__ SplatBatch sb;
+    __shared__ uint32_t s_idx[BATCH];
+    __shared__ uint32_t s_max[GS_TILE_PIX / 32];
+    const int t = blockIdx.x;
+    const int v = view_of_tile(tile_base, n_views, t);
+    const ViewDev& vd = views[v];
+    const int W = vd.W, H = vd.H, gw = vd.gw;
+    const int lt = t - vd.tile_base;
+    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
+    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const bool inside = px < W && py < H;
+    const float fpx = (float)px, fpy = (float)py;
+    uint32_t s = starts[t], e = starts[t + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    const size_t vbase = (size_t)v * n;
+    // per-pixel state
+    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, l1 = 0.0f;
+    uint32_t last = 0;
+    if (inside) {
+        const size_t p = (size_t)py * W + px;
+        const size_t np = (size_t)W * H;
+        T = T_final[vd.pix_off + p];
+        last = n_contrib[vd.pix_off + p];
+        const float* img = image + vd.img_off;
+        if (loss_kind == GS_LOSS_DLDC || loss_kind == GS_LOSS_L1_DSSIM) {
+            const float* d = dldc + vd.img_off;
+            g0 = d[p]; g1 = d[np + p]; g2 = d[2 * np + p];
+        }
+        if (loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM) {
+            const float* tg = target + vd.img_off;
+            const float sc = w_l1 * vd.inv_npix3;
+            const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
+            g0 += d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+            g1 += d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+            g2 += d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+            l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
+        }
+    }
+    if (tile_loss) {
+        float r = l1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = __float_as_uint(r);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < GS_TILE_PIX / 32; w++) acc += __uint_as_float(s_max[w]);
+            tile_loss[t] = acc;
+        }
+        __syncthreads();
+    }
+    // colour accumulated behind the current splat, starting with the background
+    float S0 = T * rp.bg[0], S1 = T * rp.bg[1], S2 = T * rp.bg[2];
+    // longest list prefix used by any pixel of the tile
+    uint32_t mx = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    uint32_t tile_last = 0;
+    for (int w = 0; w < GS_TILE_PIX / 32; w++) tile_last = max(tile_last, s_max[w]);
+    if (tile_last > e - s) tile_last = e - s;
+    const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
+    uint32_t n_eval = 0, n_used = 0;
+    for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
+        const int bstart = max(0, bend - BATCH);
+        const int cnt = bend - bstart;
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t id = sorted_idx[s + bstart + threadIdx.x];
+            const size_t k = vbase + id;
+            s_idx[threadIdx.x] = id;
+            sb.A[threadIdx.x] = sp.A[k];
+            sb.B[threadIdx.x] = sp.B[k];
+            sb.Cb[threadIdx.x] = sp.Cb[k];
+        }
+        __syncthreads();
+        for (int jj = cnt - 1; jj >= 0; jj--) {
+            const uint32_t pos = (uint32_t)(bstart + jj);
+            bool use = inside && any_grad && pos < last;
+            const float4 a = sb.A[jj];
+            const float4 b = sb.B[jj];
+            float dx = 0.f, dy = 0.f, G = 0.f, alpha = 0.f;
+            bool cl = false;
+            n_eval += use;
+            if (use) use = pair_alpha(a, b, fpx, fpy, rp.alpha_min, rp.alpha_max, dx, dy, G, alpha, cl);
+            n_used += use;
+            float r[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) r[c] = 0.0f;
+            if (use) {
+                const float cb = sb.Cb[jj];
+                const float om = 1.0f - alpha;
+                const float Ti = T / om;
+                const float wgt = alpha * Ti;
+                r[6] = wgt * g0; r[7] = wgt * g1; r[8] = wgt * g2;
+                const float dLda = Ti * (b.z * g0 + b.w * g1 + cb * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / om;
+                S0 = fmaf(b.z, wgt, S0); S1 = fmaf(b.w, wgt, S1); S2 = fmaf(cb, wgt, S2);
+                T = Ti;
+                if (!cl) {
+                    r[5] = G * dLda;
+                    const float dp = alpha * dLda;
+                    r[0] = dp * (a.z * dx + a.w * dy);
+                    r[1] = dp * (a.w * dx + b.x * dy);
+                    r[2] = -0.5f * dp * dx * dx;
+                    r[3] = -dp * dx * dy;
+                    r[4] = -0.5f * dp * dy * dy;
+                }
+            }
+            if (__any_sync(0xffffffffu, use)) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) r[c] = warp_sum(r[c]);
+                if ((threadIdx.x & 31) == 0) {
+                    const size_t k = vbase + s_idx[jj];
+                    atomicAdd(g2d.gA + k, make_float4(r[0], r[1], r[2], r[3]));
+                    atomicAdd(g2d.gB + k, make_float4(r[4], r[5], r[6], r[7]));
+                    atomicAdd(g2d.gC + k, r[8]);
+                }
+            }
+        }
+    }
+    if (counters) {
+        unsigned long long ce = n_eval, cu = n_used;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ce += __shfl_xor_sync(0xffffffffu, ce, o);
+            cu += __shfl_xor_sync(0xffffffffu, cu, o);
+        }
+        if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cu); }
+    }
+}
+
+void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
+                      SplatArrays sp, int n, const uint32_t* starts, const uint32_t* sorted_idx, uint32_t cap,
+                      const float* image, const float* T_final, const uint32_t* n_contrib, int loss_kind, float w_l1,
+                      const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
+                      unsigned long long* counters, cudaStream_t s) {
+    if (n_tiles <= 0) return;
+    k_blend_bwd<<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap, image,
+                                                 T_final, n_contrib, loss_kind, w_l1, target, dldc, g2d, tile_loss,
+                                                 counters);
+}
+
+}  // namespace gs

@@ -1,0 +1,148 @@
+// gs_internal.cuh - device-side data layout and helpers shared by the
+// renderer's kernels (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsplat.h"
+
+#define GS_TILE 16
+#define GS_TILE_PIX (GS_TILE * GS_TILE)
+
+// Per-view constants the kernels read (built on device from the float64 pose
+// so that CUDA-graph replays see pose updates made by gs_pose_step).
+struct ViewDev {
+    float fx, fy, cx, cy;
+    int W, H, gw, gh;
+    int tile_base;          // global id of the view's first tile
+    int pad0;
+    long long img_off;      // float offset of the planar [3][H][W] image
+    long long pix_off;      // offset of the view's [H][W] per-pixel planes
+    float Rf[9], tf[3];     // pose rounded to FP32 (key path and value path)
+    float oc[3];            // camera centre -R^T t (FP32)
+    float limx, limy;       // frustum-clamp limits on x/z and y/z
+    float inv_npix3;        // 1 / (3 H W)
+};
+
+// Per-(view, Gaussian) splat record written by the forward preprocess.
+//   A  = (mu_hat.x, mu_hat.y, conic.a, conic.b)
+//   B  = (conic.c, opacity, colour.r, colour.g)
+//   Cb = colour.b
+//   rect = (x0 | y0 << 16, x1 | y1 << 16); x1 <= x0 marks a culled splat
+//   depth = key-path camera-space z
+struct SplatArrays {
+    float4* A;
+    float4* B;
+    float* Cb;
+    uint2* rect;
+    float* depth;
+    int* radius;
+};
+
+// Per-(view, Gaussian) 2D gradients accumulated by the backward blend.
+//   gA = (dmu.x, dmu.y, dconic.a, dconic.b), gB = (dconic.c, dopacity, dcol.r, dcol.g), gC = dcol.b
+struct Grad2DArrays {
+    float4* gA;
+    float4* gB;
+    float* gC;
+};
+
+struct SceneDev {
+    int n;
+    int sh_degree;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opac;
+    const float* sh;
+};
+
+struct RenderParams {
+    float bg[3];
+    float z_near, eps2d, clamp_factor, alpha_min, alpha_max, t_min;
+};
+
+// ------------------------------------------------------------ status codes
+// Device status word bits (OR-ed); the host maps them to GS_E* codes.
+#define GS_DEV_OVERFLOW 1
+#define GS_DEV_BADRANGE 2
+
+__device__ __forceinline__ void gs_set_status(int* status, int bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// ------------------------------------------------------------ small helpers
+__device__ __forceinline__ uint32_t pack16(int lo, int hi) {
+    return (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+}
+
+__device__ __forceinline__ int view_of_tile(const int* tile_base, int n_views, int t) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {  // last v with tile_base[v] <= t
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// 2^x with the SFU's approximate exponential (flush-to-zero).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+#define GS_LOG2E 1.4426950408889634f
+
+// ------------------------------------------------------------ kernel entry
+// Host-side launchers (defined in the .cu files).
+namespace gs {
+
+void launch_setup_views(const gs_view* dummy, int n_views, const double* poses, ViewDev* views_dev,
+                        const RenderParams& rp, cudaStream_t s);
+
+void launch_preprocess_fwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
+                           SplatArrays sp, uint32_t* tile_counts, cudaStream_t s);
+
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t tmp_bytes, cudaStream_t s);
+size_t scan_tmp_bytes(int n);
+
+void launch_scatter_keys(int n, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
+                         uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s);
+
+void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys,
+                         unsigned long long* tmp_keys, uint32_t* sorted_idx, uint32_t cap, int idx_bits,
+                         cudaStream_t s);
+
+void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+                      const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+                      const uint32_t* sorted_idx, uint32_t cap, float* image, float* T_final,
+                      uint32_t* n_contrib, const float* target, float* tile_loss, unsigned long long* counters,
+                      cudaStream_t s);
+
+void launch_loss_finalize(int n_views, const ViewDev* views, const float* tile_loss, double w, const double* addend,
+                          double* loss_out, cudaStream_t s);
+
+void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+                      const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+                      const uint32_t* sorted_idx, uint32_t cap, const float* image, const float* T_final,
+                      const uint32_t* n_contrib, int loss_kind, float w_l1, const float* target,
+                      const float* dldc, Grad2DArrays g2d, float* tile_loss, unsigned long long* counters,
+                      cudaStream_t s);
+
+void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
+                           SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials,
+                           int n_blocks, cudaStream_t s);
+int preprocess_bwd_blocks(int n);
+
+void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* pose_grad, cudaStream_t s);
+
+void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr,
+                      double b1, double b2, double eps, int step, cudaStream_t s);
+
+void launch_dssim(int n_views, const gs_view* views_host, const long long* img_off_host, const float* image,
+                  const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
+                  cudaStream_t s);
+
+}  // namespace gs

@@ -168,11 +168,13 @@ def joint_workload(seed: int = 2, n: int = 300_000, n_views: int = 20) -> dict:
 
 
 def batched_workload(seed: int = 3, n: int = 1_000_000, n_views: int = 64,
-                     resolutions=RESOLUTIONS_MIXED) -> dict:
+                     resolutions=RESOLUTIONS_MIXED, view_seed: int | None = None) -> dict:
     """1M SH3 Gaussians seen by 64 cameras of mixed resolution on a jittered
-    8x8 grid with up to +-5 degrees of yaw and pitch."""
+    8x8 grid with up to +-5 degrees of yaw and pitch.  view_seed (default:
+    seed) draws the cameras, so that several GPUs can render different views
+    of one scene."""
     scene = make_scene_box(seed, n, 3)
-    rng = _rng(seed + 1000)
+    rng = _rng((seed if view_seed is None else view_seed) + 1000)
     nx = int(math.ceil(math.sqrt(n_views)))
     ny = int(math.ceil(n_views / nx))
     pick = lambda r: resolutions[r.integers(len(resolutions))]

@@ -1,0 +1,60 @@
+"""Helpers shared by the GPU parity tests: move a synthetic scene to the
+device, run the library's forward/backward, compare with tolerances."""
+import numpy as np
+import torch
+
+from paper_2410_08743_gb300 import _lib as L
+from paper_2410_08743_gb300.render import Renderer
+
+DEV = "cuda:0"
+
+
+def to_dev(scene):
+    p = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(DEV) for k in ("means", "scales", "quats", "opac", "sh")}
+    p["sh_degree"] = int(scene["sh_degree"])
+    return p
+
+
+def zero_grads(p):
+    return {k: torch.zeros_like(p[k]) for k in ("means", "scales", "quats", "opac", "sh")}
+
+
+def poses_dev(poses):
+    return torch.from_numpy(np.ascontiguousarray(poses, np.float64)).to(DEV)
+
+
+def gpu_forward(r: Renderer, scene, views, poses, target=None):
+    p = to_dev(scene)
+    P = poses_dev(poses)
+    tg = torch.from_numpy(np.ascontiguousarray(target, np.float32)).to(DEV) if target is not None else None
+    loss = torch.zeros(len(views), dtype=torch.float64, device=DEV) if target is not None else None
+    img = r.forward(p, views, P, target=tg, loss_out=loss)
+    torch.cuda.synchronize()
+    return p, P, img, tg, loss
+
+
+def gpu_backward_dldc(r: Renderer, p, views, P, img, dldc):
+    d = torch.from_numpy(np.ascontiguousarray(dldc, np.float32)).to(DEV)
+    g = zero_grads(p)
+    pg = torch.zeros(len(views), 6, dtype=torch.float64, device=DEV)
+    r.backward(p, views, P, img, L.make_loss(L.GS_LOSS_DLDC, dl_dimage=d), g, pg)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}, pg.cpu().numpy()
+
+
+def assert_grad_close(got, ref, name, rel=1e-3, abs_floor=1e-6, frac=1.0, mask=None):
+    """Per element |got - ref| <= max(rel |ref|, abs_floor) on at least `frac`
+    of the elements (all by default); mask selects the compared elements."""
+    got = np.asarray(got, np.float64).reshape(len(ref), -1) if np.ndim(ref) > 0 else np.asarray(got)
+    ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    got = got.reshape(ref.shape)
+    if mask is not None:
+        got, ref = got[mask], ref[mask]
+    err = np.abs(got - ref)
+    tol = np.maximum(rel * np.abs(ref), abs_floor)
+    ok = err <= tol
+    worst = np.argsort(-(err / tol).ravel())[:5]
+    msg = f"{name}: {np.mean(ok):.6f} within tol; worst (got, ref): " + ", ".join(
+        f"({got.ravel()[w]:.4g}, {ref.ravel()[w]:.4g})" for w in worst)
+    assert np.mean(ok) >= frac, msg
+    return float(np.mean(ok))
