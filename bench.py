@@ -278,8 +278,10 @@ def run_gpu(args):
         vl = [L.make_loss(L.GS_LOSS_L1, target=vt[k], w_l1=1.0, loss_out=loss_v[k:k + 1]) for k in range(V)]
         vP = [P[k:k + 1].contiguous() for k in range(V)]
         pr = Renderer(local)
-        for k in range(V):  # grow workspaces for the largest view
+        for k in range(V):  # grow workspaces and cache every view's tables
             pr.forward(p, views[k:k + 1], vP[k], image=vimg[k])
+            pr.backward(p, views[k:k + 1], vP[k], vimg[k], vl[k], grads, pose_grad[k:k + 1])
+        torch.cuda.synchronize()
         pr.set_flags(L.GS_F_NO_SYNC)
 
         def plain_step():

@@ -130,6 +130,33 @@ struct DevBuf {
     }
 };
 
+// Device tables of one view configuration (intrinsics and sizes); the
+// pose-dependent fields are refreshed on the device by every forward.  Each
+// table keeps its own pinned staging so that switching configurations never
+// waits for an earlier upload.
+struct ViewTable {
+    std::vector<gs_view> views;
+    std::vector<ViewDev> vdev_host;
+    std::vector<int> tile_base_host;
+    ViewDev* vdev_pinned = nullptr;
+    int* tb_pinned = nullptr;
+    DevBuf<ViewDev> vdev;
+    DevBuf<int> tile_base;
+    int total_tiles = 0;
+    long long total_pixels = 0;
+    long long total_image = 0;
+    void release() {
+        vdev.release();
+        tile_base.release();
+        if (vdev_pinned) cudaFreeHost(vdev_pinned);
+        if (tb_pinned) cudaFreeHost(tb_pinned);
+        vdev_pinned = nullptr;
+        tb_pinned = nullptr;
+    }
+};
+
+static const size_t kMaxViewTables = 512;
+
 struct gs_frames {
     gs_ctx* ctx = nullptr;
     // launch configuration of the last forward
@@ -140,14 +167,12 @@ struct gs_frames {
     long long total_image = 0;
     uint32_t n_keys = 0;
     bool have_forward = false;
+    std::vector<ViewTable*> tables;   // cache of view configurations
+    ViewTable* cur = nullptr;         // configuration of the last forward
     std::vector<gs_view> views_host;
     std::vector<ViewDev> vdev_host;
-    std::vector<int> tile_base_host;
-    ViewDev* vdev_pinned = nullptr;
-    int* tb_pinned = nullptr;
-    size_t pinned_views_cap = 0;
-    DevBuf<ViewDev> vdev;
-    DevBuf<int> tile_base;
+    DevBuf<ViewDev> vdev;             // aliases cur->vdev (not owned)
+    DevBuf<int> tile_base;            // aliases cur->tile_base (not owned)
     // per (view, Gaussian)
     DevBuf<float4> A, B, gA, gB;
     DevBuf<float> Cb, depth, gC;
@@ -192,10 +217,11 @@ struct gs_frames {
         loss_tmp.release(); counters.release();
         st_params.release(); st_target.release(); st_image.release(); st_grads.release();
         st_poses.release(); st_pose_grad.release(); st_loss.release();
-        vdev.release(); tile_base.release(); img_off_dev.release();
-        if (vdev_pinned) cudaFreeHost(vdev_pinned);
-        if (tb_pinned) cudaFreeHost(tb_pinned);
-        vdev_pinned = nullptr; tb_pinned = nullptr;
+        img_off_dev.release();
+        for (ViewTable* t : tables) { t->release(); delete t; }
+        tables.clear();
+        cur = nullptr;
+        vdev.p = nullptr; tile_base.p = nullptr;
     }
 };
 
@@ -240,54 +266,71 @@ static bool same_views(const std::vector<gs_view>& a, int n, const gs_view* b) {
     return true;
 }
 
-// Builds the host view tables and uploads them when the views changed.
+// Selects (or builds and uploads) the device tables of a view configuration.
 static int upload_views(gs_frames* fr, int n_views, const gs_view* views, bool allow_grow, cudaStream_t s) {
-    if (same_views(fr->views_host, n_views, views) && fr->vdev.p) return GS_OK;
-    if (!allow_grow) return fail(GS_EOVERFLOW, "views changed in no-sync mode");
-    fr->views_host.assign(views, views + n_views);
-    fr->vdev_host.assign(n_views, ViewDev{});
-    fr->tile_base_host.assign(n_views + 1, 0);
-    long long img = 0, pix = 0;
-    int tb = 0;
-    for (int v = 0; v < n_views; v++) {
-        ViewDev& d = fr->vdev_host[v];
-        const gs_view& w = views[v];
-        d.fx = w.fx; d.fy = w.fy; d.cx = w.cx; d.cy = w.cy;
-        d.W = w.width; d.H = w.height;
-        d.gw = (w.width + GS_TILE - 1) / GS_TILE;
-        d.gh = (w.height + GS_TILE - 1) / GS_TILE;
-        d.tile_base = tb;
-        d.img_off = img;
-        d.pix_off = pix;
-        fr->tile_base_host[v] = tb;
-        tb += d.gw * d.gh;
-        img += 3LL * w.width * w.height;
-        pix += (long long)w.width * w.height;
+    ViewTable* hit = nullptr;
+    if (fr->cur && same_views(fr->cur->views, n_views, views)) hit = fr->cur;
+    for (size_t k = 0; !hit && k < fr->tables.size(); k++)
+        if (same_views(fr->tables[k]->views, n_views, views)) hit = fr->tables[k];
+    if (!hit) {
+        if (!allow_grow) return fail(GS_EOVERFLOW, "new view configuration in no-sync mode (run it once without GS_F_NO_SYNC)");
+        if (fr->tables.size() >= kMaxViewTables) {
+            CK(cudaStreamSynchronize(s));
+            for (ViewTable* t : fr->tables) { t->release(); delete t; }
+            fr->tables.clear();
+            fr->cur = nullptr;
+        }
+        ViewTable* t = new (std::nothrow) ViewTable();
+        if (!t) return fail(GS_ENOMEM, "host allocation failed");
+        t->views.assign(views, views + n_views);
+        t->vdev_host.assign(n_views, ViewDev{});
+        t->tile_base_host.assign(n_views + 1, 0);
+        long long img = 0, pix = 0;
+        int tb = 0;
+        for (int v = 0; v < n_views; v++) {
+            ViewDev& d = t->vdev_host[v];
+            const gs_view& w = views[v];
+            d.fx = w.fx; d.fy = w.fy; d.cx = w.cx; d.cy = w.cy;
+            d.W = w.width; d.H = w.height;
+            d.gw = (w.width + GS_TILE - 1) / GS_TILE;
+            d.gh = (w.height + GS_TILE - 1) / GS_TILE;
+            d.tile_base = tb;
+            d.img_off = img;
+            d.pix_off = pix;
+            t->tile_base_host[v] = tb;
+            tb += d.gw * d.gh;
+            img += 3LL * w.width * w.height;
+            pix += (long long)w.width * w.height;
+        }
+        t->tile_base_host[n_views] = tb;
+        t->total_tiles = tb;
+        t->total_pixels = pix;
+        t->total_image = img;
+        int rc;
+        if ((rc = t->vdev.ensure(std::max(n_views, 1), true, "views")) ||
+            (rc = t->tile_base.ensure(n_views + 1, true, "tile_base"))) {
+            t->release(); delete t;
+            return rc;
+        }
+        cudaError_t e = cudaMallocHost(&t->vdev_pinned, sizeof(ViewDev) * std::max(n_views, 1));
+        if (e == cudaSuccess) e = cudaMallocHost(&t->tb_pinned, sizeof(int) * (n_views + 1));
+        if (e != cudaSuccess) { t->release(); delete t; return fail(GS_ENOMEM, "pinned allocation failed"); }
+        memcpy(t->vdev_pinned, t->vdev_host.data(), sizeof(ViewDev) * n_views);
+        memcpy(t->tb_pinned, t->tile_base_host.data(), sizeof(int) * (n_views + 1));
+        if (n_views > 0)
+            CK(cudaMemcpyAsync(t->vdev.p, t->vdev_pinned, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t->tile_base.p, t->tb_pinned, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+        fr->tables.push_back(t);
+        hit = t;
     }
-    fr->tile_base_host[n_views] = tb;
-    fr->total_tiles = tb;
-    fr->total_pixels = pix;
-    fr->total_image = img;
-    int rc;
-    if ((rc = fr->vdev.ensure(std::max(n_views, 1), true, "views")) != GS_OK) return rc;
-    if ((rc = fr->tile_base.ensure(n_views + 1, true, "tile_base")) != GS_OK) return rc;
-    if (fr->pinned_views_cap < (size_t)n_views + 1) {
-        // the pinned staging may still feed an earlier upload
-        CK(cudaStreamSynchronize(s));
-        if (fr->vdev_pinned) cudaFreeHost(fr->vdev_pinned);
-        if (fr->tb_pinned) cudaFreeHost(fr->tb_pinned);
-        fr->vdev_pinned = nullptr; fr->tb_pinned = nullptr;
-        size_t c = (size_t)n_views + 16;
-        CK(cudaMallocHost(&fr->vdev_pinned, c * sizeof(ViewDev)));
-        CK(cudaMallocHost(&fr->tb_pinned, (c + 1) * sizeof(int)));
-        fr->pinned_views_cap = c;
-    } else {
-        CK(cudaStreamSynchronize(s));
-    }
-    memcpy(fr->vdev_pinned, fr->vdev_host.data(), sizeof(ViewDev) * n_views);
-    memcpy(fr->tb_pinned, fr->tile_base_host.data(), sizeof(int) * (n_views + 1));
-    if (n_views > 0) CK(cudaMemcpyAsync(fr->vdev.p, fr->vdev_pinned, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(fr->tile_base.p, fr->tb_pinned, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+    fr->cur = hit;
+    fr->views_host = hit->views;
+    fr->vdev_host = hit->vdev_host;
+    fr->vdev.p = hit->vdev.p; fr->vdev.cap = hit->vdev.cap;
+    fr->tile_base.p = hit->tile_base.p; fr->tile_base.cap = hit->tile_base.cap;
+    fr->total_tiles = hit->total_tiles;
+    fr->total_pixels = hit->total_pixels;
+    fr->total_image = hit->total_image;
     return GS_OK;
 }
 

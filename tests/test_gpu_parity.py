@@ -98,8 +98,11 @@ def test_forward_image_and_splats(R, case):
     got = R.query(L.GS_Q_SPLAT).reshape(-1, 9).astype(np.float64)
     ok = oracle.keys(sc, views, poses)["valid"].astype(bool)
     np.testing.assert_allclose(got[ok, :2], vals[ok, :2], rtol=0, atol=2e-4)
+    # the conic is an inverse: its FP32 error grows with the condition of Sigma_hat
     scale = np.abs(vals[ok, 2:5]).max(1, keepdims=True)
-    assert np.all(np.abs(got[ok, 2:5] - vals[ok, 2:5]) <= 1e-5 * scale + 1e-12)
+    a, b, c = vals[ok, 2], vals[ok, 3], vals[ok, 4]
+    cond = (np.abs(a) + np.abs(c)) ** 2 / np.maximum(a * c - b * b, 1e-300)
+    assert np.all(np.abs(got[ok, 2:5] - vals[ok, 2:5]) <= 1e-6 * cond[:, None] * scale + 1e-12)
     np.testing.assert_allclose(got[ok, 5], vals[ok, 5], rtol=1e-7)
     np.testing.assert_allclose(got[ok, 6:9], vals[ok, 6:9], rtol=0, atol=2e-6)
 
@@ -153,13 +156,23 @@ def test_fused_l1_loss_and_gradient(R):
     R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_L1, target=tg, w_l1=1.0, loss_out=lo), g, pg)
     torch.cuda.synchronize()
     assert abs(lo.item() - L1) <= 1e-6 * max(1.0, L1) + 1e-7
-    if frag.any():
-        pytest.skip(f"{frag.sum()} near-threshold pixels: fused L1 path not comparable element-wise")
     go = oracle.backward(sc, views, poses, dldc)
     keep = ~go["fragile_g"].astype(bool)
+    pose_slack = np.zeros(6)
+    if frag.any():
+        # near-threshold pixels: back-propagate their own share to find the
+        # Gaussians they touch and bound their effect on the pose gradient
+        m = np.tile(frag, 3)
+        gf = oracle.backward(sc, views, poses, np.where(m, dldc, 0.0), want_g2d=True)
+        ind = oracle.backward(sc, views, poses, np.where(m, 1.0, 0.0), want_g2d=True)
+        keep &= ~(np.abs(ind["g2d"]).sum(1) > 0)
+        pose_slack = 2.0 * np.abs(gf["pose"][0])
+    assert keep.mean() > 0.9
     assert_grad_close(g["means"].cpu().numpy(), go["means"], "means", mask=keep)
+    assert_grad_close(g["scales"].cpu().numpy(), go["scales"], "scales", mask=keep)
     assert_grad_close(g["opac"].cpu().numpy().reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
-    np.testing.assert_allclose(pg.cpu().numpy()[0], go["pose"][0], rtol=1e-3, atol=1e-3 * np.abs(go["pose"]).max())
+    gp = pg.cpu().numpy()[0]
+    assert np.all(np.abs(gp - go["pose"][0]) <= 1e-3 * np.abs(go["pose"][0]) + 1e-6 + pose_slack), (gp, go["pose"][0])
 
 
 def test_pose_adam_step_matches_oracle(R):
