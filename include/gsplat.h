@@ -242,6 +242,28 @@ int64_t gs_ctx_launch_count(gs_ctx* ctx);
  * contributed gradients in the backward. */
 int gs_frames_counters(gs_frames* fr, int64_t out[4]);
 
+/* D-SSIM loss term and its image gradient for ONE view, allocating nothing.
+ * (The paper has no counterpart: this is a deployment variant of the D-SSIM
+ * part of GS_LOSS_L1_DSSIM.)  It exists for callers that cannot call
+ * cudaMalloc at the point where they need the loss: code running while a
+ * stream is being captured into a CUDA graph (allocation is not capturable),
+ * real-time or serving loops that forbid allocator calls after start-up, and
+ * hosts that hand the library a fixed memory budget.  Its scratch (11 planes
+ * of up to GS_DSSIM_STATIC_MAX_PIXELS floats, 11.5 MiB) is a file-scope device
+ * array that every GPU loading the library holds until the process exits.
+ *   image, target  device, planar float32 [3][height][width];
+ *   dl_dimage      device output [3][height][width]: w_dssim * d(1 - SSIM)/dC;
+ *   loss           device float64 [1], nullable: w_dssim * (1 - mean SSIM).
+ * width * height above GS_DSSIM_STATIC_MAX_PIXELS is rejected with GS_EINVAL.
+ * The first call on a device resolves the scratch's device address (and
+ * uploads the filter window); make that first call before any stream capture.
+ * All calls share the one scratch array: calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * No scratch needs clearing: each call writes every scratch value it reads. */
+#define GS_DSSIM_STATIC_MAX_PIXELS (512 * 512)
+int gs_loss_dssim_static(const float* image, const float* target, int width, int height, float w_dssim,
+                         float* dl_dimage, double* loss, void* stream);
+
 /* Thread-local message describing the calling thread's last error. */
 const char* gs_last_error(void);
 

@@ -26,7 +26,7 @@ EXPORTED = (
     "gs_default_opts", "gs_ctx_create", "gs_ctx_destroy", "gs_scene_load", "gs_scene_borrow", "gs_scene_free",
     "gs_frames_create", "gs_frames_destroy", "gs_frames_reserve", "gs_render_forward", "gs_render_backward",
     "gs_pose_step", "gs_status", "gs_frames_query", "gs_last_error", "gs_version", "gs_ctx_set_profiling",
-    "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step",
+    "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step", "gs_loss_dssim_static",
 )
 
 
@@ -93,6 +93,8 @@ def load(path: str | None = None):
     L.gs_step.argtypes = [vp, vp, C.POINTER(gs_scene_desc), i32, C.POINTER(gs_view), vp, C.POINTER(gs_render_opts),
                           C.POINTER(gs_loss), vp, C.POINTER(gs_grads), vp, vp, vp]
     L.gs_step.restype = C.c_int
+    L.gs_loss_dssim_static.argtypes = [vp, vp, i32, i32, C.c_float, vp, vp, vp]
+    L.gs_loss_dssim_static.restype = C.c_int
     L.gs_pose_step.argtypes = [vp, i32, vp, vp, vp, vp, f64, f64, f64, f64, i32, vp]
     L.gs_status.argtypes = [vp, vp]
     L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -235,6 +237,13 @@ def gs_pose_step(ctx: int, poses, m, v, grad, lr: float, step: int, beta1=0.9, b
                  stream=None) -> None:
     _ck(load().gs_pose_step(C.c_void_p(ctx), int(poses.shape[0]), _ptr(poses), _ptr(m), _ptr(v), _ptr(grad),
                             float(lr), float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def gs_loss_dssim_static(image, target, width: int, height: int, w_dssim: float, dl_dimage, loss=None,
+                         stream=None) -> None:
+    """D-SSIM term of one view with the library's static scratch (no allocation)."""
+    _ck(load().gs_loss_dssim_static(_ptr(image), _ptr(target), int(width), int(height), float(w_dssim),
+                                    _ptr(dl_dimage), _ptr(loss), _stream(stream)))
 
 
 def gs_status(ctx: int, stream=None) -> int:

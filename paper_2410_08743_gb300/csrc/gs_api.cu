@@ -26,6 +26,13 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+namespace gs {
+int set_error(int code, const char* msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+}  // namespace gs
+
 #define CK(call)                                                                               \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \

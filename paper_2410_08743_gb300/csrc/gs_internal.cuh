@@ -145,4 +145,7 @@ void launch_dssim(int n_views, const gs_view* views_host, const long long* img_o
                   const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
                   cudaStream_t s);
 
+// Records a message for gs_last_error() and returns `code` (defined in gs_api.cu).
+int set_error(int code, const char* msg);
+
 }  // namespace gs

@@ -7,6 +7,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cstdio>
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -153,3 +156,72 @@ void launch_dssim(int n_views, const gs_view* views, const long long* img_off, c
 }
 
 }  // namespace gs
+
+// ------------------------------------------------------------ no-alloc variant
+// gs_loss_dssim_static runs the same D-SSIM kernels as the backward pass, but
+// with its scratch in a static device array instead of workspace memory, so
+// that it calls no allocator at all.  Callers that cannot allocate at the
+// point of use (inside CUDA-graph capture, in allocation-free serving loops,
+// under a fixed memory budget) use it.  The array is device memory reserved
+// when the module loads; host code only ever sees the address that
+// cudaGetSymbolAddress returns for the current device.
+
+static __device__ __align__(256) float g_dssim_static_scratch[11 * GS_DSSIM_STATIC_MAX_PIXELS];
+
+namespace {
+std::mutex g_dssim_static_mu;
+constexpr int kMaxDevices = 256;
+float* g_dssim_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int gs_loss_dssim_static(const float* image, const float* target, int width, int height, float w_dssim,
+                                    float* dl_dimage, double* loss, void* stream) {
+    char msg[256];
+    if (!image || !target || !dl_dimage) return gs::set_error(GS_EINVAL, "gs_loss_dssim_static: NULL image/target/output");
+    if (width <= 0 || height <= 0) return gs::set_error(GS_EINVAL, "gs_loss_dssim_static: width and height must be > 0");
+    if ((long long)width * height > GS_DSSIM_STATIC_MAX_PIXELS) {
+        snprintf(msg, sizeof(msg), "gs_loss_dssim_static: %dx%d = %lld pixels exceeds the static scratch limit of %d",
+                 width, height, (long long)width * height, GS_DSSIM_STATIC_MAX_PIXELS);
+        return gs::set_error(GS_EINVAL, msg);
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        snprintf(msg, sizeof(msg), "gs_loss_dssim_static: cudaGetDevice: %s", cudaGetErrorString(e));
+        return gs::set_error(GS_ECUDA, msg);
+    }
+    float* scratch = nullptr;
+    {
+        // once per device, with that device current: the symbol's device address
+        std::lock_guard<std::mutex> lock(g_dssim_static_mu);
+        if (!g_dssim_static_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_dssim_static_scratch);
+            if (e != cudaSuccess || !p) {
+                snprintf(msg, sizeof(msg), "gs_loss_dssim_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+                return gs::set_error(GS_ECUDA, msg);
+            }
+            float w[11];
+            double g[11], sum = 0.0;
+            for (int k = 0; k < 11; k++) { const double x = k - 5; g[k] = exp(-x * x / (2.0 * 1.5 * 1.5)); sum += g[k]; }
+            for (int k = 0; k < 11; k++) w[k] = (float)(g[k] / sum);
+            e = cudaMemcpyToSymbol(gs::c_win, w, sizeof(w));
+            if (e != cudaSuccess) {
+                snprintf(msg, sizeof(msg), "gs_loss_dssim_static: window upload: %s", cudaGetErrorString(e));
+                return gs::set_error(GS_ECUDA, msg);
+            }
+            g_dssim_static_ptr[dev] = static_cast<float*>(p);
+        }
+        scratch = g_dssim_static_ptr[dev];
+    }
+    const gs_view v = {1.0f, 1.0f, 0.0f, 0.0f, width, height};
+    const long long off = 0;
+    gs::launch_dssim(1, &v, &off, image, target, w_dssim, dl_dimage, loss, scratch, static_cast<cudaStream_t>(stream));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof(msg), "gs_loss_dssim_static: launch: %s", cudaGetErrorString(e));
+        return gs::set_error(GS_ECUDA, msg);
+    }
+    return GS_OK;
+}
+
