@@ -239,8 +239,9 @@ int64_t gs_ctx_launch_count(gs_ctx* ctx);
 /* Work counters of the last forward/backward of `fr` (synchronous):
  * out[0] (pixel, splat) pairs evaluated by the forward blend, out[1] pairs
  * blended, out[2] pairs evaluated by the backward blend, out[3] pairs that
- * contributed gradients in the backward. */
-int gs_frames_counters(gs_frames* fr, int64_t out[4]);
+ * contributed gradients in the backward, out[4] sorted-list entries read by
+ * the forward blend, out[5] sorted-list entries read by the backward blend. */
+int gs_frames_counters(gs_frames* fr, int64_t out[6]);
 
 /* D-SSIM loss term and its image gradient for ONE view, allocating nothing.
  * (The paper has no counterpart: this is a deployment variant of the D-SSIM

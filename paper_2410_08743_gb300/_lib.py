@@ -285,7 +285,7 @@ def gs_ctx_launch_count(ctx: int) -> int:
 
 
 def gs_frames_counters(fr: int):
-    out = (C.c_int64 * 4)()
+    out = (C.c_int64 * 6)()
     _ck(load().gs_frames_counters(C.c_void_p(fr), out))
     return [int(x) for x in out]
 

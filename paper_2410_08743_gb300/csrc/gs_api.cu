@@ -52,11 +52,11 @@ int set_error(int code, const char* msg) {
 // Kernel kinds reported by the profiler.
 enum ProfKind {
     PK_SETUP = 0, PK_PRE_FWD, PK_SCAN, PK_SCATTER, PK_SORT, PK_BLEND_FWD, PK_LOSS, PK_DSSIM, PK_BLEND_BWD,
-    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT
+    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT_TILES, PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"setup_views", "preprocess_fwd", "scan_tiles", "scatter_keys",
                                            "segment_sort", "blend_fwd", "loss_finalize", "dssim", "blend_bwd",
-                                           "preprocess_bwd", "pose_reduce", "pose_adam", "memset"};
+                                           "preprocess_bwd", "pose_reduce", "pose_adam", "memset", "count_tiles"};
 
 struct ProfRec {
     int kind;
@@ -186,7 +186,7 @@ struct gs_frames {
     DevBuf<uint2> rect;
     DevBuf<int> radius;
     // per tile
-    DevBuf<uint32_t> counts, starts, cursor, scan_tmp;
+    DevBuf<uint32_t> counts, starts, cursor, scan_tmp, sort_lists, sort_counters;
     DevBuf<float> tile_loss;
     // per key
     DevBuf<unsigned long long> keys, tmp_keys;
@@ -199,7 +199,7 @@ struct gs_frames {
     DevBuf<float> dldc_ssim, ssim_tmp;
     DevBuf<long long> img_off_dev;
     DevBuf<double> loss_tmp;
-    DevBuf<unsigned long long> counters;  // [4] pair counters
+    DevBuf<unsigned long long> counters;  // [8] pair / entry counters
     // gs_step staging (host I/O and fresh gradients)
     DevBuf<float> st_params, st_target, st_image, st_grads;
     DevBuf<double> st_poses, st_pose_grad, st_loss;
@@ -220,6 +220,7 @@ struct gs_frames {
         DevBuf<float>* f1[] = {&Cb, &depth, &gC, &tile_loss, &T_final, &dldc_ssim, &ssim_tmp};
         for (auto* b : f1) b->release();
         rect.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
+        sort_lists.release(); sort_counters.release();
         keys.release(); tmp_keys.release(); sorted_idx.release(); n_contrib.release(); pose_partials.release();
         loss_tmp.release(); counters.release();
         st_params.release(); st_target.release(); st_image.release(); st_grads.release();
@@ -354,7 +355,9 @@ static int ensure_tile_buffers(gs_frames* fr, size_t tiles, bool grow) {
     int rc;
     if ((rc = fr->counts.ensure(tiles + 1, grow, "tile counts")) || (rc = fr->starts.ensure(tiles + 1, grow, "tile starts")) ||
         (rc = fr->cursor.ensure(tiles + 1, grow, "tile cursor")) || (rc = fr->tile_loss.ensure(tiles + 1, grow, "tile loss")) ||
-        (rc = fr->scan_tmp.ensure(gs::scan_tmp_bytes((int)tiles + 1) / 4 + 1, grow, "scan tmp")))
+        (rc = fr->scan_tmp.ensure(gs::scan_tmp_bytes((int)tiles + 1) / 4 + 1, grow, "scan tmp")) ||
+        (rc = fr->sort_lists.ensure(3 * (tiles + 1), grow, "sort lists")) ||
+        (rc = fr->sort_counters.ensure(8, grow, "sort counters")))
         return rc;
     return GS_OK;
 }
@@ -538,7 +541,7 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
     if (n_views == 0) { fr->have_forward = true; return GS_OK; }
     const RenderParams rp = make_params(opts);
     SplatArrays sp = fr->splats();
-    if ((rc = fr->counters.ensure(4, grow, "counters"))) return rc;
+    if ((rc = fr->counters.ensure(8, grow, "counters"))) return rc;
     {
         PROF(PK_SETUP, 1);
         gs::launch_setup_views(views, n_views, poses, fr->vdev.p, rp, s);
@@ -548,7 +551,7 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
         PROF(PK_MEMSET, 0);
         CK(cudaMemsetAsync(fr->counts.p, 0, sizeof(uint32_t) * (T + 1), s));
         CK(cudaMemsetAsync(fr->cursor.p, 0, sizeof(uint32_t) * (T + 1), s));
-        CK(cudaMemsetAsync(fr->counters.p, 0, sizeof(unsigned long long) * 4, s));
+        CK(cudaMemsetAsync(fr->counters.p, 0, sizeof(unsigned long long) * 8, s));
     }
     for (int v0 = 0; v0 < n_views; v0 += kViewChunk) {
         const int nv = std::min(kViewChunk, n_views - v0);
@@ -557,10 +560,15 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
         spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
         {
             PROF(PK_PRE_FWD, 1);
-            gs::launch_preprocess_fwd(scene->d, nv, fr->vdev.p + v0, rp, spc, fr->counts.p, s);
+            gs::launch_preprocess_fwd(scene->d, nv, fr->vdev.p + v0, rp, spc, nullptr, s);
         }
         CK_LAUNCH();
     }
+    {
+        PROF(PK_COUNT_TILES, 1);
+        gs::launch_count_tiles(n, n_views, fr->vdev.p, sp.rect, fr->counts.p, s);
+    }
+    CK_LAUNCH();
     {
         PROF(PK_SCAN, (T + 1 > 4096) ? 3 : 1);
         gs::launch_scan_u32(fr->counts.p, fr->starts.p, T + 1, fr->scan_tmp.p, fr->scan_tmp.cap * 4, s);
@@ -580,8 +588,9 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
     }
     CK_LAUNCH();
     {
-        PROF(PK_SORT, 3);
-        gs::launch_segment_sort(T, fr->starts.p, fr->keys.p, fr->tmp_keys.p, fr->sorted_idx.p, cap, 0, s);
+        PROF(PK_SORT, 4);
+        gs::launch_segment_sort(T, fr->starts.p, fr->keys.p, fr->tmp_keys.p, fr->sorted_idx.p, cap, fr->sort_lists.p,
+                                fr->sort_counters.p, s);
     }
     CK_LAUNCH();
     {
@@ -862,14 +871,16 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 
 int64_t gs_ctx_launch_count(gs_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
-int gs_frames_counters(gs_frames* fr, int64_t out[4]) {
+int gs_frames_counters(gs_frames* fr, int64_t out[6]) {
     if (!fr || !out) return fail(GS_EINVAL, "NULL argument");
-    for (int k = 0; k < 4; k++) out[k] = 0;
+    for (int k = 0; k < 6; k++) out[k] = 0;
     if (!fr->counters.p) return GS_OK;
     CK(cudaSetDevice(fr->ctx->device));
-    unsigned long long c[4];
+    unsigned long long c[8];
     CK(cudaMemcpy(c, fr->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 4; k++) out[k] = (int64_t)c[k];
+    out[4] = (int64_t)c[4];
+    out[5] = (int64_t)c[6];
     return GS_OK;
 }
 

@@ -23,16 +23,29 @@ struct SplatBatch {
     float4 A[BATCH];
     float4 B[BATCH];
     float Cb[BATCH];
+    float2 H[BATCH];   // half-extents of the box holding every pixel with alpha >= alpha_min
 };
+
+// Conservative half-extents of {d : o exp(-1/2 d^T Q d) >= alpha_min}, the
+// ellipse d^T Q d <= R^2 with R^2 = 2 ln(o / alpha_min): |dx| <= R sqrt(Q^-1_xx),
+// |dy| <= R sqrt(Q^-1_yy), widened by 1% + 0.01 px (far above the FP32 error
+// of the alpha test), so a pixel outside the box is certainly skipped by
+// pair_alpha and the box changes no decision.  Near-singular conics get no box.
+__device__ __forceinline__ float2 alpha_box(const float4 a, const float4 b, float amin) {
+    if (!(b.y >= amin)) return make_float2(-1.0f, -1.0f);
+    const float R2 = 2.0f * logf(b.y / amin);
+    const float dq = a.z * b.x - a.w * a.w;
+    if (!(dq > 1e-6f * a.z * b.x)) return make_float2(INFINITY, INFINITY);
+    const float hx = sqrtf(R2 * b.x / dq), hy = sqrtf(R2 * a.z / dq);
+    return make_float2(fmaf(hx, 1.01f, 0.01f), fmaf(hy, 1.01f, 0.01f));
+}
 
 // alpha of one (pixel, splat) pair with a fixed operation sequence, so that
 // the forward and the backward take the same skip decisions.
 //   power = -1/2 (a dx^2 + c dy^2) - b dx dy with d = p - mu_hat (Eq. 3)
 //   returns false when the pair is skipped (power > 0 or alpha < alpha_min).
-__device__ __forceinline__ bool pair_alpha(const float4 a, const float4 b, float px, float py, float amin, float amax,
-                                           float& dx, float& dy, float& G, float& alpha, bool& clamped) {
-    dx = __fsub_rn(px, a.x);
-    dy = __fsub_rn(py, a.y);
+__device__ __forceinline__ bool pair_alpha(const float4 a, const float4 b, float dx, float dy, float amin, float amax,
+                                           float& G, float& alpha, bool& clamped) {
     float q = __fmul_rn(a.z, __fmul_rn(dx, dx));
     q = __fmaf_rn(b.x, __fmul_rn(dy, dy), q);
     const float power = __fmaf_rn(-a.w, __fmul_rn(dx, dy), __fmul_rn(-0.5f, q));
@@ -74,22 +87,28 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
     for (uint32_t base = s; base < e; base += BATCH) {
         if (__syncthreads_count(done) == GS_TILE_PIX) break;
         const uint32_t j = base + threadIdx.x;
+        if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)min((uint32_t)BATCH, e - base));
         if (j < e) {
             const size_t k = vbase + sorted_idx[j];
-            sb.A[threadIdx.x] = sp.A[k];
-            sb.B[threadIdx.x] = sp.B[k];
+            const float4 a = sp.A[k], b = sp.B[k];
+            sb.A[threadIdx.x] = a;
+            sb.B[threadIdx.x] = b;
             sb.Cb[threadIdx.x] = sp.Cb[k];
+            sb.H[threadIdx.x] = alpha_box(a, b, rp.alpha_min);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)BATCH, e - base);
         if (!done) {
             for (int jj = 0; jj < cnt; jj++) {
                 const float4 a = sb.A[jj];
-                const float4 b = sb.B[jj];
-                float dx, dy, G, alpha;
-                bool cl;
+                const float2 h = sb.H[jj];
                 n_eval++;
-                if (!pair_alpha(a, b, fpx, fpy, rp.alpha_min, rp.alpha_max, dx, dy, G, alpha, cl)) continue;
+                const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
+                if (fabsf(dx) > h.x || fabsf(dy) > h.y) continue;
+                const float4 b = sb.B[jj];
+                float G, alpha;
+                bool cl;
+                if (!pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < rp.t_min) { done = true; break; }
                 n_blend++;
@@ -197,6 +216,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
     __shared__ SplatBatch sb;
     __shared__ uint32_t s_idx[BATCH];
     __shared__ uint32_t s_max[GS_TILE_PIX / 32];
+    __shared__ float s_acc[BATCH * 9];
     const int t = blockIdx.x;
     const int v = view_of_tile(tile_base, n_views, t);
     const ViewDev& vd = views[v];
@@ -257,8 +277,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
     uint32_t tile_last = 0;
     for (int w = 0; w < GS_TILE_PIX / 32; w++) tile_last = max(tile_last, s_max[w]);
     if (tile_last > e - s) tile_last = e - s;
+    if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
     const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
     uint32_t n_eval = 0, n_used = 0;
+    const int lane = threadIdx.x & 31;
+    // component held by this lane after the transposed reduction
+    const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
@@ -266,31 +290,39 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
         if ((int)threadIdx.x < cnt) {
             const uint32_t id = sorted_idx[s + bstart + threadIdx.x];
             const size_t k = vbase + id;
+            const float4 a = sp.A[k], b = sp.B[k];
             s_idx[threadIdx.x] = id;
-            sb.A[threadIdx.x] = sp.A[k];
-            sb.B[threadIdx.x] = sp.B[k];
+            sb.A[threadIdx.x] = a;
+            sb.B[threadIdx.x] = b;
             sb.Cb[threadIdx.x] = sp.Cb[k];
+            sb.H[threadIdx.x] = alpha_box(a, b, rp.alpha_min);
         }
+        for (int q = threadIdx.x; q < BATCH * 9; q += GS_TILE_PIX) s_acc[q] = 0.0f;
         __syncthreads();
         for (int jj = cnt - 1; jj >= 0; jj--) {
             const uint32_t pos = (uint32_t)(bstart + jj);
-            bool use = inside && any_grad && pos < last;
             const float4 a = sb.A[jj];
-            const float4 b = sb.B[jj];
-            float dx = 0.f, dy = 0.f, G = 0.f, alpha = 0.f;
-            bool cl = false;
+            const float2 h = sb.H[jj];
+            bool use = inside && any_grad && pos < last;
             n_eval += use;
-            if (use) use = pair_alpha(a, b, fpx, fpy, rp.alpha_min, rp.alpha_max, dx, dy, G, alpha, cl);
+            const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
+            use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
+            if (!__any_sync(0xffffffffu, use)) continue;
+            const float4 b = sb.B[jj];
+            float G = 0.f, alpha = 0.f;
+            bool cl = false;
+            if (use) use = pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl);
+            if (!__any_sync(0xffffffffu, use)) continue;
             n_used += use;
-            float r[9];
+            float r[8], r8 = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 9; c++) r[c] = 0.0f;
+            for (int c = 0; c < 8; c++) r[c] = 0.0f;
             if (use) {
                 const float cb = sb.Cb[jj];
                 const float om = 1.0f - alpha;
                 const float Ti = T / om;
                 const float wgt = alpha * Ti;
-                r[6] = wgt * g0; r[7] = wgt * g1; r[8] = wgt * g2;
+                r[6] = wgt * g0; r[7] = wgt * g1; r8 = wgt * g2;
                 const float dLda = Ti * (b.z * g0 + b.w * g1 + cb * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / om;
                 S0 = fmaf(b.z, wgt, S0); S1 = fmaf(b.w, wgt, S1); S2 = fmaf(cb, wgt, S2);
                 T = Ti;
@@ -304,15 +336,47 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
                     r[4] = -0.5f * dp * dy * dy;
                 }
             }
-            if (__any_sync(0xffffffffu, use)) {
+            // transposed reduce-scatter of r[0..7]: afterwards lane L (L % 4 == 0)
+            // holds the warp sum of component comp(L)
 #pragma unroll
-                for (int c = 0; c < 9; c++) r[c] = warp_sum(r[c]);
-                if ((threadIdx.x & 31) == 0) {
-                    const size_t k = vbase + s_idx[jj];
-                    atomicAdd(g2d.gA + k, make_float4(r[0], r[1], r[2], r[3]));
-                    atomicAdd(g2d.gB + k, make_float4(r[4], r[5], r[6], r[7]));
-                    atomicAdd(g2d.gC + k, r[8]);
-                }
+            for (int k = 0; k < 4; k++) {
+                const bool hi = lane & 16;
+                const float send = hi ? r[k] : r[k + 4];
+                const float keep = hi ? r[k + 4] : r[k];
+                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const bool hi = lane & 8;
+                const float send = hi ? r[k] : r[k + 2];
+                const float keep = hi ? r[k + 2] : r[k];
+                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            {
+                const bool hi = lane & 4;
+                const float send = hi ? r[0] : r[1];
+                const float keep = hi ? r[1] : r[0];
+                r[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            r[0] += __shfl_xor_sync(0xffffffffu, r[0], 2);
+            r[0] += __shfl_xor_sync(0xffffffffu, r[0], 1);
+            r8 = warp_sum(r8);
+            if ((lane & 3) == 0) atomicAdd(&s_acc[jj * 9 + comp], r[0]);
+            if (lane == 1) atomicAdd(&s_acc[jj * 9 + 8], r8);
+        }
+        __syncthreads();
+        // one set of vector atomics per (tile, splat) of the batch
+        if ((int)threadIdx.x < cnt) {
+            const float* acc = s_acc + threadIdx.x * 9;
+            const float4 ga = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            const float4 gb = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            const bool nz = (ga.x != 0.f) | (ga.y != 0.f) | (ga.z != 0.f) | (ga.w != 0.f) | (gb.x != 0.f) |
+                            (gb.y != 0.f) | (gb.z != 0.f) | (gb.w != 0.f) | (acc[8] != 0.f);
+            if (nz) {
+                const size_t k = vbase + s_idx[threadIdx.x];
+                atomicAdd(g2d.gA + k, ga);
+                atomicAdd(g2d.gB + k, gb);
+                atomicAdd(g2d.gC + k, acc[8]);
             }
         }
     }

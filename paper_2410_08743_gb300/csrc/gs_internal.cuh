@@ -111,9 +111,13 @@ size_t scan_tmp_bytes(int n);
 void launch_scatter_keys(int n, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
                          uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s);
 
+void launch_count_tiles(int n, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
+                        cudaStream_t s);
+
+// lists: [3][n_tiles] work lists; counters: 6 words (list lengths, work cursors)
 void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys,
-                         unsigned long long* tmp_keys, uint32_t* sorted_idx, uint32_t cap, int idx_bits,
-                         cudaStream_t s);
+                         unsigned long long* tmp_keys, uint32_t* sorted_idx, uint32_t cap, uint32_t* lists,
+                         uint32_t* counters, cudaStream_t s);
 
 void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
                       const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,

@@ -317,9 +317,11 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views
         sp.rect[k] = make_uint2(pack16(ko.x0, ko.y0), pack16(ko.x1, ko.y1));
         sp.depth[k] = ko.depth;
         sp.radius[k] = ko.radius;
-        uint32_t* tc = tile_counts + vd.tile_base;
-        for (int ty = ko.y0; ty < ko.y1; ty++)
-            for (int tx = ko.x0; tx < ko.x1; tx++) atomicAdd(tc + ty * vd.gw + tx, 1u);
+        if (tile_counts) {  // direct per-key counting (the sort stage normally counts per chunk)
+            uint32_t* tc = tile_counts + vd.tile_base;
+            for (int ty = ko.y0; ty < ko.y1; ty++)
+                for (int tx = ko.x0; tx < ko.x1; tx++) atomicAdd(tc + ty * vd.gw + tx, 1u);
+        }
     }
 }
 

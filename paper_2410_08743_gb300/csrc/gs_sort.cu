@@ -103,64 +103,177 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t
     }
 }
 
-// ------------------------------------------------------------ scatter
-__global__ void __launch_bounds__(256) k_scatter_keys(int n, int n_views, const ViewDev* __restrict__ views,
-                                                      const uint2* __restrict__ rect, const float* __restrict__ depth,
-                                                      const uint32_t* __restrict__ starts, uint32_t* __restrict__ cursor,
-                                                      unsigned long long* __restrict__ keys, uint32_t cap,
-                                                      int* __restrict__ status) {
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (size_t)n * n_views) return;
-    const uint2 r = rect[k];
-    const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-    if (x1 <= x0) return;
-    const int v = (int)(k / (size_t)n);
-    const uint32_t i = (uint32_t)(k - (size_t)v * n);
-    const int gw = views[v].gw, tb = views[v].tile_base;
-    const unsigned long long key = ((unsigned long long)__float_as_uint(depth[k]) << 32) | i;
-    for (int ty = y0; ty < y1; ty++)
-        for (int tx = x0; tx < x1; tx++) {
-            const int t = tb + ty * gw + tx;
-            const uint32_t pos = starts[t] + atomicAdd(cursor + t, 1u);
-            if (pos < cap) keys[pos] = key;
-            else gs_set_status(status, GS_DEV_OVERFLOW);
+// ------------------------------------------------------------ count + scatter
+// One CTA per (view, chunk of CHUNK Gaussians).  The CTA first builds a
+// shared-memory histogram of its keys over the view's tiles, so that global
+// atomics go per (CTA, tile) instead of per key:
+//   count:   tile_counts[t] += hist[t]
+//   scatter: base = cursor[t] += hist[t]; each key takes starts[t] + base + a
+//            shared-memory slot.
+// Views with more than SMEM_TILES tiles fall back to one global atomic per key.
+#define CHUNK 4096
+#define SMEM_TILES 8192
+#define CS_THREADS 256
+
+__device__ __forceinline__ void rect_of(const uint2 r, int& x0, int& y0, int& x1, int& y1) {
+    x0 = r.x & 0xffff; y0 = r.x >> 16; x1 = r.y & 0xffff; y1 = r.y >> 16;
+}
+
+__global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, const ViewDev* __restrict__ views,
+                                                           const uint2* __restrict__ rect,
+                                                           uint32_t* __restrict__ tile_counts) {
+    __shared__ uint32_t hist[SMEM_TILES];
+    const int v = blockIdx.y;
+    const int gw = views[v].gw, ntile = gw * views[v].gh, tb = views[v].tile_base;
+    const int i0 = blockIdx.x * CHUNK, i1 = min(n, i0 + CHUNK);
+    const size_t vb = (size_t)v * n;
+    if (ntile > SMEM_TILES) {
+        for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
+            int x0, y0, x1, y1;
+            rect_of(rect[vb + i], x0, y0, x1, y1);
+            for (int ty = y0; ty < y1; ty++)
+                for (int tx = x0; tx < x1; tx++) atomicAdd(tile_counts + tb + ty * gw + tx, 1u);
         }
+        return;
+    }
+    for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
+        int x0, y0, x1, y1;
+        rect_of(rect[vb + i], x0, y0, x1, y1);
+        for (int ty = y0; ty < y1; ty++)
+            for (int tx = x0; tx < x1; tx++) atomicAdd(hist + ty * gw + tx, 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntile; t += CS_THREADS)
+        if (hist[t]) atomicAdd(tile_counts + tb + t, hist[t]);
+}
+
+__global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewDev* __restrict__ views,
+                                                             const uint2* __restrict__ rect,
+                                                             const float* __restrict__ depth,
+                                                             const uint32_t* __restrict__ starts,
+                                                             uint32_t* __restrict__ cursor,
+                                                             unsigned long long* __restrict__ keys, uint32_t cap,
+                                                             int* __restrict__ status) {
+    __shared__ uint32_t hist[SMEM_TILES];
+    __shared__ int s_over;
+    const int v = blockIdx.y;
+    const int gw = views[v].gw, ntile = gw * views[v].gh, tb = views[v].tile_base;
+    const int i0 = blockIdx.x * CHUNK, i1 = min(n, i0 + CHUNK);
+    const size_t vb = (size_t)v * n;
+    if (threadIdx.x == 0) s_over = 0;
+    if (ntile > SMEM_TILES) {
+        __syncthreads();
+        for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
+            int x0, y0, x1, y1;
+            rect_of(rect[vb + i], x0, y0, x1, y1);
+            if (x1 <= x0) continue;
+            const unsigned long long key = ((unsigned long long)__float_as_uint(depth[vb + i]) << 32) | (uint32_t)i;
+            for (int ty = y0; ty < y1; ty++)
+                for (int tx = x0; tx < x1; tx++) {
+                    const int t = tb + ty * gw + tx;
+                    const uint32_t pos = starts[t] + atomicAdd(cursor + t, 1u);
+                    if (pos < cap) keys[pos] = key; else s_over = 1;
+                }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
+        return;
+    }
+    for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
+        int x0, y0, x1, y1;
+        rect_of(rect[vb + i], x0, y0, x1, y1);
+        for (int ty = y0; ty < y1; ty++)
+            for (int tx = x0; tx < x1; tx++) atomicAdd(hist + ty * gw + tx, 1u);
+    }
+    __syncthreads();
+    // reserve this CTA's range in every touched tile
+    for (int t = threadIdx.x; t < ntile; t += CS_THREADS) {
+        const uint32_t c = hist[t];
+        if (c) hist[t] = starts[tb + t] + atomicAdd(cursor + tb + t, c);
+    }
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
+        int x0, y0, x1, y1;
+        rect_of(rect[vb + i], x0, y0, x1, y1);
+        if (x1 <= x0) continue;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(depth[vb + i]) << 32) | (uint32_t)i;
+        for (int ty = y0; ty < y1; ty++)
+            for (int tx = x0; tx < x1; tx++) {
+                const uint32_t pos = atomicAdd(hist + ty * gw + tx, 1u);
+                if (pos < cap) keys[pos] = key; else s_over = 1;
+            }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
+}
+
+void launch_count_tiles(int n, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
+                        cudaStream_t s) {
+    if (n <= 0 || n_views <= 0) return;
+    dim3 grid((n + CHUNK - 1) / CHUNK, n_views);
+    k_count_tiles<<<grid, CS_THREADS, 0, s>>>(n, views, rect, tile_counts);
 }
 
 void launch_scatter_keys(int n, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
                          uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s) {
-    const size_t total = (size_t)n * n_views;
-    if (total == 0) return;
-    k_scatter_keys<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, n_views, views, sp.rect, sp.depth, starts, cursor,
-                                                                   keys, cap, status);
+    if (n <= 0 || n_views <= 0) return;
+    dim3 grid((n + CHUNK - 1) / CHUNK, n_views);
+    k_scatter_tiles<<<grid, CS_THREADS, 0, s>>>(n, views, sp.rect, sp.depth, starts, cursor, keys, cap, status);
 }
 
 // ------------------------------------------------------------ segment sort
-// Stable LSD radix sort (8-bit digits) of one tile's 64-bit keys held in
-// `src`/`dst` (shared or global memory).  Digits on which every key agrees
-// are skipped.  Each warp owns a contiguous chunk; ranks inside a 32-key step
-// come from match_any, so equal digits keep their order and the sort is
-// stable.  Returns the buffer holding the result.
+// Keys are (depth bits << 32 | Gaussian index), unique within a tile.  A tile
+// is sorted by a stable LSD radix sort (8-bit digits) over the depth digits
+// that vary within it; equal depths then sit in runs that are put in index
+// order by a short insertion sort.  If some run is longer than RUN_MAX the
+// whole list is re-sorted on every varying digit (index digits first).
+#define RUN_MAX 32
+
+// Block-wide exclusive scan of `v` (one value per thread); returns the
+// thread's offset.  s_warp holds THREADS/32 words.
 template <int THREADS>
-__device__ unsigned long long* block_radix_sort(unsigned long long* src, unsigned long long* dst, int n,
-                                                uint32_t* hist /* [THREADS/32][256] */) {
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < THREADS / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < THREADS / 32) s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t r = inc - v + s_warp[warp];
+    __syncthreads();
+    return r;
+}
+
+// Stable LSD radix passes (8-bit digits) over the digits set in `vary`.  Each
+// warp owns a contiguous chunk; ranks inside a 32-key step come from
+// match_any, so equal digits keep their order.  hist is [THREADS/32][256].
+// Returns the buffer holding the result.
+template <int THREADS>
+__device__ unsigned long long* block_radix_sort_bits(unsigned long long* src, unsigned long long* dst, int n,
+                                                     unsigned long long vary, uint32_t* hist) {
     constexpr int W = THREADS / 32;
+    constexpr int E = 256 * W / THREADS;  // = 8 digit-major counters per thread
+    __shared__ uint32_t s_warp[W];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // bits that vary across the segment
-    __shared__ unsigned long long s_or[W], s_and[W];
-    unsigned long long vo = 0ull, va = ~0ull;
-    for (int j = threadIdx.x; j < n; j += THREADS) { unsigned long long x = src[j]; vo |= x; va &= x; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) { vo |= __shfl_xor_sync(0xffffffffu, vo, o); va &= __shfl_xor_sync(0xffffffffu, va, o); }
-    if (lane == 0) { s_or[warp] = vo; s_and[warp] = va; }
-    __syncthreads();
-    unsigned long long vary = 0ull;
-    {
-        unsigned long long o2 = 0ull, a2 = ~0ull;
-        for (int w = 0; w < W; w++) { o2 |= s_or[w]; a2 &= s_and[w]; }
-        vary = o2 ^ a2;
-    }
     const int chunk = ((n + W - 1) / W + 31) & ~31;
     const int cb = warp * chunk;
     const int ce = min(n, cb + chunk);
@@ -181,25 +294,23 @@ __device__ unsigned long long* block_radix_sort(unsigned long long* src, unsigne
             __syncwarp();
         }
         __syncthreads();
-        // B: offsets in (digit, warp) order.  Threads 0..255 own one digit
-        // each: warp prefix within the digit, then a scan of digit totals.
-        if (threadIdx.x < 256) {
-            __shared__ uint32_t s_ws[8];
-            const int d = threadIdx.x;
-            uint32_t run = 0;
-            for (int w = 0; w < W; w++) { const uint32_t c = hist[w * 256 + d]; hist[w * 256 + d] = run; run += c; }
-            uint32_t inc = run;
+        // B: exclusive scan in (digit, warp) order; thread t owns entries
+        // [E t, E t + E) of that order.
+        {
+            uint32_t c[E], sum = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
+            for (int k = 0; k < E; k++) {
+                const int q = E * threadIdx.x + k;        // q = d * W + w
+                c[k] = hist[(q % W) * 256 + q / W];
+                sum += c[k];
             }
-            if (lane == 31) s_ws[warp] = inc;
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            uint32_t wpre = 0;
-            for (int w = 0; w < warp; w++) wpre += s_ws[w];
-            const uint32_t dbase = inc - run + wpre;
-            for (int w = 0; w < W; w++) hist[w * 256 + d] += dbase;
+            uint32_t off = block_scan_excl<THREADS>(sum, s_warp);
+#pragma unroll
+            for (int k = 0; k < E; k++) {
+                const int q = E * threadIdx.x + k;
+                hist[(q % W) * 256 + q / W] = off;
+                off += c[k];
+            }
         }
         __syncthreads();
         // C: stable scatter
@@ -224,71 +335,238 @@ __device__ unsigned long long* block_radix_sort(unsigned long long* src, unsigne
     return src;
 }
 
-// Shared-memory variant for segments of at most CAP keys; segments outside
-// (lo, hi] are left to another launch.
+// OR and AND of n keys over the block -> bits that vary.
+template <int THREADS>
+__device__ unsigned long long block_vary_bits(const unsigned long long* src, int n) {
+    constexpr int W = THREADS / 32;
+    __shared__ unsigned long long s_or[W], s_and[W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long vo = 0ull, va = ~0ull;
+    for (int j = threadIdx.x; j < n; j += THREADS) { const unsigned long long x = src[j]; vo |= x; va &= x; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) { vo |= __shfl_xor_sync(0xffffffffu, vo, o); va &= __shfl_xor_sync(0xffffffffu, va, o); }
+    if (lane == 0) { s_or[warp] = vo; s_and[warp] = va; }
+    __syncthreads();
+    unsigned long long o2 = 0ull, a2 = ~0ull;
+    for (int w = 0; w < W; w++) { o2 |= s_or[w]; a2 &= s_and[w]; }
+    __syncthreads();
+    return o2 ^ a2;
+}
+
+// Longest run of equal depth bits in a depth-sorted list (block-wide max).
+template <int THREADS>
+__device__ int block_max_depth_run(const unsigned long long* a, int n) {
+    __shared__ int s_max;
+    if (threadIdx.x == 0) s_max = 1;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += THREADS) {
+        const uint32_t dj = (uint32_t)(a[j] >> 32);
+        if (j > 0 && (uint32_t)(a[j - 1] >> 32) == dj) continue;  // not a run start
+        int m = 1;
+        while (j + m < n && (uint32_t)(a[j + m] >> 32) == dj && m <= RUN_MAX) m++;
+        if (m > 1) atomicMax(&s_max, m);
+    }
+    __syncthreads();
+    const int r = s_max;
+    __syncthreads();
+    return r;
+}
+
+// Puts every run of equal depth in index order (runs of at most RUN_MAX).
+template <int THREADS>
+__device__ void block_fix_ties(unsigned long long* a, int n) {
+    for (int j = threadIdx.x; j < n; j += THREADS) {
+        const uint32_t dj = (uint32_t)(a[j] >> 32);
+        if (j > 0 && (uint32_t)(a[j - 1] >> 32) == dj) continue;
+        int m = 1;
+        while (j + m < n && (uint32_t)(a[j + m] >> 32) == dj) m++;
+        for (int p = j + 1; p < j + m; p++) {  // insertion sort of the run
+            const unsigned long long x = a[p];
+            int q = p - 1;
+            while (q >= j && a[q] > x) { a[q + 1] = a[q]; q--; }
+            a[q + 1] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Sorts n unique keys held in b0 (b1 is scratch of the same size) into
+// (depth, index) order; returns the buffer holding the result.
+template <int THREADS>
+__device__ unsigned long long* sort_tile_keys(unsigned long long* b0, unsigned long long* b1, int n, uint32_t* hist) {
+    const unsigned long long vary = block_vary_bits<THREADS>(b0, n);
+    unsigned long long* r = block_radix_sort_bits<THREADS>(b0, b1, n, vary & 0xffffffff00000000ull, hist);
+    if (block_max_depth_run<THREADS>(r, n) > RUN_MAX) {
+        unsigned long long* o = (r == b0) ? b1 : b0;
+        r = block_radix_sort_bits<THREADS>(r, o, n, vary, hist);
+    } else {
+        block_fix_ties<THREADS>(r, n);
+    }
+    return r;
+}
+
+// Classifies tiles by list length into work lists: [0] <= SMALL_CAP keys,
+// [1] <= MED_CAP, [2] longer.  Single-key tiles are written directly.
+#define SMALL_T 256
+#define SMALL_CAP 2048
+#define MED_T 512
+#define MED_CAP 5632
+#define LARGE_T 512
+
+__global__ void k_classify_tiles(int n_tiles, const uint32_t* __restrict__ starts, uint32_t cap,
+                                 const unsigned long long* __restrict__ keys, uint32_t* __restrict__ sorted_idx,
+                                 uint32_t* __restrict__ lists, uint32_t* __restrict__ counts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    uint32_t s = starts[t], e = starts[t + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    const uint32_t n = e - s;
+    if (n == 0) return;
+    if (n == 1) { sorted_idx[s] = (uint32_t)(keys[s] & 0xffffffffull); return; }
+    const int c = n <= SMALL_CAP ? 0 : (n <= MED_CAP ? 1 : 2);
+    const uint32_t pos = atomicAdd(counts + c, 1u);
+    lists[(size_t)c * n_tiles + pos] = (uint32_t)t;
+}
+
+// Persistent shared-memory sort over a work list (small or medium tiles).
 template <int THREADS, int CAP>
-__global__ void __launch_bounds__(THREADS) k_segsort_smem(int n_tiles, const uint32_t* __restrict__ starts,
+__global__ void __launch_bounds__(THREADS) k_segsort_list(int n_tiles, const uint32_t* __restrict__ starts, uint32_t cap,
                                                           const unsigned long long* __restrict__ keys,
-                                                          uint32_t* __restrict__ sorted_idx, uint32_t cap, int lo,
-                                                          int hi) {
+                                                          uint32_t* __restrict__ sorted_idx,
+                                                          const uint32_t* __restrict__ list,
+                                                          const uint32_t* __restrict__ list_count,
+                                                          uint32_t* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* b0 = reinterpret_cast<unsigned long long*>(smem_raw);
     unsigned long long* b1 = b0 + CAP;
     uint32_t* hist = reinterpret_cast<uint32_t*>(b1 + CAP);
-    const int t = blockIdx.x;
-    if (t >= n_tiles) return;
-    uint32_t s = starts[t], e = starts[t + 1];
-    if (s > cap) s = cap;
-    if (e > cap) e = cap;
-    const int n = (int)(e - s);
-    if (n <= lo || n > hi) return;
-    for (int j = threadIdx.x; j < n; j += THREADS) b0[j] = keys[s + j];
-    __syncthreads();
-    unsigned long long* r = block_radix_sort<THREADS>(b0, b1, n, hist);
-    for (int j = threadIdx.x; j < n; j += THREADS) sorted_idx[s + j] = (uint32_t)(r[j] & 0xffffffffull);
+    __shared__ uint32_t s_item;
+    const uint32_t total = *list_count;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        const uint32_t t = list[item];
+        uint32_t s = starts[t], e = starts[t + 1];
+        if (s > cap) s = cap;
+        if (e > cap) e = cap;
+        const int n = (int)(e - s);
+        for (int j = threadIdx.x; j < n; j += THREADS) b0[j] = keys[s + j];
+        __syncthreads();
+        unsigned long long* r = sort_tile_keys<THREADS>(b0, b1, n, hist);
+        for (int j = threadIdx.x; j < n; j += THREADS) sorted_idx[s + j] = (uint32_t)(r[j] & 0xffffffffull);
+        __syncthreads();
+    }
 }
 
-// Global-memory variant for long segments (one block per segment).
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_segsort_global(int n_tiles, const uint32_t* __restrict__ starts,
-                                                            unsigned long long* __restrict__ keys,
-                                                            unsigned long long* __restrict__ tmp,
-                                                            uint32_t* __restrict__ sorted_idx, uint32_t cap, int lo) {
-    __shared__ uint32_t hist[(THREADS / 32) * 256];
-    const int t = blockIdx.x;
-    if (t >= n_tiles) return;
-    uint32_t s = starts[t], e = starts[t + 1];
-    if (s > cap) s = cap;
-    if (e > cap) e = cap;
-    const int n = (int)(e - s);
-    if (n <= lo) return;
-    unsigned long long* r = block_radix_sort<THREADS>(keys + s, tmp + s, n, hist);
-    for (int j = threadIdx.x; j < n; j += THREADS) sorted_idx[s + j] = (uint32_t)(r[j] & 0xffffffffull);
+// Long lists: one MSD pass in global memory on the highest varying digit
+// splits the list into 256 buckets (written to tmp), then runs of whole
+// buckets of at most MED_CAP keys are sorted in shared memory.  A bucket
+// longer than MED_CAP is sorted in global memory.
+__global__ void __launch_bounds__(LARGE_T) k_segsort_large(int n_tiles, const uint32_t* __restrict__ starts,
+                                                           uint32_t cap, unsigned long long* __restrict__ keys,
+                                                           unsigned long long* __restrict__ tmp,
+                                                           uint32_t* __restrict__ sorted_idx,
+                                                           const uint32_t* __restrict__ list,
+                                                           const uint32_t* __restrict__ list_count,
+                                                           uint32_t* __restrict__ work) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* b0 = reinterpret_cast<unsigned long long*>(smem_raw);
+    unsigned long long* b1 = b0 + MED_CAP;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(b1 + MED_CAP);
+    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_bucket[257];
+    __shared__ uint32_t s_start[257];
+    const uint32_t total = *list_count;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        const uint32_t t = list[item];
+        uint32_t s = starts[t], e = starts[t + 1];
+        if (s > cap) s = cap;
+        if (e > cap) e = cap;
+        const int n = (int)(e - s);
+        unsigned long long* src = keys + s;
+        unsigned long long* dst = tmp + s;
+        const unsigned long long vary = block_vary_bits<LARGE_T>(src, n);
+        int top = 56;
+        while (top > 0 && ((vary >> top) & 0xffull) == 0ull) top -= 8;
+        for (int d = threadIdx.x; d < 257; d += LARGE_T) s_bucket[d] = 0u;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += LARGE_T) atomicAdd(&s_bucket[(src[j] >> top) & 0xffull], 1u);
+        __syncthreads();
+        {
+            const uint32_t c = threadIdx.x < 256 ? s_bucket[threadIdx.x] : 0u;
+            __shared__ uint32_t s_w[LARGE_T / 32];
+            const uint32_t off = block_scan_excl<LARGE_T>(c, s_w);
+            if (threadIdx.x < 256) { s_bucket[threadIdx.x] = off; s_start[threadIdx.x] = off; }
+            if (threadIdx.x == 0) s_start[256] = (uint32_t)n;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += LARGE_T) {
+            const unsigned long long x = src[j];
+            const uint32_t pos = atomicAdd(&s_bucket[(x >> top) & 0xffull], 1u);
+            dst[pos] = x;
+        }
+        __syncthreads();
+        int d0 = 0;
+        while (d0 < 256) {
+            const uint32_t c0 = s_start[d0];
+            int d1 = d0 + 1;
+            while (d1 < 256 && s_start[d1 + 1] - c0 <= (uint32_t)MED_CAP) d1++;
+            const int m = (int)(s_start[d1] - c0);
+            if (m > MED_CAP) {
+                // one oversized bucket: sort in global memory (tmp <-> keys)
+                unsigned long long* r = sort_tile_keys<LARGE_T>(dst + c0, src + c0, m, hist);
+                for (int j = threadIdx.x; j < m; j += LARGE_T) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
+            } else if (m > 0) {
+                for (int j = threadIdx.x; j < m; j += LARGE_T) b0[j] = dst[c0 + j];
+                __syncthreads();
+                unsigned long long* r = sort_tile_keys<LARGE_T>(b0, b1, m, hist);
+                for (int j = threadIdx.x; j < m; j += LARGE_T) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
+            }
+            __syncthreads();
+            d0 = d1;
+        }
+        __syncthreads();
+    }
 }
 
-#define SEG_SMALL_T 256
-#define SEG_SMALL_CAP 2048
-#define SEG_MED_T 512
-#define SEG_MED_CAP 12288
+static int g_num_sms = 0;
 
 void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys, unsigned long long* tmp_keys,
-                         uint32_t* sorted_idx, uint32_t cap, int, cudaStream_t s) {
+                         uint32_t* sorted_idx, uint32_t cap, uint32_t* lists, uint32_t* counters, cudaStream_t s) {
     if (n_tiles <= 0) return;
     static bool attr_done = false;
-    const size_t sm_small = 2 * sizeof(unsigned long long) * SEG_SMALL_CAP + sizeof(uint32_t) * (SEG_SMALL_T / 32) * 256;
-    const size_t sm_med = 2 * sizeof(unsigned long long) * SEG_MED_CAP + sizeof(uint32_t) * (SEG_MED_T / 32) * 256;
+    const size_t sm_small = 2 * sizeof(unsigned long long) * SMALL_CAP + sizeof(uint32_t) * (SMALL_T / 32) * 256;
+    const size_t sm_med = 2 * sizeof(unsigned long long) * MED_CAP + sizeof(uint32_t) * (MED_T / 32) * 256;
+    const size_t sm_large = 2 * sizeof(unsigned long long) * MED_CAP + sizeof(uint32_t) * (LARGE_T / 32) * 256;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_segsort_smem<SEG_SMALL_T, SEG_SMALL_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_segsort_list<SMALL_T, SMALL_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm_small);
-        cudaFuncSetAttribute(k_segsort_smem<SEG_MED_T, SEG_MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm_med);
+        cudaFuncSetAttribute(k_segsort_list<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_med);
+        cudaFuncSetAttribute(k_segsort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_large);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         attr_done = true;
     }
-    k_segsort_smem<SEG_SMALL_T, SEG_SMALL_CAP><<<n_tiles, SEG_SMALL_T, sm_small, s>>>(n_tiles, starts, keys, sorted_idx,
-                                                                                      cap, 0, SEG_SMALL_CAP);
-    k_segsort_smem<SEG_MED_T, SEG_MED_CAP><<<n_tiles, SEG_MED_T, sm_med, s>>>(n_tiles, starts, keys, sorted_idx, cap,
-                                                                              SEG_SMALL_CAP, SEG_MED_CAP);
-    k_segsort_global<1024><<<n_tiles, 1024, 0, s>>>(n_tiles, starts, keys, tmp_keys, sorted_idx, cap, SEG_MED_CAP);
+    // counters: [0..2] list lengths, [3..5] work cursors
+    cudaMemsetAsync(counters, 0, 6 * sizeof(uint32_t), s);
+    k_classify_tiles<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_tiles, starts, cap, keys, sorted_idx, lists, counters);
+    const int sms = g_num_sms > 0 ? g_num_sms : 152;
+    k_segsort_large<<<sms * 2, LARGE_T, sm_large, s>>>(n_tiles, starts, cap, keys, tmp_keys, sorted_idx,
+                                                       lists + 2 * (size_t)n_tiles, counters + 2, counters + 5);
+    k_segsort_list<MED_T, MED_CAP><<<sms * 2, MED_T, sm_med, s>>>(n_tiles, starts, cap, keys, sorted_idx,
+                                                                  lists + (size_t)n_tiles, counters + 1, counters + 4);
+    k_segsort_list<SMALL_T, SMALL_CAP><<<sms * 5, SMALL_T, sm_small, s>>>(n_tiles, starts, cap, keys, sorted_idx,
+                                                                          lists, counters, counters + 3);
 }
 
 }  // namespace gs

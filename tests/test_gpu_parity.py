@@ -42,11 +42,37 @@ def _ragged_case(seed=5, n=3000, deg=3):
     return sc, views, poses
 
 
+def _dense_case(n, seed=31):
+    """Many Gaussians in a small image: long per-tile lists (the medium and
+    the MSD-split paths of the per-tile sort)."""
+    sc = synth.make_scene_box(seed, n, sh_degree=1, lo=(-1.2, -0.9, 3.0), hi=(1.2, 0.9, 6.0))
+    views = [dict(fx=40.0, fy=40.0, cx=24.0, cy=20.0, width=48, height=40)]
+    return sc, views, synth.pose_from_center(np.eye(3), np.zeros(3))[None]
+
+
+def _same_depth_case(n=30000, seed=32):
+    """Nearly equal depths: FP32 depth ties (broken by index) and one MSD bucket
+    longer than the shared-memory capacity (a few far Gaussians widen the
+    varying depth bits)."""
+    rng = np.random.default_rng(seed)
+    sc = synth.make_scene_box(seed, n, sh_degree=0, lo=(-0.3, -0.25, 4.0), hi=(0.3, 0.25, 4.1))
+    sc["means"][:, 2] = (4.0 + rng.integers(0, 4, n) * 1e-6).astype(np.float32)
+    sc["means"][:3] = np.array([[0.0, 0.0, 60.0], [0.01, 0.0, 90.0], [0.0, 0.01, 120.0]], np.float32)
+    sc["scales"][:3] = 1.0
+    sc["opac"][:] = 0.05
+    views = [dict(fx=60.0, fy=60.0, cx=16.0, cy=16.0, width=32, height=32)]
+    return sc, views, synth.pose_from_center(np.eye(3), np.zeros(3))[None]
+
+
 CASES = {
     "tiny": lambda: (lambda w: (w["scene"], w["views"], w["poses"]))(synth.tiny_workload(0)),
     "ragged_sh3": lambda: _ragged_case(),
     "ragged_sh1": lambda: _ragged_case(7, 2500, 1),
+    "dense_medium": lambda: _dense_case(20000),
+    "dense_large": lambda: _dense_case(120000),
+    "same_depth": lambda: _same_depth_case(),
 }
+GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium"]
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -65,6 +91,11 @@ def test_keys_bit_exact(R, case):
     assert int(R.query(L.GS_Q_NUM_KEYS)[0]) == k["n_keys"]
     assert np.array_equal(R.query(L.GS_Q_TILE_RANGES).reshape(-1, 2), k["ranges"])
     assert np.array_equal(R.query(L.GS_Q_SORTED_IDX), k["idx"]), "sorted tile lists differ"
+    lens = k["ranges"][:, 1] - k["ranges"][:, 0]
+    if case == "dense_medium":
+        assert lens.max() > 2048          # medium path exercised
+    if case in ("dense_large", "same_depth"):
+        assert lens.max() > 12288         # MSD-split path exercised
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -107,7 +138,7 @@ def test_forward_image_and_splats(R, case):
     np.testing.assert_allclose(got[ok, 6:9], vals[ok, 6:9], rtol=0, atol=2e-6)
 
 
-@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("case", GRAD_CASES)
 def test_backward_gradients_and_pose(R, case):
     sc, views, poses = CASES[case]()
     p, P, img, _, _ = gpu_forward(R, sc, views, poses)
