@@ -362,6 +362,7 @@ def run_gpu(args):
             "counters": {"keys": n_keys, "pairs_eval_fwd": counters[0], "pairs_blend_fwd": counters[1],
                          "pairs_eval_bwd": counters[2], "pairs_grad_bwd": counters[3],
                          "entries_read_fwd": counters[4], "entries_read_bwd": counters[5],
+                         "entries_sorted": counters[6],
                          "keys_per_gaussian_view": n_keys / (n * V)},
             "status": st,
         }

@@ -61,7 +61,12 @@ enum {
                                  capacities reserved so far and report
                                  GS_EOVERFLOW through gs_status() instead of
                                  growing (required inside CUDA-graph capture) */
-    GS_F_HOST_IO = 1u << 1    /* gs_step only: every array argument is host memory */
+    GS_F_HOST_IO = 1u << 1,   /* gs_step only: every array argument is host memory */
+    GS_F_FULL_SORT = 1u << 2  /* sort every tile's whole list before blending.  By
+                                 default a tile is sorted only as far as the forward
+                                 blend consumes it (identical image and gradients);
+                                 GS_Q_SORTED_IDX then holds each tile's sorted prefix
+                                 of GS_Q_SORTED_COUNT entries. */
 };
 
 typedef struct gs_ctx gs_ctx;
@@ -219,7 +224,8 @@ enum {
     GS_Q_T_FINAL = 6,         /* float [pixels]: final transmittance */
     GS_Q_N_CONTRIB = 7,       /* uint32 [pixels]: 1 + last blended list position in the tile */
     GS_Q_MEAN2D = 8,          /* float [V*N][2]: projected mean (0 where culled) */
-    GS_Q_SPLAT = 9            /* float [V*N][9]: mu_hat(2), conic(3), opacity, colour(3) */
+    GS_Q_SPLAT = 9,           /* float [V*N][9]: mu_hat(2), conic(3), opacity, colour(3) */
+    GS_Q_SORTED_COUNT = 10    /* uint32 [tiles]: length of each tile's sorted prefix */
 };
 int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* size_out);
 
@@ -240,8 +246,9 @@ int64_t gs_ctx_launch_count(gs_ctx* ctx);
  * out[0] (pixel, splat) pairs evaluated by the forward blend, out[1] pairs
  * blended, out[2] pairs evaluated by the backward blend, out[3] pairs that
  * contributed gradients in the backward, out[4] sorted-list entries read by
- * the forward blend, out[5] sorted-list entries read by the backward blend. */
-int gs_frames_counters(gs_frames* fr, int64_t out[6]);
+ * the forward blend, out[5] sorted-list entries read by the backward blend,
+ * out[6] list entries the forward sorted (all keys with GS_F_FULL_SORT). */
+int gs_frames_counters(gs_frames* fr, int64_t out[7]);
 
 /* D-SSIM loss term and its image gradient for ONE view, allocating nothing.
  * (The paper has no counterpart: this is a deployment variant of the D-SSIM

@@ -16,10 +16,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libgsplat.so")
 
 GS_OK, GS_PENDING = 0, 1
 GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3, -4, -5, -6
-GS_F_NO_SYNC, GS_F_HOST_IO = 1, 2
+GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT = 1, 2, 4
 GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM = 0, 1, 2
 (GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
- GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT) = range(10)
+ GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT) = range(11)
 
 # names declared in include/gsplat.h (checked by the CPU test suite)
 EXPORTED = (
@@ -258,7 +258,8 @@ def gs_frames_query(fr: int, what: int):
     _ck(L.gs_frames_query(C.c_void_p(fr), int(what), None, 0, C.byref(size)))
     dtype = {GS_Q_NUM_KEYS: np.int64, GS_Q_DEPTH: np.float32, GS_Q_RECT: np.int32, GS_Q_RADIUS: np.int32,
              GS_Q_TILE_RANGES: np.uint32, GS_Q_SORTED_IDX: np.uint32, GS_Q_T_FINAL: np.float32,
-             GS_Q_N_CONTRIB: np.uint32, GS_Q_MEAN2D: np.float32, GS_Q_SPLAT: np.float32}[what]
+             GS_Q_N_CONTRIB: np.uint32, GS_Q_MEAN2D: np.float32, GS_Q_SPLAT: np.float32,
+             GS_Q_SORTED_COUNT: np.uint32}[what]
     out = np.zeros(max(1, size.value // np.dtype(dtype).itemsize), dtype)
     _ck(L.gs_frames_query(C.c_void_p(fr), int(what), out.ctypes.data_as(C.c_void_p), out.nbytes, None))
     return out[: size.value // np.dtype(dtype).itemsize]
@@ -285,7 +286,7 @@ def gs_ctx_launch_count(ctx: int) -> int:
 
 
 def gs_frames_counters(fr: int):
-    out = (C.c_int64 * 6)()
+    out = (C.c_int64 * 7)()
     _ck(load().gs_frames_counters(C.c_void_p(fr), out))
     return [int(x) for x in out]
 

@@ -186,7 +186,8 @@ struct gs_frames {
     DevBuf<uint2> rect;
     DevBuf<int> radius;
     // per tile
-    DevBuf<uint32_t> counts, starts, cursor, scan_tmp, sort_lists, sort_counters;
+    DevBuf<uint32_t> counts, starts, cursor, scan_tmp, sort_lists, sort_counters, sorted_count;
+    bool full_sort = false;           // the last forward sorted whole lists
     DevBuf<float> tile_loss;
     // per key
     DevBuf<unsigned long long> keys, tmp_keys;
@@ -220,7 +221,7 @@ struct gs_frames {
         DevBuf<float>* f1[] = {&Cb, &depth, &gC, &tile_loss, &T_final, &dldc_ssim, &ssim_tmp};
         for (auto* b : f1) b->release();
         rect.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
-        sort_lists.release(); sort_counters.release();
+        sort_lists.release(); sort_counters.release(); sorted_count.release();
         keys.release(); tmp_keys.release(); sorted_idx.release(); n_contrib.release(); pose_partials.release();
         loss_tmp.release(); counters.release();
         st_params.release(); st_target.release(); st_image.release(); st_grads.release();
@@ -357,7 +358,8 @@ static int ensure_tile_buffers(gs_frames* fr, size_t tiles, bool grow) {
         (rc = fr->cursor.ensure(tiles + 1, grow, "tile cursor")) || (rc = fr->tile_loss.ensure(tiles + 1, grow, "tile loss")) ||
         (rc = fr->scan_tmp.ensure(gs::scan_tmp_bytes((int)tiles + 1) / 4 + 1, grow, "scan tmp")) ||
         (rc = fr->sort_lists.ensure(3 * (tiles + 1), grow, "sort lists")) ||
-        (rc = fr->sort_counters.ensure(8, grow, "sort counters")))
+        (rc = fr->sort_counters.ensure(8, grow, "sort counters")) ||
+        (rc = fr->sorted_count.ensure(tiles + 1, grow, "sorted count")))
         return rc;
     return GS_OK;
 }
@@ -587,19 +589,28 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
         gs::launch_scatter_keys(n, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p, fr->keys.p, cap, ctx->status, s);
     }
     CK_LAUNCH();
-    {
-        PROF(PK_SORT, 4);
-        gs::launch_segment_sort(T, fr->starts.p, fr->keys.p, fr->tmp_keys.p, fr->sorted_idx.p, cap, fr->sort_lists.p,
-                                fr->sort_counters.p, s);
-    }
-    CK_LAUNCH();
-    {
+    fr->full_sort = (opts->flags & GS_F_FULL_SORT) != 0;
+    if (fr->full_sort) {
+        {
+            PROF(PK_SORT, 4);
+            gs::launch_segment_sort(T, fr->starts.p, fr->keys.p, fr->tmp_keys.p, fr->sorted_idx.p, cap,
+                                    fr->sort_lists.p, fr->sort_counters.p, s);
+        }
+        CK_LAUNCH();
+        {
+            PROF(PK_BLEND_FWD, 1);
+            gs::launch_blend_fwd(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->sorted_idx.p,
+                                 cap, image, fr->T_final.p, fr->n_contrib.p, target,
+                                 target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
+        }
+        CK_LAUNCH();
+    } else {
         PROF(PK_BLEND_FWD, 1);
-        gs::launch_blend_fwd(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->sorted_idx.p, cap,
-                             image, fr->T_final.p, fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr,
-                             fr->counters.p, s);
+        gs::launch_blend_fwd_lazy(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
+                                  fr->tmp_keys.p, fr->sorted_idx.p, fr->sorted_count.p, cap, image, fr->T_final.p,
+                                  fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
+        CK_LAUNCH();
     }
-    CK_LAUNCH();
     if (target && loss_out) {
         PROF(PK_LOSS, 1);
         gs::launch_loss_finalize(n_views, fr->vdev.p, fr->tile_loss.p, 1.0, nullptr, loss_out, s);
@@ -871,9 +882,9 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 
 int64_t gs_ctx_launch_count(gs_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
-int gs_frames_counters(gs_frames* fr, int64_t out[6]) {
+int gs_frames_counters(gs_frames* fr, int64_t out[7]) {
     if (!fr || !out) return fail(GS_EINVAL, "NULL argument");
-    for (int k = 0; k < 6; k++) out[k] = 0;
+    for (int k = 0; k < 7; k++) out[k] = 0;
     if (!fr->counters.p) return GS_OK;
     CK(cudaSetDevice(fr->ctx->device));
     unsigned long long c[8];
@@ -881,6 +892,7 @@ int gs_frames_counters(gs_frames* fr, int64_t out[6]) {
     for (int k = 0; k < 4; k++) out[k] = (int64_t)c[k];
     out[4] = (int64_t)c[4];
     out[5] = (int64_t)c[6];
+    out[6] = fr->full_sort ? (int64_t)fr->n_keys : (int64_t)c[5];
     return GS_OK;
 }
 
@@ -902,6 +914,7 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         case GS_Q_N_CONTRIB: need = (size_t)fr->total_pixels * sizeof(uint32_t); break;
         case GS_Q_MEAN2D: need = vn * 2 * sizeof(float); break;
         case GS_Q_SPLAT: need = vn * 9 * sizeof(float); break;
+        case GS_Q_SORTED_COUNT: need = (size_t)fr->total_tiles * sizeof(uint32_t); break;
         default: return fail(GS_EINVAL, "unknown query %d", what);
     }
     if (size_out) *size_out = need;
@@ -923,6 +936,17 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         CK(cudaMemcpy(&K, fr->starts.p + fr->total_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost));
         const size_t nb = std::min<size_t>((size_t)K * 4, need);
         if (nb) CK(cudaMemcpy(dst, fr->sorted_idx.p, nb, cudaMemcpyDeviceToHost));
+        return GS_OK;
+    }
+    if (what == GS_Q_SORTED_COUNT) {
+        std::vector<uint32_t> st(fr->total_tiles + 1);
+        CK(cudaMemcpy(st.data(), fr->starts.p, st.size() * 4, cudaMemcpyDeviceToHost));
+        uint32_t* o = static_cast<uint32_t*>(dst);
+        if (fr->full_sort) {
+            for (int t = 0; t < fr->total_tiles; t++) o[t] = st[t + 1] - st[t];
+        } else if (fr->total_tiles) {
+            CK(cudaMemcpy(o, fr->sorted_count.p, need, cudaMemcpyDeviceToHost));
+        }
         return GS_OK;
     }
     if (what == GS_Q_TILE_RANGES) {

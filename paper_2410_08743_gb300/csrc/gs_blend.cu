@@ -11,6 +11,7 @@
 // splat's nine 2D gradients over the warp before one vector atomic per warp.
 #include <cuda_runtime.h>
 
+#include "gs_block_sort.cuh"
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -159,6 +160,259 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
         }
         if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cbl); }
     }
+}
+
+// ------------------------------------------------------------ forward with lazy tile sort
+// The forward blend usually stops long before the end of a tile's list (every
+// pixel saturates), so the tile's keys are sorted only as far as they are
+// consumed.  A list of at most LZ_CAP keys is sorted whole in shared memory.
+// A longer list is bucketed by depth (LZ_NB buckets spanning the tile's depth
+// range; bucket order is depth order and equal depths share a bucket), then
+// runs of consecutive buckets of at most LZ_CAP keys are sorted and blended one
+// after another until every pixel has stopped.  The concatenation of the
+// sorted runs is exactly the (depth, index) order, so the image equals the one
+// of a fully sorted list.  The sorted prefix and its length go to sorted_idx /
+// sorted_count for the backward pass, which never reads past it.
+#define LZ_CAP 2048
+#define LZ_NB 1024
+#define LZ_T GS_TILE_PIX
+
+struct LazySmem {
+    union {
+        struct {
+            unsigned long long b0[LZ_CAP];
+            unsigned long long b1[LZ_CAP];
+        } srt;
+        SplatBatch sb;  // blending reuses the sort buffers
+    } u;
+    uint32_t hist[(LZ_T / 32) * 256];  // radix histograms, then bucket cursors
+    uint32_t bstart[LZ_NB + 1];
+};
+
+__global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
+                                                         const ViewDev* __restrict__ views, RenderParams rp,
+                                                         SplatArrays sp, int n, const uint32_t* __restrict__ starts,
+                                                         unsigned long long* __restrict__ keys,
+                                                         unsigned long long* __restrict__ tmp,
+                                                         uint32_t* __restrict__ sorted_idx,
+                                                         uint32_t* __restrict__ sorted_count, uint32_t cap,
+                                                         float* __restrict__ image, float* __restrict__ T_final,
+                                                         uint32_t* __restrict__ n_contrib,
+                                                         const float* __restrict__ target,
+                                                         float* __restrict__ tile_loss,
+                                                         unsigned long long* __restrict__ counters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LazySmem& sm = *reinterpret_cast<LazySmem*>(smem_raw);
+    __shared__ float s_red[LZ_T / 32];
+    __shared__ uint32_t s_warp[LZ_T / 32];
+    __shared__ uint32_t s_mm[2];
+    const int t = blockIdx.x;
+    const int v = view_of_tile(tile_base, n_views, t);
+    const ViewDev& vd = views[v];
+    const int W = vd.W, H = vd.H, gw = vd.gw;
+    const int lt = t - vd.tile_base;
+    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
+    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const bool inside = px < W && py < H;
+    const float fpx = (float)px, fpy = (float)py;
+    uint32_t s = starts[t], e = starts[t + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    const uint32_t n_list = e - s;
+    const size_t vbase = (size_t)v * n;
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0, n_eval = 0, n_blend = 0, n_read = 0;
+    bool done = !inside;
+    uint32_t n_sorted = 0;
+
+    // Blends list positions [p0, p1) read from sorted_idx; returns true when
+    // every pixel of the tile has stopped.
+    auto blend_range = [&](uint32_t p0, uint32_t p1) -> bool {
+        for (uint32_t base = p0; base < p1; base += BATCH) {
+            if (__syncthreads_count(done) == LZ_T) return true;
+            const uint32_t j = base + threadIdx.x;
+            n_read += (threadIdx.x == 0) ? min((uint32_t)BATCH, p1 - base) : 0u;
+            if (j < p1) {
+                const size_t k = vbase + sorted_idx[s + j];
+                const float4 a = sp.A[k], b = sp.B[k];
+                sm.u.sb.A[threadIdx.x] = a;
+                sm.u.sb.B[threadIdx.x] = b;
+                sm.u.sb.Cb[threadIdx.x] = sp.Cb[k];
+                sm.u.sb.H[threadIdx.x] = alpha_box(a, b, rp.alpha_min);
+            }
+            __syncthreads();
+            const int cnt = (int)min((uint32_t)BATCH, p1 - base);
+            if (!done) {
+                for (int jj = 0; jj < cnt; jj++) {
+                    const float4 a = sm.u.sb.A[jj];
+                    const float2 h = sm.u.sb.H[jj];
+                    n_eval++;
+                    const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
+                    if (fabsf(dx) > h.x || fabsf(dy) > h.y) continue;
+                    const float4 b = sm.u.sb.B[jj];
+                    float G, alpha;
+                    bool cl;
+                    if (!pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
+                    const float Tn = T * (1.0f - alpha);
+                    if (Tn < rp.t_min) { done = true; break; }
+                    n_blend++;
+                    const float w = alpha * T;
+                    C0 = fmaf(b.z, w, C0);
+                    C1 = fmaf(b.w, w, C1);
+                    C2 = fmaf(sm.u.sb.Cb[jj], w, C2);
+                    T = Tn;
+                    last = base + jj + 1;
+                }
+            }
+        }
+        return __syncthreads_count(done) == LZ_T;
+    };
+    // Sorts list positions [c0, c0 + m) found in src (shared b0 or global) and
+    // writes their indices to sorted_idx.
+    auto sort_write = [&](unsigned long long* src, unsigned long long* scratch, uint32_t c0, int m) {
+        unsigned long long* r = sort_tile_keys<LZ_T>(src, scratch, m, sm.hist);
+        for (int j = threadIdx.x; j < m; j += LZ_T) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
+        __syncthreads();
+    };
+
+    if (n_list <= LZ_CAP) {
+        for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) sm.u.srt.b0[j] = keys[s + j];
+        __syncthreads();
+        if (n_list > 0) sort_write(sm.u.srt.b0, sm.u.srt.b1, 0, (int)n_list);
+        n_sorted = n_list;
+        blend_range(0, n_list);
+    } else {
+        // depth range of the tile
+        uint32_t lo = 0xffffffffu, hi = 0u;
+        for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+            const uint32_t d = (uint32_t)(keys[s + j] >> 32);
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (threadIdx.x == 0) { s_mm[0] = 0xffffffffu; s_mm[1] = 0u; }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { atomicMin(&s_mm[0], lo); atomicMax(&s_mm[1], hi); }
+        __syncthreads();
+        lo = s_mm[0];
+        hi = s_mm[1];
+        if (lo == hi) {
+            // one depth for the whole list: index order, sorted in global memory
+            sort_write(keys + s, tmp + s, 0, (int)n_list);
+            n_sorted = n_list;
+            blend_range(0, n_list);
+        } else {
+            const int bits = 32 - __clz(hi - lo);
+            const int shift = bits > 10 ? bits - 10 : 0;
+            for (int b = threadIdx.x; b <= LZ_NB; b += LZ_T) sm.bstart[b] = 0u;
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T)
+                atomicAdd(&sm.bstart[((uint32_t)(keys[s + j] >> 32) - lo) >> shift], 1u);
+            __syncthreads();
+            {
+                uint32_t c[LZ_NB / LZ_T], sum = 0;
+#pragma unroll
+                for (int k = 0; k < LZ_NB / LZ_T; k++) { c[k] = sm.bstart[threadIdx.x * (LZ_NB / LZ_T) + k]; sum += c[k]; }
+                uint32_t off = block_scan_excl<LZ_T>(sum, s_warp);
+#pragma unroll
+                for (int k = 0; k < LZ_NB / LZ_T; k++) {
+                    const int b = threadIdx.x * (LZ_NB / LZ_T) + k;
+                    sm.bstart[b] = off;
+                    sm.hist[b] = off;
+                    off += c[k];
+                }
+                if (threadIdx.x == 0) sm.bstart[LZ_NB] = n_list;
+            }
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+                const unsigned long long x = keys[s + j];
+                const uint32_t pos = atomicAdd(&sm.hist[((uint32_t)(x >> 32) - lo) >> shift], 1u);
+                tmp[s + pos] = x;
+            }
+            __syncthreads();
+            int cb = 0;
+            while (cb < LZ_NB) {
+                const uint32_t c0 = sm.bstart[cb];
+                if (c0 >= n_list) break;
+                int cb1 = cb + 1;
+                while (cb1 < LZ_NB && sm.bstart[cb1 + 1] - c0 <= (uint32_t)LZ_CAP) cb1++;
+                const int m = (int)(sm.bstart[cb1] - c0);
+                if (m > LZ_CAP) {
+                    sort_write(tmp + s + c0, keys + s + c0, c0, m);  // one oversized bucket
+                } else {
+                    for (int j = threadIdx.x; j < m; j += LZ_T) sm.u.srt.b0[j] = tmp[s + c0 + j];
+                    __syncthreads();
+                    sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
+                }
+                n_sorted = c0 + (uint32_t)m;
+                if (blend_range(c0, c0 + (uint32_t)m)) break;
+                cb = cb1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) sorted_count[t] = n_sorted;
+    float l1 = 0.0f;
+    if (inside) {
+        const size_t p = (size_t)py * W + px;
+        const size_t np = (size_t)W * H;
+        float* img = image + vd.img_off;
+        C0 = fmaf(T, rp.bg[0], C0);
+        C1 = fmaf(T, rp.bg[1], C1);
+        C2 = fmaf(T, rp.bg[2], C2);
+        img[p] = C0;
+        img[np + p] = C1;
+        img[2 * np + p] = C2;
+        T_final[vd.pix_off + p] = T;
+        n_contrib[vd.pix_off + p] = last;
+        if (target) {
+            const float* tg = target + vd.img_off;
+            l1 = fabsf(C0 - tg[p]) + fabsf(C1 - tg[np + p]) + fabsf(C2 - tg[2 * np + p]);
+        }
+    }
+    if (target) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = l1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < LZ_T / 32; w++) acc += s_red[w];
+            tile_loss[t] = acc;
+        }
+    }
+    if (counters) {
+        unsigned long long ce = n_eval, cbl = n_blend;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ce += __shfl_xor_sync(0xffffffffu, ce, o);
+            cbl += __shfl_xor_sync(0xffffffffu, cbl, o);
+        }
+        if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cbl); }
+        if (threadIdx.x == 0) {
+            atomicAdd(counters + 4, (unsigned long long)n_read);
+            atomicAdd(counters + 5, (unsigned long long)n_sorted);
+        }
+    }
+}
+
+void launch_blend_fwd_lazy(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+                           const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+                           unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
+                           uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
+                           const float* target, float* tile_loss, unsigned long long* counters, cudaStream_t s) {
+    if (n_tiles <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_blend_fwd_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LazySmem));
+        attr = true;
+    }
+    k_blend_fwd_lazy<<<n_tiles, LZ_T, sizeof(LazySmem), s>>>(n_views, tile_base, views, rp, sp, n, starts, keys, tmp,
+                                                             sorted_idx, sorted_count, cap, image, T_final, n_contrib,
+                                                             target, tile_loss, counters);
 }
 
 void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,

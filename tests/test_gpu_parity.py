@@ -75,10 +75,15 @@ CASES = {
 GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium"]
 
 
+@pytest.mark.parametrize("full", [True, False], ids=["full_sort", "lazy_sort"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_keys_bit_exact(R, case):
+def test_keys_bit_exact(R, case, full):
     sc, views, poses = CASES[case]()
-    gpu_forward(R, sc, views, poses)
+    R.opts.flags = L.GS_F_FULL_SORT if full else 0
+    try:
+        gpu_forward(R, sc, views, poses)
+    finally:
+        R.opts.flags = 0
     k = oracle.keys(sc, views, poses)
     valid = k["valid"].astype(bool)
     rect = R.query(L.GS_Q_RECT).reshape(-1, 4)
@@ -89,13 +94,52 @@ def test_keys_bit_exact(R, case):
     m2 = R.query(L.GS_Q_MEAN2D).reshape(-1, 2)
     assert np.array_equal(m2[valid].view(np.uint32), k["mu2f"][valid].view(np.uint32))
     assert int(R.query(L.GS_Q_NUM_KEYS)[0]) == k["n_keys"]
-    assert np.array_equal(R.query(L.GS_Q_TILE_RANGES).reshape(-1, 2), k["ranges"])
-    assert np.array_equal(R.query(L.GS_Q_SORTED_IDX), k["idx"]), "sorted tile lists differ"
+    ranges = R.query(L.GS_Q_TILE_RANGES).reshape(-1, 2)
+    assert np.array_equal(ranges, k["ranges"])
+    got = R.query(L.GS_Q_SORTED_IDX)
+    cnt = R.query(L.GS_Q_SORTED_COUNT)
     lens = k["ranges"][:, 1] - k["ranges"][:, 0]
+    if full:
+        assert np.array_equal(cnt, lens)
+        assert np.array_equal(got, k["idx"]), "sorted tile lists differ"
+    else:
+        # every tile's sorted prefix is the oracle's prefix, and covers what
+        # the blend consumed (the longest n_contrib of the tile's pixels)
+        assert np.all(cnt <= lens)
+        for t in np.nonzero(cnt)[0]:
+            s0 = k["ranges"][t, 0]
+            assert np.array_equal(got[s0:s0 + cnt[t]], k["idx"][s0:s0 + cnt[t]]), t
+        nc = R.query(L.GS_Q_N_CONTRIB)
+        off = 0; tb = 0
+        for v in views:
+            W, H = v["width"], v["height"]
+            gw, gh = (W + 15) // 16, (H + 15) // 16
+            ncv = nc[off:off + W * H].reshape(H, W)
+            for ty in range(gh):
+                for tx in range(gw):
+                    tile_max = ncv[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].max()
+                    assert cnt[tb + ty * gw + tx] >= tile_max
+            off += W * H; tb += gw * gh
     if case == "dense_medium":
         assert lens.max() > 2048          # medium path exercised
     if case in ("dense_large", "same_depth"):
         assert lens.max() > 12288         # MSD-split path exercised
+
+
+@pytest.mark.parametrize("case", ["ragged_sh3", "dense_large", "same_depth"])
+def test_lazy_sort_equals_full_sort(R, case):
+    """Sorting tiles only as far as they are consumed changes nothing."""
+    sc, views, poses = CASES[case]()
+    outs = []
+    for flags in (L.GS_F_FULL_SORT, 0):
+        R.opts.flags = flags
+        try:
+            _, _, img, _, _ = gpu_forward(R, sc, views, poses)
+        finally:
+            R.opts.flags = 0
+        outs.append((img.cpu().numpy(), R.query(L.GS_Q_T_FINAL), R.query(L.GS_Q_N_CONTRIB)))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("case", list(CASES))
