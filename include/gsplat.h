@@ -243,8 +243,9 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 int64_t gs_ctx_launch_count(gs_ctx* ctx);
 
 /* Work counters of the last forward/backward of `fr` (synchronous):
- * out[0] (pixel, splat) pairs evaluated by the forward blend, out[1] pairs
- * blended, out[2] pairs evaluated by the backward blend, out[3] pairs that
+ * out[0] (pixel, splat) pairs whose alpha the forward blend evaluated (pairs
+ * inside the splat's alpha box), out[1] pairs blended, out[2] pairs whose
+ * alpha the backward blend evaluated, out[3] pairs that
  * contributed gradients in the backward, out[4] sorted-list entries read by
  * the forward blend, out[5] sorted-list entries read by the backward blend,
  * out[6] list entries the forward sorted (all keys with GS_F_FULL_SORT). */

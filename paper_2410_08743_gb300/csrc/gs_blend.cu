@@ -41,6 +41,32 @@ __device__ __forceinline__ float2 alpha_box(const float4 a, const float4 b, floa
     return make_float2(fmaf(hx, 1.01f, 0.01f), fmaf(hy, 1.01f, 0.01f));
 }
 
+// Per-warp compaction of a staged batch: the entries (in order) whose alpha
+// box can touch a pixel of this warp's 16x2 footprint (x in [fx0, fx0+15],
+// y in [fy0, fy0+1]).  The test is conservative (0.01 px slack over the
+// per-pixel box test), so skipping the other entries changes no decision.
+// Returns the number of entries written to wl.
+__device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float fx0, float fy0,
+                                            unsigned char* wl) {
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    for (int r = 0; r < cnt; r += 32) {
+        const int e = r + lane;
+        bool hit = false;
+        if (e < cnt) {
+            const float4 a = sb.A[e];
+            const float2 h = sb.H[e];
+            hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx0 + (GS_TILE - 1)) &&
+                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy0 + 1.0f);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) wl[n + __popc(m & ((1u << lane) - 1u))] = (unsigned char)e;
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
 // alpha of one (pixel, splat) pair with a fixed operation sequence, so that
 // the forward and the backward take the same skip decisions.
 //   power = -1/2 (a dx^2 + c dy^2) - b dx dy with d = p - mu_hat (Eq. 3)
@@ -187,6 +213,7 @@ struct LazySmem {
     } u;
     uint32_t hist[(LZ_T / 32) * 256];  // radix histograms, then bucket cursors
     uint32_t bstart[LZ_NB + 1];
+    unsigned char wl[LZ_T / 32][BATCH];  // per-warp compacted batch entries
 };
 
 __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
@@ -242,13 +269,17 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             }
             __syncthreads();
             const int cnt = (int)min((uint32_t)BATCH, p1 - base);
+            unsigned char* wl = sm.wl[threadIdx.x >> 5];
+            const int nw = warp_compact(sm.u.sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
+                                        (float)((lt / gw) * GS_TILE + 2 * ((threadIdx.x >> 5))), wl);
             if (!done) {
-                for (int jj = 0; jj < cnt; jj++) {
+                for (int q = 0; q < nw; q++) {
+                    const int jj = wl[q];
                     const float4 a = sm.u.sb.A[jj];
                     const float2 h = sm.u.sb.H[jj];
-                    n_eval++;
                     const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
                     if (fabsf(dx) > h.x || fabsf(dy) > h.y) continue;
+                    n_eval++;
                     const float4 b = sm.u.sb.B[jj];
                     float G, alpha;
                     bool cl;
@@ -471,6 +502,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
     __shared__ uint32_t s_idx[BATCH];
     __shared__ uint32_t s_max[GS_TILE_PIX / 32];
     __shared__ float s_acc[BATCH * 9];
+    __shared__ unsigned char s_wl[GS_TILE_PIX / 32][BATCH];
     const int t = blockIdx.x;
     const int v = view_of_tile(tile_base, n_views, t);
     const ViewDev& vd = views[v];
@@ -553,14 +585,18 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
         }
         for (int q = threadIdx.x; q < BATCH * 9; q += GS_TILE_PIX) s_acc[q] = 0.0f;
         __syncthreads();
-        for (int jj = cnt - 1; jj >= 0; jj--) {
+        unsigned char* wl = s_wl[threadIdx.x >> 5];
+        const int nw = warp_compact(sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
+                                    (float)((lt / gw) * GS_TILE + 2 * (threadIdx.x >> 5)), wl);
+        for (int q = nw - 1; q >= 0; q--) {
+            const int jj = wl[q];
             const uint32_t pos = (uint32_t)(bstart + jj);
             const float4 a = sb.A[jj];
             const float2 h = sb.H[jj];
             bool use = inside && any_grad && pos < last;
-            n_eval += use;
             const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
             use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
+            n_eval += use;
             if (!__any_sync(0xffffffffu, use)) continue;
             const float4 b = sb.B[jj];
             float G = 0.f, alpha = 0.f;
@@ -573,11 +609,11 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
             for (int c = 0; c < 8; c++) r[c] = 0.0f;
             if (use) {
                 const float cb = sb.Cb[jj];
-                const float om = 1.0f - alpha;
-                const float Ti = T / om;
+                const float inv_om = __fdividef(1.0f, 1.0f - alpha);
+                const float Ti = T * inv_om;
                 const float wgt = alpha * Ti;
                 r[6] = wgt * g0; r[7] = wgt * g1; r8 = wgt * g2;
-                const float dLda = Ti * (b.z * g0 + b.w * g1 + cb * g2) - (S0 * g0 + S1 * g1 + S2 * g2) / om;
+                const float dLda = Ti * (b.z * g0 + b.w * g1 + cb * g2) - (S0 * g0 + S1 * g1 + S2 * g2) * inv_om;
                 S0 = fmaf(b.z, wgt, S0); S1 = fmaf(b.w, wgt, S1); S2 = fmaf(cb, wgt, S2);
                 T = Ti;
                 if (!cl) {

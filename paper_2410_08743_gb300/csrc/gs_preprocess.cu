@@ -345,13 +345,15 @@ void launch_preprocess_fwd(const SceneDev& sc, int n_views, const ViewDev* views
 //   colour -> SH coefficients and viewing direction -> mu
 //   pose: rho += g_mu_c + R_c g_mu(SH);  phi += mu_c x g_mu_c + 2 w(Sigma_c G_Sigma_c)
 template <int D>
-__global__ void __launch_bounds__(256) k_preprocess_bwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
+__global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
                                                         RenderParams rp, SplatArrays sp, Grad2DArrays g2d,
                                                         gs_grads grads, double* __restrict__ pose_partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ViewDev* sv = reinterpret_cast<ViewDev*>(smem_raw);
     const int nwarps = blockDim.x >> 5;
     double* spose = reinterpret_cast<double*>(smem_raw + ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15));
+    // SH-coefficient gradient accumulators of every thread, [coefficient][thread]
+    float* sgf = reinterpret_cast<float*>(spose + (size_t)nwarps * n_views * 6);
     {
         const int words = n_views * (int)(sizeof(ViewDev) / 4);
         const int* src = reinterpret_cast<const int*>(views);
@@ -399,9 +401,8 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(SceneDev sc, int n_views
 #pragma unroll
     for (int k = 0; k < 9; k++) gSig[k] = 0.0f;
     float gop = 0.0f;
-    float gf[NC * 3];
 #pragma unroll
-    for (int k = 0; k < NC * 3; k++) gf[k] = 0.0f;
+    for (int k = 0; k < NC * 3; k++) sgf[k * blockDim.x + threadIdx.x] = 0.0f;
 
     for (int v = 0; v < n_views; v++) {
         const ViewDev& vd = sv[v];
@@ -513,7 +514,10 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(SceneDev sc, int n_views
                 for (int b = 0; b < NC; b++) raw = fmaf(f[b * 3 + ch], Y[b], raw);
                 const float gch = raw < 0.0f ? 0.0f : gcol[ch];
 #pragma unroll
-                for (int b = 0; b < NC; b++) { gf[b * 3 + ch] += Y[b] * gch; wsum[b] += f[b * 3 + ch] * gch; }
+                for (int b = 0; b < NC; b++) {
+                    sgf[(b * 3 + ch) * blockDim.x + threadIdx.x] += Y[b] * gch;
+                    wsum[b] += f[b * 3 + ch] * gch;
+                }
             }
             float gd[3];
             sh_grad<D>(dx, dy, dz, wsum, gd);
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(SceneDev sc, int n_views
         if (grads.sh) {
             float* gsp = grads.sh + (size_t)i * 48;
 #pragma unroll
-            for (int kk = 0; kk < NC * 3; kk++) gsp[kk] += gf[kk];
+            for (int kk = 0; kk < NC * 3; kk++) gsp[kk] += sgf[kk * blockDim.x + threadIdx.x];
         }
     }
     __syncthreads();
@@ -611,7 +615,18 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
                            cudaStream_t s) {
     if (sc.n <= 0 || n_views <= 0) return;
     const int T = 256;
-    const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6;
+    const int nc3 = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
+    const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6 +
+                      sizeof(float) * nc3 * T;
+    static bool attr = false;
+    if (!attr) {
+        const int mx = 200 * 1024;
+        cudaFuncSetAttribute(k_preprocess_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr = true;
+    }
     switch (sc.sh_degree) {
         case 0: k_preprocess_bwd<0><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;
         case 1: k_preprocess_bwd<1><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;

@@ -120,6 +120,30 @@ __device__ __forceinline__ void rect_of(const uint2 r, int& x0, int& y0, int& x1
     x0 = r.x & 0xffff; y0 = r.x >> 16; x1 = r.y & 0xffff; y1 = r.y >> 16;
 }
 
+// Rectangles of four chunk entries per thread are loaded before any of them
+// is used, so that the loads overlap.
+#define CS_PREFETCH 4
+
+// Adds every key of this thread's entries of [i0, i1) to the shared histogram.
+__device__ __forceinline__ void chunk_histogram(const uint2* __restrict__ rect, size_t vb, int i0, int i1, int gw,
+                                                uint32_t* hist) {
+    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS * CS_PREFETCH) {
+        uint2 r[CS_PREFETCH];
+#pragma unroll
+        for (int u = 0; u < CS_PREFETCH; u++) {
+            const int iu = i + u * CS_THREADS;
+            r[u] = iu < i1 ? rect[vb + iu] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < CS_PREFETCH; u++) {
+            int x0, y0, x1, y1;
+            rect_of(r[u], x0, y0, x1, y1);
+            for (int ty = y0; ty < y1; ty++)
+                for (int tx = x0; tx < x1; tx++) atomicAdd(hist + ty * gw + tx, 1u);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, const ViewDev* __restrict__ views,
                                                            const uint2* __restrict__ rect,
                                                            uint32_t* __restrict__ tile_counts) {
@@ -139,12 +163,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, const ViewDev
     }
     for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
     __syncthreads();
-    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
-        int x0, y0, x1, y1;
-        rect_of(rect[vb + i], x0, y0, x1, y1);
-        for (int ty = y0; ty < y1; ty++)
-            for (int tx = x0; tx < x1; tx++) atomicAdd(hist + ty * gw + tx, 1u);
-    }
+    chunk_histogram(rect, vb, i0, i1, gw, hist);
     __syncthreads();
     for (int t = threadIdx.x; t < ntile; t += CS_THREADS)
         if (hist[t]) atomicAdd(tile_counts + tb + t, hist[t]);
@@ -184,12 +203,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewD
     }
     for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
     __syncthreads();
-    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
-        int x0, y0, x1, y1;
-        rect_of(rect[vb + i], x0, y0, x1, y1);
-        for (int ty = y0; ty < y1; ty++)
-            for (int tx = x0; tx < x1; tx++) atomicAdd(hist + ty * gw + tx, 1u);
-    }
+    chunk_histogram(rect, vb, i0, i1, gw, hist);
     __syncthreads();
     // reserve this CTA's range in every touched tile
     for (int t = threadIdx.x; t < ntile; t += CS_THREADS) {
@@ -197,16 +211,27 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewD
         if (c) hist[t] = starts[tb + t] + atomicAdd(cursor + tb + t, c);
     }
     __syncthreads();
-    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
-        int x0, y0, x1, y1;
-        rect_of(rect[vb + i], x0, y0, x1, y1);
-        if (x1 <= x0) continue;
-        const unsigned long long key = ((unsigned long long)__float_as_uint(depth[vb + i]) << 32) | (uint32_t)i;
-        for (int ty = y0; ty < y1; ty++)
-            for (int tx = x0; tx < x1; tx++) {
-                const uint32_t pos = atomicAdd(hist + ty * gw + tx, 1u);
-                if (pos < cap) keys[pos] = key; else s_over = 1;
-            }
+    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS * CS_PREFETCH) {
+        uint2 r[CS_PREFETCH];
+        float dz[CS_PREFETCH];
+#pragma unroll
+        for (int u = 0; u < CS_PREFETCH; u++) {
+            const int iu = i + u * CS_THREADS;
+            r[u] = iu < i1 ? rect[vb + iu] : make_uint2(0u, 0u);
+            dz[u] = iu < i1 ? depth[vb + iu] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < CS_PREFETCH; u++) {
+            int x0, y0, x1, y1;
+            rect_of(r[u], x0, y0, x1, y1);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(dz[u]) << 32) | (uint32_t)(i + u * CS_THREADS);
+            for (int ty = y0; ty < y1; ty++)
+                for (int tx = x0; tx < x1; tx++) {
+                    const uint32_t pos = atomicAdd(hist + ty * gw + tx, 1u);
+                    if (pos < cap) keys[pos] = key; else s_over = 1;
+                }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
