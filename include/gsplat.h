@@ -207,6 +207,95 @@ int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* adam_m, double
                  const double* pose_grad, double lr, double beta1, double beta2, double eps,
                  int step, void* stream);
 
+/* Raw (unactivated) Gaussian parameters optimised in joint refinement
+ * (device; layouts as the scene's, log-scales and logit-opacities in place of
+ * the activated values). */
+typedef struct {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* logit_opacities;
+    float* sh;
+} gs_raw_params;
+
+/* Per-group Adam learning rates (sh_dc for the degree-0 coefficients,
+ * sh_rest for the others). */
+typedef struct {
+    float means, scales, quats, opacities, sh_dc, sh_rest;
+} gs_gaussian_lrs;
+
+/* One Adam step on the raw Gaussian parameters (joint reconstruction and pose
+ * refinement, Sec. 3.3).  `grads` are the renderer's gradients w.r.t. the
+ * ACTIVATED scales and opacities; the step chains them through s = exp(log s)
+ * and o = sigmoid(logit o), updates `raw` in place and writes the activated
+ * scales_out [n][3] and opacities_out [n] that the next render reads.
+ * adam_m, adam_v: device float [59 n] each, groups at offsets means 0,
+ * log-scales 3n, quats 6n, opacities 10n, sh 11n.  step is 1-based.  SH
+ * coefficients above sh_degree are left untouched. */
+int gs_gaussian_adam(gs_ctx* ctx, int64_t n, int sh_degree, gs_raw_params* raw, float* scales_out,
+                     float* opacities_out, const gs_grads* grads, float* adam_m, float* adam_v,
+                     const gs_gaussian_lrs* lrs, float beta1, float beta2, float eps, int step, void* stream);
+
+/* ------------------------------------------------------------ pose serving
+ * A request loop of 6-DoF pose-estimation solves against a device-resident
+ * scene (Sec. 3.4 / Sec. 4.2: estimate the camera pose of a query image from a
+ * trained model by gradient descent on the photometric L1 loss).  Continuous
+ * batching: a worker thread admits queued requests into free slots as slots
+ * and memory allow, and each iteration runs ONE batched forward + L1 +
+ * pose-only backward + Adam step over every active solve, so solves that
+ * arrive while others run share the device.  Each solve's result depends only
+ * on its own view (equal alone and in the mix up to FP32 summation order). */
+typedef struct gs_server gs_server;
+
+typedef struct {
+    int32_t max_slots;        /* solves batched per iteration (1 = one solve at a time) */
+    int32_t max_width;        /* largest accepted query image */
+    int32_t max_height;
+    int64_t mem_budget;       /* device bytes the active solves' working set may use (0: no limit) */
+    int32_t queue_capacity;   /* pending requests beyond which submit returns GS_EBUSY */
+} gs_server_config;
+
+typedef struct {
+    gs_view view;             /* intrinsics and size of the query image */
+    const float* image;       /* host, planar float32 [3][H][W]; copied by gs_solve_submit */
+    double init_pose[12];     /* world->camera initial estimate */
+    int32_t steps;            /* Adam steps (> 0) */
+    double lr_start, lr_end;  /* pose learning rate, cosine decay from start to end */
+} gs_solve_request;
+
+typedef struct {
+    double pose[12];          /* final world->camera estimate */
+    double loss;              /* L1 loss of the last step's render */
+    double latency_ms;        /* submission to completion (host clock) */
+    double queue_ms;          /* submission to admission */
+    int32_t steps_done;
+    int32_t status;           /* GS_OK, or the error that ended the solve */
+} gs_solve_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, iterations, active, queued;
+    double busy_ms;           /* wall time spent in iterations */
+    double views_per_iteration; /* mean batch size */
+} gs_server_stats;
+
+/* Starts a server on `scene` (which must outlive it).  The server owns its own
+ * context, stream, forward state and slot storage. */
+int gs_server_create(int device, const gs_scene* scene, const gs_render_opts* opts, const gs_server_config* cfg,
+                     gs_server** out);
+/* Queues a solve; the image is copied.  GS_EBUSY when the queue is full,
+ * GS_EINVAL for an image larger than the configured maximum. */
+int gs_solve_submit(gs_server* srv, const gs_solve_request* req, uint64_t* ticket);
+/* GS_PENDING while the solve runs; GS_OK once it has finished (the result is
+ * returned and the ticket is released); GS_EINVAL for an unknown ticket. */
+int gs_solve_poll(gs_server* srv, uint64_t ticket, gs_solve_result* out);
+/* Like poll, but waits up to timeout_ms; GS_ETIMEOUT if still running. */
+int gs_solve_wait(gs_server* srv, uint64_t ticket, int timeout_ms, gs_solve_result* out);
+/* Cancels a queued or running solve (its result reports GS_EBUSY). */
+int gs_solve_cancel(gs_server* srv, uint64_t ticket);
+int gs_server_stats_get(gs_server* srv, gs_server_stats* out);
+/* Stops the worker (running solves end with GS_EBUSY) and frees the server. */
+void gs_server_destroy(gs_server* srv);
+
 /* Synchronises `stream`, returns and clears the context's device status word
  * (GS_OK, GS_EOVERFLOW from a GS_F_NO_SYNC call, ...). */
 int gs_status(gs_ctx* ctx, void* stream);

@@ -74,6 +74,9 @@ def lib():
         L.or_se3_left_update.argtypes = [F64P, F64P]
         L.or_pose_adam.argtypes = [C.c_int, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int]
+        PP = C.POINTER(F64P)
+        L.or_gaussian_adam.argtypes = [C.c_int, C.c_int, PP, PP, PP, PP, F64P, C.c_double, C.c_double, C.c_double,
+                                       C.c_int, F64P, F64P]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_max_threads.restype = C.c_int
         _lib = L
@@ -261,6 +264,32 @@ def pose_adam(poses, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-8):
     g = np.ascontiguousarray(grad, np.float64)
     lib().or_pose_adam(V, _p(poses, F64P), _p(m, F64P), _p(v, F64P), _p(g, F64P), float(lr), float(b1),
                        float(b2), float(eps), int(step))
+
+
+ADAM_GROUPS = ("means", "log_scales", "quats", "logit_opac", "sh")
+GRAD_GROUPS = ("means", "scales", "quats", "opac", "sh")
+
+
+def gaussian_adam(raw, grads, m, v, lrs, step, sh_degree, b1=0.9, b2=0.999, eps=1e-15):
+    """In place on the float64 dicts raw, m, v (keys ADAM_GROUPS, arrays
+    [n, width]); grads keyed by GRAD_GROUPS.  Returns (scales, opacities)."""
+    n = len(raw["means"])
+    arrs = {}
+    def ptrs(d, keys):
+        out = (F64P * 5)()
+        for j, k in enumerate(keys):
+            a = np.ascontiguousarray(d[k], np.float64)
+            assert a.flags.c_contiguous
+            d[k] = a
+            out[j] = _p(a, F64P)
+        return out
+    g = {k: np.ascontiguousarray(grads[k], np.float64) for k in GRAD_GROUPS}
+    pr, pg, pm, pv = ptrs(raw, ADAM_GROUPS), ptrs(g, GRAD_GROUPS), ptrs(m, ADAM_GROUPS), ptrs(v, ADAM_GROUPS)
+    lr = np.array([lrs["means"], lrs["scales"], lrs["quats"], lrs["opac"], lrs["sh_dc"], lrs["sh_rest"]], np.float64)
+    sc = np.zeros((n, 3)); op = np.zeros(n)
+    lib().or_gaussian_adam(n, int(sh_degree), pr, pg, pm, pv, _p(lr, F64P), b1, b2, eps, int(step), _p(sc, F64P),
+                           _p(op, F64P))
+    return sc, op
 
 
 def image_to_hwc(image, views, v):

@@ -1201,3 +1201,37 @@ void or_pose_adam(int V, double* poses, double* m, double* v, const double* grad
         or_se3_left_update(d, poses + 12 * i);
     }
 }
+
+/* Adam on the raw Gaussian parameters of joint refinement (Sec. 3.3).  The
+ * renderer's gradients are w.r.t. the activated scales s = exp(log s) and
+ * opacities o = 1/(1 + exp(-logit)); the chain rule gives the raw gradients
+ * g_log_s = g_s s and g_logit = g_o o (1 - o).  Group order and widths:
+ * means 3, log-scales 3, quats 4, logit-opacities 1, SH 48 (only the first
+ * 3 (deg+1)^2 coefficients are updated; SH DC at lr[4], the rest at lr[5]).
+ * raw/grad/m/v are [n * width] per group, passed as 5 pointers each. */
+void or_gaussian_adam(int n, int sh_degree, double** raw, double** grad, double** m, double** v,
+                      const double* lr, double b1, double b2, double eps, int step,
+                      double* scales_out, double* opac_out) {
+    static const int width[5] = {3, 3, 4, 1, 48};
+    double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    int used_sh = 3 * (sh_degree + 1) * (sh_degree + 1);
+    for (int gi = 0; gi < 5; gi++) {
+        int w = width[gi];
+        int used = gi == 4 ? used_sh : w;
+        for (int i = 0; i < n; i++)
+            for (int k = 0; k < used; k++) {
+                size_t id = (size_t)i * w + k;
+                double p = raw[gi][id];
+                double g = grad[gi][id];
+                if (gi == 1) g *= exp(p);
+                if (gi == 3) { double o = 1.0 / (1.0 + exp(-p)); g *= o * (1.0 - o); }
+                m[gi][id] = b1 * m[gi][id] + (1.0 - b1) * g;
+                v[gi][id] = b2 * v[gi][id] + (1.0 - b2) * g * g;
+                double l = gi < 4 ? lr[gi] : (k < 3 ? lr[4] : lr[5]);
+                p -= l * (m[gi][id] / c1) / (sqrt(v[gi][id] / c2) + eps);
+                raw[gi][id] = p;
+            }
+    }
+    for (size_t id = 0; id < (size_t)n * 3; id++) scales_out[id] = exp(raw[1][id]);
+    for (int i = 0; i < n; i++) opac_out[i] = 1.0 / (1.0 + exp(-raw[3][i]));
+}

@@ -27,6 +27,8 @@ EXPORTED = (
     "gs_frames_create", "gs_frames_destroy", "gs_frames_reserve", "gs_render_forward", "gs_render_backward",
     "gs_pose_step", "gs_status", "gs_frames_query", "gs_last_error", "gs_version", "gs_ctx_set_profiling",
     "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step", "gs_loss_dssim_static",
+    "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
+    "gs_server_stats_get", "gs_server_destroy",
 )
 
 
@@ -59,6 +61,37 @@ class gs_loss(C.Structure):
 class gs_grads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p),
                 ("sh", C.c_void_p)]
+
+
+class gs_raw_params(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("logit_opacities", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class gs_gaussian_lrs(C.Structure):
+    _fields_ = [("means", C.c_float), ("scales", C.c_float), ("quats", C.c_float), ("opacities", C.c_float),
+                ("sh_dc", C.c_float), ("sh_rest", C.c_float)]
+
+
+class gs_server_config(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("max_width", C.c_int32), ("max_height", C.c_int32),
+                ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32)]
+
+
+class gs_solve_request(C.Structure):
+    _fields_ = [("view", gs_view), ("image", C.c_void_p), ("init_pose", C.c_double * 12), ("steps", C.c_int32),
+                ("lr_start", C.c_double), ("lr_end", C.c_double)]
+
+
+class gs_solve_result(C.Structure):
+    _fields_ = [("pose", C.c_double * 12), ("loss", C.c_double), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("steps_done", C.c_int32), ("status", C.c_int32)]
+
+
+class gs_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("iterations", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64), ("busy_ms", C.c_double),
+                ("views_per_iteration", C.c_double)]
 
 
 _lib = None
@@ -95,6 +128,20 @@ def load(path: str | None = None):
     L.gs_step.restype = C.c_int
     L.gs_loss_dssim_static.argtypes = [vp, vp, i32, i32, C.c_float, vp, vp, vp]
     L.gs_loss_dssim_static.restype = C.c_int
+    L.gs_gaussian_adam.argtypes = [vp, i64, i32, C.POINTER(gs_raw_params), vp, vp, C.POINTER(gs_grads), vp, vp,
+                                   C.POINTER(gs_gaussian_lrs), C.c_float, C.c_float, C.c_float, i32, vp]
+    L.gs_gaussian_adam.restype = C.c_int
+    L.gs_server_create.argtypes = [i32, vp, C.POINTER(gs_render_opts), C.POINTER(gs_server_config), C.POINTER(vp)]
+    L.gs_solve_submit.argtypes = [vp, C.POINTER(gs_solve_request), C.POINTER(C.c_uint64)]
+    L.gs_solve_poll.argtypes = [vp, C.c_uint64, C.POINTER(gs_solve_result)]
+    L.gs_solve_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(gs_solve_result)]
+    L.gs_solve_cancel.argtypes = [vp, C.c_uint64]
+    L.gs_server_stats_get.argtypes = [vp, C.POINTER(gs_server_stats)]
+    L.gs_server_destroy.argtypes = [vp]
+    L.gs_server_destroy.restype = None
+    for name in ("gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
+                 "gs_server_stats_get"):
+        getattr(L, name).restype = C.c_int
     L.gs_pose_step.argtypes = [vp, i32, vp, vp, vp, vp, f64, f64, f64, f64, i32, vp]
     L.gs_status.argtypes = [vp, vp]
     L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -244,6 +291,70 @@ def gs_loss_dssim_static(image, target, width: int, height: int, w_dssim: float,
     """D-SSIM term of one view with the library's static scratch (no allocation)."""
     _ck(load().gs_loss_dssim_static(_ptr(image), _ptr(target), int(width), int(height), float(w_dssim),
                                     _ptr(dl_dimage), _ptr(loss), _stream(stream)))
+
+
+def gs_gaussian_adam(ctx: int, raw: dict, act_scales, act_opac, grads: dict, m, v, lrs: dict, step: int,
+                     sh_degree: int, beta1=0.9, beta2=0.999, eps=1e-15, stream=None) -> None:
+    """raw: means, log_scales, quats, logit_opac, sh (device tensors, updated in
+    place); grads: renderer gradients (means, scales, quats, opac, sh)."""
+    rp = gs_raw_params(_ptr(raw["means"]), _ptr(raw["log_scales"]), _ptr(raw["quats"]), _ptr(raw["logit_opac"]),
+                       _ptr(raw["sh"]))
+    g = make_grads(grads.get("means"), grads.get("scales"), grads.get("quats"), grads.get("opac"), grads.get("sh"))
+    lr = gs_gaussian_lrs(lrs["means"], lrs["scales"], lrs["quats"], lrs["opac"], lrs["sh_dc"], lrs["sh_rest"])
+    _ck(load().gs_gaussian_adam(C.c_void_p(ctx), int(raw["means"].shape[0]), int(sh_degree), C.byref(rp),
+                                _ptr(act_scales), _ptr(act_opac), C.byref(g), _ptr(m), _ptr(v), C.byref(lr),
+                                float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def gs_server_create(device: int, scene: int, opts: gs_render_opts, max_slots: int, max_width: int, max_height: int,
+                     mem_budget: int = 0, queue_capacity: int = 65536) -> int:
+    cfg = gs_server_config(int(max_slots), int(max_width), int(max_height), int(mem_budget), int(queue_capacity))
+    h = C.c_void_p()
+    _ck(load().gs_server_create(int(device), C.c_void_p(scene), C.byref(opts), C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def gs_solve_submit(srv: int, view: dict, image, init_pose, steps: int, lr_start: float, lr_end: float) -> int:
+    """image: host float32 array [3*H*W] (planar)."""
+    import numpy as np
+    img = np.ascontiguousarray(image, np.float32)
+    req = gs_solve_request(views_array([view])[0], img.ctypes.data_as(C.c_void_p),
+                           (C.c_double * 12)(*[float(x) for x in np.asarray(init_pose).reshape(12)]), int(steps),
+                           float(lr_start), float(lr_end))
+    t = C.c_uint64(0)
+    _ck(load().gs_solve_submit(C.c_void_p(srv), C.byref(req), C.byref(t)))
+    return int(t.value)
+
+
+def _result_dict(r: gs_solve_result) -> dict:
+    return dict(pose=list(r.pose), loss=r.loss, latency_ms=r.latency_ms, queue_ms=r.queue_ms, steps_done=r.steps_done,
+                status=r.status)
+
+
+def gs_solve_poll(srv: int, ticket: int):
+    r = gs_solve_result()
+    rc = _ck(load().gs_solve_poll(C.c_void_p(srv), C.c_uint64(ticket), C.byref(r)))
+    return None if rc == GS_PENDING else _result_dict(r)
+
+
+def gs_solve_wait(srv: int, ticket: int, timeout_ms: int):
+    r = gs_solve_result()
+    _ck(load().gs_solve_wait(C.c_void_p(srv), C.c_uint64(ticket), int(timeout_ms), C.byref(r)))
+    return _result_dict(r)
+
+
+def gs_solve_cancel(srv: int, ticket: int) -> None:
+    _ck(load().gs_solve_cancel(C.c_void_p(srv), C.c_uint64(ticket)))
+
+
+def gs_server_stats_get(srv: int) -> dict:
+    st = gs_server_stats()
+    _ck(load().gs_server_stats_get(C.c_void_p(srv), C.byref(st)))
+    return {k: getattr(st, k) for k, _ in gs_server_stats._fields_}
+
+
+def gs_server_destroy(srv: int) -> None:
+    load().gs_server_destroy(C.c_void_p(srv))
 
 
 def gs_status(ctx: int, stream=None) -> int:

@@ -27,6 +27,10 @@ static int fail(int code, const char* fmt, ...) {
 }
 
 namespace gs {
+int set_error(int code, const char* msg);
+}
+
+namespace gs {
 int set_error(int code, const char* msg) {
     g_err = msg ? msg : "";
     return code;
@@ -143,12 +147,14 @@ struct DevBuf {
 // waits for an earlier upload.
 struct ViewTable {
     std::vector<gs_view> views;
+    std::vector<long long> offs;      // custom image offsets (empty: packed)
     std::vector<ViewDev> vdev_host;
     std::vector<int> tile_base_host;
     ViewDev* vdev_pinned = nullptr;
     int* tb_pinned = nullptr;
     DevBuf<ViewDev> vdev;
     DevBuf<int> tile_base;
+    size_t pinned_cap = 0;
     int total_tiles = 0;
     long long total_pixels = 0;
     long long total_image = 0;
@@ -159,10 +165,11 @@ struct ViewTable {
         if (tb_pinned) cudaFreeHost(tb_pinned);
         vdev_pinned = nullptr;
         tb_pinned = nullptr;
+        pinned_cap = 0;
     }
 };
 
-static const size_t kMaxViewTables = 512;
+static const size_t kMaxViewTables = 64;
 
 struct gs_frames {
     gs_ctx* ctx = nullptr;
@@ -175,6 +182,7 @@ struct gs_frames {
     uint32_t n_keys = 0;
     bool have_forward = false;
     std::vector<ViewTable*> tables;   // cache of view configurations
+    size_t evict_next = 0;            // next entry to recycle when the cache is full
     ViewTable* cur = nullptr;         // configuration of the last forward
     std::vector<gs_view> views_host;
     std::vector<ViewDev> vdev_host;
@@ -275,23 +283,42 @@ static bool same_views(const std::vector<gs_view>& a, int n, const gs_view* b) {
     return true;
 }
 
+static bool same_offs(const std::vector<long long>& a, int n, const long long* b) {
+    if (!b) return a.empty();
+    if ((int)a.size() != n) return false;
+    for (int v = 0; v < n; v++)
+        if (a[v] != b[v]) return false;
+    return true;
+}
+
 // Selects (or builds and uploads) the device tables of a view configuration.
-static int upload_views(gs_frames* fr, int n_views, const gs_view* views, bool allow_grow, cudaStream_t s) {
+static int upload_views(gs_frames* fr, int n_views, const gs_view* views, const long long* offs, bool allow_grow,
+                        cudaStream_t s) {
     ViewTable* hit = nullptr;
-    if (fr->cur && same_views(fr->cur->views, n_views, views)) hit = fr->cur;
+    if (fr->cur && same_views(fr->cur->views, n_views, views) && same_offs(fr->cur->offs, n_views, offs)) hit = fr->cur;
     for (size_t k = 0; !hit && k < fr->tables.size(); k++)
-        if (same_views(fr->tables[k]->views, n_views, views)) hit = fr->tables[k];
+        if (same_views(fr->tables[k]->views, n_views, views) && same_offs(fr->tables[k]->offs, n_views, offs))
+            hit = fr->tables[k];
     if (!hit) {
         if (!allow_grow) return fail(GS_EOVERFLOW, "new view configuration in no-sync mode (run it once without GS_F_NO_SYNC)");
+        ViewTable* t = nullptr;
         if (fr->tables.size() >= kMaxViewTables) {
+            // recycle an entry other than the current one; its pinned staging
+            // may still feed a pending upload, so drain the stream first
             CK(cudaStreamSynchronize(s));
-            for (ViewTable* t : fr->tables) { t->release(); delete t; }
-            fr->tables.clear();
-            fr->cur = nullptr;
+            for (size_t k = 0; k < fr->tables.size(); k++) {
+                ViewTable* c = fr->tables[(fr->evict_next + k) % fr->tables.size()];
+                if (c != fr->cur) { t = c; fr->evict_next = (fr->evict_next + k + 1) % fr->tables.size(); break; }
+            }
         }
-        ViewTable* t = new (std::nothrow) ViewTable();
-        if (!t) return fail(GS_ENOMEM, "host allocation failed");
+        if (!t) {
+            t = new (std::nothrow) ViewTable();
+            if (!t) return fail(GS_ENOMEM, "host allocation failed");
+            fr->tables.push_back(t);
+        }
         t->views.assign(views, views + n_views);
+        t->offs.clear();
+        if (offs) t->offs.assign(offs, offs + n_views);
         t->vdev_host.assign(n_views, ViewDev{});
         t->tile_base_host.assign(n_views + 1, 0);
         long long img = 0, pix = 0;
@@ -304,11 +331,11 @@ static int upload_views(gs_frames* fr, int n_views, const gs_view* views, bool a
             d.gw = (w.width + GS_TILE - 1) / GS_TILE;
             d.gh = (w.height + GS_TILE - 1) / GS_TILE;
             d.tile_base = tb;
-            d.img_off = img;
+            d.img_off = offs ? offs[v] : img;
             d.pix_off = pix;
             t->tile_base_host[v] = tb;
             tb += d.gw * d.gh;
-            img += 3LL * w.width * w.height;
+            img = offs ? std::max(img, offs[v] + 3LL * w.width * w.height) : img + 3LL * w.width * w.height;
             pix += (long long)w.width * w.height;
         }
         t->tile_base_host[n_views] = tb;
@@ -317,19 +344,24 @@ static int upload_views(gs_frames* fr, int n_views, const gs_view* views, bool a
         t->total_image = img;
         int rc;
         if ((rc = t->vdev.ensure(std::max(n_views, 1), true, "views")) ||
-            (rc = t->tile_base.ensure(n_views + 1, true, "tile_base"))) {
-            t->release(); delete t;
+            (rc = t->tile_base.ensure(n_views + 1, true, "tile_base")))
             return rc;
+        if (t->pinned_cap < (size_t)n_views + 1) {
+            if (t->vdev_pinned) cudaFreeHost(t->vdev_pinned);
+            if (t->tb_pinned) cudaFreeHost(t->tb_pinned);
+            t->vdev_pinned = nullptr;
+            t->tb_pinned = nullptr;
+            const size_t c = (size_t)n_views + 16;
+            cudaError_t e = cudaMallocHost(&t->vdev_pinned, sizeof(ViewDev) * c);
+            if (e == cudaSuccess) e = cudaMallocHost(&t->tb_pinned, sizeof(int) * (c + 1));
+            if (e != cudaSuccess) { t->pinned_cap = 0; return fail(GS_ENOMEM, "pinned allocation failed"); }
+            t->pinned_cap = c;
         }
-        cudaError_t e = cudaMallocHost(&t->vdev_pinned, sizeof(ViewDev) * std::max(n_views, 1));
-        if (e == cudaSuccess) e = cudaMallocHost(&t->tb_pinned, sizeof(int) * (n_views + 1));
-        if (e != cudaSuccess) { t->release(); delete t; return fail(GS_ENOMEM, "pinned allocation failed"); }
         memcpy(t->vdev_pinned, t->vdev_host.data(), sizeof(ViewDev) * n_views);
         memcpy(t->tb_pinned, t->tile_base_host.data(), sizeof(int) * (n_views + 1));
         if (n_views > 0)
             CK(cudaMemcpyAsync(t->vdev.p, t->vdev_pinned, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(t->tile_base.p, t->tb_pinned, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
-        fr->tables.push_back(t);
         hit = t;
     }
     fr->cur = hit;
@@ -519,16 +551,31 @@ int gs_frames_reserve(gs_frames* fr, int64_t keys, int64_t pairs, int64_t pixels
 int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views, const double* poses,
                       const gs_render_opts* opts, gs_frames* fr, float* image, const float* target, double* loss_out,
                       void* stream) {
+    return gs::render_forward_impl(ctx, scene, n_views, views, nullptr, poses, opts, fr, image, target, loss_out,
+                                   static_cast<cudaStream_t>(stream));
+}
+
+int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views, const double* poses,
+                       const gs_render_opts* opts, gs_frames* fr, const float* image, const gs_loss* loss,
+                       gs_grads* grads, double* pose_grad, void* stream) {
+    return gs::render_backward_impl(ctx, scene, n_views, views, nullptr, poses, opts, fr, image, loss, grads, pose_grad,
+                                    static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                            const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
+                            float* image, const float* target, double* loss_out, cudaStream_t s) {
     if (!ctx || !fr || !opts) return fail(GS_EINVAL, "NULL ctx/frames/opts");
     if (fr->ctx != ctx) return fail(GS_EINVAL, "frames belong to another context");
     int rc;
     if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
     if (n_views > 0 && (!poses || !image)) return fail(GS_EINVAL, "poses/image is NULL");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool grow = !(opts->flags & GS_F_NO_SYNC);
     CK(cudaSetDevice(ctx->device));
     fr->have_forward = false;
-    if ((rc = upload_views(fr, n_views, views, grow, s))) return rc;
+    if ((rc = upload_views(fr, n_views, views, img_offs, grow, s))) return rc;
     const int n = scene->d.n;
     const size_t vn = (size_t)n * n_views;
     const int T = fr->total_tiles;
@@ -620,13 +667,15 @@ int gs_render_forward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_
     return GS_OK;
 }
 
-int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views, const double* poses,
-                       const gs_render_opts* opts, gs_frames* fr, const float* image, const gs_loss* loss,
-                       gs_grads* grads, double* pose_grad, void* stream) {
+int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                             const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
+                             const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad,
+                             cudaStream_t s) {
     if (!ctx || !fr || !opts || !loss) return fail(GS_EINVAL, "NULL ctx/frames/opts/loss");
     int rc;
     if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
-    if (!fr->have_forward || fr->n_views != n_views || fr->n != scene->d.n || !same_views(fr->views_host, n_views, views))
+    if (!fr->have_forward || fr->n_views != n_views || fr->n != scene->d.n || !fr->cur ||
+        !same_views(fr->views_host, n_views, views) || !same_offs(fr->cur->offs, n_views, img_offs))
         return fail(GS_EINVAL, "backward does not match the frames' last forward");
     if (n_views == 0) return GS_OK;
     if (!image) return fail(GS_EINVAL, "image is NULL");
@@ -634,7 +683,6 @@ int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs
     if ((loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM) && !loss->target)
         return fail(GS_EINVAL, "loss needs a target");
     if (loss->kind < 0 || loss->kind > 2) return fail(GS_EINVAL, "unknown loss kind %d", loss->kind);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool grow = !(opts->flags & GS_F_NO_SYNC);
     CK(cudaSetDevice(ctx->device));
     const int n = scene->d.n;
@@ -713,6 +761,8 @@ int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs
     }
     return GS_OK;
 }
+
+extern "C" {
 
 int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, const gs_view* views,
             const double* poses, const gs_render_opts* opts, const gs_loss* loss, float* image_out, gs_grads* grads,
@@ -813,6 +863,33 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
             CK(cudaMemcpyAsync(pose_grad, dpose_grad, 6 * sizeof(double) * n_views, cudaMemcpyDeviceToHost, s));
         if (loss_out && n_views) CK(cudaMemcpyAsync(loss_out, dloss, sizeof(double) * n_views, cudaMemcpyDeviceToHost, s));
     }
+    return GS_OK;
+}
+
+int gs_gaussian_adam(gs_ctx* ctx, int64_t n, int sh_degree, gs_raw_params* raw, float* scales_out,
+                     float* opacities_out, const gs_grads* grads, float* m, float* v, const gs_gaussian_lrs* lrs,
+                     float b1, float b2, float eps, int step, void* stream) {
+    if (!ctx || !raw || !grads || !lrs) return fail(GS_EINVAL, "NULL argument");
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || step < 1) return fail(GS_EINVAL, "bad n, sh_degree or step");
+    if (n > 0 && (!raw->means || !raw->log_scales || !raw->quats || !raw->logit_opacities || !raw->sh || !m || !v ||
+                  !scales_out || !opacities_out))
+        return fail(GS_EINVAL, "NULL parameter, moment or output array");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = n;
+    gs::AdamGroup G[5];
+    G[0] = {raw->means, grads->means, m, v, nullptr, 3, 3, 0, lrs->means, lrs->means, 3};
+    G[1] = {raw->log_scales, grads->scales, m + 3 * N, v + 3 * N, scales_out, 3, 3, 1, lrs->scales, lrs->scales, 3};
+    G[2] = {raw->quats, grads->quats, m + 6 * N, v + 6 * N, nullptr, 4, 4, 0, lrs->quats, lrs->quats, 4};
+    G[3] = {raw->logit_opacities, grads->opacities, m + 10 * N, v + 10 * N, opacities_out, 1, 1, 2, lrs->opacities,
+            lrs->opacities, 1};
+    G[4] = {raw->sh, grads->sh, m + 11 * N, v + 11 * N, nullptr, 48, 3 * (sh_degree + 1) * (sh_degree + 1), 0,
+            lrs->sh_dc, lrs->sh_rest, 3};
+    {
+        PROF(PK_POSE_ADAM, 5);
+        gs::launch_gaussian_adam(N, G, 5, b1, b2, eps, step, s);
+    }
+    CK_LAUNCH();
     return GS_OK;
 }
 
@@ -988,3 +1065,8 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
 }
 
 }  // extern "C"
+
+int gs::scene_count(const gs_scene* scene) { return scene ? scene->d.n : 0; }
+
+uint32_t gs::frames_num_keys(const gs_frames* fr) { return fr ? fr->n_keys : 0u; }
+

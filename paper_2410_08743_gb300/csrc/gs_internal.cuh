@@ -151,11 +151,49 @@ void launch_pose_reduce(int n_views, int n_blocks, const double* partials, doubl
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr,
                       double b1, double b2, double eps, int step, cudaStream_t s);
 
+void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
+                            const double* lrs, double b1, double b2, double eps, cudaStream_t s);
+
+void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s);
+void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m, double* v, const double* grad,
+                            const int* steps, const double* lrs, double b1, double b2, double eps, cudaStream_t s);
+
+// One parameter group of the Gaussian Adam update (gs_pose.cu).
+struct AdamGroup {
+    float* p;          // raw parameter
+    const float* g;    // gradient w.r.t. the activated parameter
+    float* m;
+    float* v;
+    float* act;        // activated output (scales / opacities) or nullptr
+    int width;         // floats per Gaussian
+    int used;          // leading floats per Gaussian that are optimised
+    int act_kind;      // 0 none, 1 exp, 2 sigmoid
+    float lr;
+    float lr_tail;     // learning rate of elements >= tail_from (SH beyond DC)
+    int tail_from;
+};
+void launch_gaussian_adam(int64_t n, const AdamGroup* groups, int n_groups, float b1, float b2, float eps, int step,
+                          cudaStream_t s);
+
 void launch_dssim(int n_views, const gs_view* views_host, const long long* img_off_host, const float* image,
                   const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
                   cudaStream_t s);
 
 // Records a message for gs_last_error() and returns `code` (defined in gs_api.cu).
 int set_error(int code, const char* msg);
+
+// Accessors of the opaque ABI objects (gs_api.cu).
+int scene_count(const gs_scene* scene);
+uint32_t frames_num_keys(const gs_frames* fr);
+
+// Forward / backward with optional per-view float offsets of the planar
+// images (img_offs == nullptr: packed layout).  Used by the serving loop,
+// whose views keep their images in fixed per-slot storage.
+int render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                        const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
+                        float* image, const float* target, double* loss_out, cudaStream_t s);
+int render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
+                         const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
+                         const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad, cudaStream_t s);
 
 }  // namespace gs

@@ -75,4 +75,133 @@ void launch_pose_adam(int n_views, double* poses, double* m, double* v, const do
     k_pose_adam<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, lr, b1, b2, eps, c1, c2);
 }
 
+// Per-view variant: every view has its own step count (1-based, <= 0 means
+// "leave this view alone") and learning rate, as in a batch of independent
+// pose solves that started at different times.
+__global__ void k_pose_adam_multi(int n_views, double* __restrict__ poses, double* __restrict__ m,
+                                  double* __restrict__ v, const double* __restrict__ g, const int* __restrict__ steps,
+                                  const double* __restrict__ lrs, double b1, double b2, double eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_views) return;
+    const int step = steps[i];
+    if (step <= 0) return;
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    const double lr = lrs[i];
+    double d[6];
+    for (int k = 0; k < 6; k++) {
+        const double gk = g[6 * i + k];
+        const double mk = b1 * m[6 * i + k] + (1.0 - b1) * gk;
+        const double vk = b2 * v[6 * i + k] + (1.0 - b2) * gk * gk;
+        m[6 * i + k] = mk;
+        v[6 * i + k] = vk;
+        d[k] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
+    }
+    double E[9], te[3];
+    se3_exp(d, E, te);
+    double* P = poses + 12 * i;
+    double R[9], t[3];
+    for (int a = 0; a < 3; a++) {
+        for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
+        t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
+    }
+    for (int k = 0; k < 9; k++) P[k] = R[k];
+    for (int k = 0; k < 3; k++) P[9 + k] = t[k];
+}
+
+void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
+                            const double* lrs, double b1, double b2, double eps, cudaStream_t s) {
+    if (n_views <= 0) return;
+    k_pose_adam_multi<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2, eps);
+}
+
+// Slot-indexed variants for a batch of independent solves whose state lives
+// in fixed slots: view k of the batch is slot slot_of[k].
+__global__ void k_gather_poses(int n, const int* __restrict__ slot_of, const double* __restrict__ slot_poses,
+                               double* __restrict__ packed) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * 12) return;
+    packed[k] = slot_poses[(size_t)slot_of[k / 12] * 12 + k % 12];
+}
+
+__global__ void k_pose_adam_slots(int n, const int* __restrict__ slot_of, double* __restrict__ poses,
+                                  double* __restrict__ m, double* __restrict__ v, const double* __restrict__ g,
+                                  const int* __restrict__ steps, const double* __restrict__ lrs, double b1, double b2,
+                                  double eps) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = slot_of[k];
+    const int step = steps[k];
+    if (step <= 0) return;
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    const double lr = lrs[k];
+    double d[6];
+    for (int c = 0; c < 6; c++) {
+        const double gk = g[6 * k + c];
+        const double mk = b1 * m[6 * i + c] + (1.0 - b1) * gk;
+        const double vk = b2 * v[6 * i + c] + (1.0 - b2) * gk * gk;
+        m[6 * i + c] = mk;
+        v[6 * i + c] = vk;
+        d[c] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
+    }
+    double E[9], te[3];
+    se3_exp(d, E, te);
+    double* P = poses + 12 * (size_t)i;
+    double R[9], t[3];
+    for (int a = 0; a < 3; a++) {
+        for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
+        t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
+    }
+    for (int c = 0; c < 9; c++) P[c] = R[c];
+    for (int c = 0; c < 3; c++) P[9 + c] = t[c];
+}
+
+void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s) {
+    if (n <= 0) return;
+    k_gather_poses<<<(n * 12 + 255) / 256, 256, 0, s>>>(n, slot_of, slot_poses, packed);
+}
+
+void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m, double* v, const double* grad,
+                            const int* steps, const double* lrs, double b1, double b2, double eps, cudaStream_t s) {
+    if (n <= 0) return;
+    k_pose_adam_slots<<<(n + 63) / 64, 64, 0, s>>>(n, slot_of, poses, m, v, grad, steps, lrs, b1, b2, eps);
+}
+
+// ------------------------------------------------------------ Gaussian Adam
+// Adam on the raw Gaussian parameters of joint refinement (Sec. 3.3): means,
+// log-scales, quaternions, logit-opacities and SH coefficients.  The renderer
+// differentiates the activated scales s = exp(log s) and opacities
+// o = sigmoid(logit o), so the update first chains ds/dlog s = s and
+// do/dlogit = o (1 - o); it then writes the activated values the next render
+// reads.  One thread per parameter element; element k of Gaussian i in a
+// group of width w lives at i * w + k in both the parameter and moment arrays.
+__global__ void k_gaussian_adam(int64_t n, AdamGroup G, float b1, float b2, float eps, float c1, float c2) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * G.width) return;
+    const int k = (int)(idx % G.width);
+    if (k >= G.used) return;
+    float p = G.p[idx];
+    float g = G.g ? G.g[idx] : 0.0f;
+    if (G.act_kind == 1) g *= expf(p);
+    else if (G.act_kind == 2) { const float o = 1.0f / (1.0f + expf(-p)); g *= o * (1.0f - o); }
+    const float mk = b1 * G.m[idx] + (1.0f - b1) * g;
+    const float vk = b2 * G.v[idx] + (1.0f - b2) * g * g;
+    G.m[idx] = mk;
+    G.v[idx] = vk;
+    const float lr = k >= G.tail_from ? G.lr_tail : G.lr;
+    p -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    G.p[idx] = p;
+    if (G.act) G.act[idx] = G.act_kind == 1 ? expf(p) : 1.0f / (1.0f + expf(-p));
+}
+
+void launch_gaussian_adam(int64_t n, const AdamGroup* groups, int n_groups, float b1, float b2, float eps, int step,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    for (int k = 0; k < n_groups; k++) {
+        const int64_t total = n * groups[k].width;
+        k_gaussian_adam<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, groups[k], b1, b2, eps, c1, c2);
+    }
+}
+
 }  // namespace gs
+

@@ -344,7 +344,7 @@ void launch_preprocess_fwd(const SceneDev& sc, int n_views, const ViewDev* views
 //   conic -> Sigma_hat -> (J, Sigma_c) -> mu_c, Sigma -> M -> (s, R -> q)
 //   colour -> SH coefficients and viewing direction -> mu
 //   pose: rho += g_mu_c + R_c g_mu(SH);  phi += mu_c x g_mu_c + 2 w(Sigma_c G_Sigma_c)
-template <int D>
+template <int D, bool POSE_ONLY>
 __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
                                                         RenderParams rp, SplatArrays sp, Grad2DArrays g2d,
                                                         gs_grads grads, double* __restrict__ pose_partials) {
@@ -491,12 +491,13 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int b = 0; b < 3; b++) T2[a * 3 + b] = Rc[0 * 3 + a] * GSc[0 * 3 + b] + Rc[1 * 3 + a] * GSc[1 * 3 + b] + Rc[2 * 3 + a] * GSc[2 * 3 + b];
+            if constexpr (!POSE_ONLY) {
 #pragma unroll
-            for (int a = 0; a < 3; a++)
+                for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int b = 0; b < 3; b++) gSig[a * 3 + b] += T2[a * 3 + 0] * Rc[0 * 3 + b] + T2[a * 3 + 1] * Rc[1 * 3 + b] + T2[a * 3 + 2] * Rc[2 * 3 + b];
-            // opacity
-            gop += b4.y;
+                    for (int b = 0; b < 3; b++) gSig[a * 3 + b] += T2[a * 3 + 0] * Rc[0 * 3 + b] + T2[a * 3 + 1] * Rc[1 * 3 + b] + T2[a * 3 + 2] * Rc[2 * 3 + b];
+                gop += b4.y;  // opacity
+            }
             // SH colour
             float dx = mu[0] - vd.oc[0], dy = mu[1] - vd.oc[1], dz = mu[2] - vd.oc[2];
             const float vl = sqrtf(dx * dx + dy * dy + dz * dz), ivl = 1.0f / vl;
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
                 const float gch = raw < 0.0f ? 0.0f : gcol[ch];
 #pragma unroll
                 for (int b = 0; b < NC; b++) {
-                    sgf[(b * 3 + ch) * blockDim.x + threadIdx.x] += Y[b] * gch;
+                    if constexpr (!POSE_ONLY) sgf[(b * 3 + ch) * blockDim.x + threadIdx.x] += Y[b] * gch;
                     wsum[b] += f[b * 3 + ch] * gch;
                 }
             }
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
             }
         }
     }
-    if (live) {
+    if (live && !POSE_ONLY) {
         // Sigma = M M^T -> dL/dM = 2 gSig M  (gSig symmetric)
         float GM[9];
 #pragma unroll
@@ -621,18 +622,27 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
     static bool attr = false;
     if (!attr) {
         const int mx = 200 * 1024;
-        cudaFuncSetAttribute(k_preprocess_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_preprocess_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_preprocess_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_preprocess_bwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_bwd<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr = true;
     }
+    const bool po = !grads.means && !grads.scales && !grads.quats && !grads.opacities && !grads.sh;
+#define GS_PRE_BWD(D)                                                                                          \
+    if (po) k_preprocess_bwd<D, true><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); \
+    else k_preprocess_bwd<D, false><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials)
     switch (sc.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;
-        case 1: k_preprocess_bwd<1><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;
-        case 2: k_preprocess_bwd<2><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;
-        default: k_preprocess_bwd<3><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); break;
+        case 0: GS_PRE_BWD(0); break;
+        case 1: GS_PRE_BWD(1); break;
+        case 2: GS_PRE_BWD(2); break;
+        default: GS_PRE_BWD(3); break;
     }
+#undef GS_PRE_BWD
 }
 
 // Deterministic sum of the block partials: one block per view, a fixed

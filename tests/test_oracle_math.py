@@ -198,3 +198,34 @@ def test_dssim_gradient_finite_differences():
         im = img.copy(); im[k] -= h
         fd = (oracle.loss_dssim(views, ip, tgt, 0.2)[0] - oracle.loss_dssim(views, im, tgt, 0.2)[0]) / (2 * h)
         assert abs(fd - d[k]) <= 1e-6 * max(1e-3, abs(d[k])) + 1e-10, (k, fd, d[k])
+
+
+def test_gaussian_adam_first_step_closed_form_and_chain():
+    """First Adam step: m_hat = g, v_hat = g^2, so each raw parameter moves by
+    -lr g / (|g| + eps); log-scales and logit-opacities see the activated
+    gradient times ds/dlog s = s and do/dlogit = o (1 - o)."""
+    rng = np.random.default_rng(15)
+    n = 7
+    raw = {"means": rng.standard_normal((n, 3)), "log_scales": rng.normal(-3, 0.5, (n, 3)),
+           "quats": rng.standard_normal((n, 4)), "logit_opac": rng.standard_normal((n, 1)),
+           "sh": rng.standard_normal((n, 48))}
+    grads = {"means": rng.standard_normal((n, 3)), "scales": rng.standard_normal((n, 3)),
+             "quats": rng.standard_normal((n, 4)), "opac": rng.standard_normal((n, 1)),
+             "sh": rng.standard_normal((n, 48))}
+    m = {k: np.zeros_like(a) for k, a in raw.items()}
+    v = {k: np.zeros_like(a) for k, a in raw.items()}
+    lrs = dict(means=1e-3, scales=5e-3, quats=1e-3, opac=5e-2, sh_dc=2.5e-3, sh_rest=1.25e-4)
+    r0 = {k: a.copy() for k, a in raw.items()}
+    sc, op = oracle.gaussian_adam(raw, grads, m, v, lrs, 1, sh_degree=1)
+    eps = 1e-15
+    step = lambda g, lr: -lr * g / (np.abs(g) + eps)
+    np.testing.assert_allclose(raw["means"], r0["means"] + step(grads["means"], 1e-3), atol=1e-15)
+    gs = grads["scales"] * np.exp(r0["log_scales"])
+    np.testing.assert_allclose(raw["log_scales"], r0["log_scales"] + step(gs, 5e-3), atol=1e-15)
+    o = 1 / (1 + np.exp(-r0["logit_opac"]))
+    np.testing.assert_allclose(raw["logit_opac"], r0["logit_opac"] + step(grads["opac"] * o * (1 - o), 5e-2), atol=1e-15)
+    np.testing.assert_allclose(raw["sh"][:, :3], r0["sh"][:, :3] + step(grads["sh"][:, :3], 2.5e-3), atol=1e-15)
+    np.testing.assert_allclose(raw["sh"][:, 3:12], r0["sh"][:, 3:12] + step(grads["sh"][:, 3:12], 1.25e-4), atol=1e-15)
+    assert np.array_equal(raw["sh"][:, 12:], r0["sh"][:, 12:])      # above degree 1: untouched
+    np.testing.assert_allclose(sc, np.exp(raw["log_scales"]), rtol=1e-15)
+    np.testing.assert_allclose(op, 1 / (1 + np.exp(-raw["logit_opac"][:, 0])), rtol=1e-15)
