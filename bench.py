@@ -44,7 +44,11 @@ def _args():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample-views", type=int, default=1)
+    ap.add_argument("--cpu-sample-views", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-steps", type=int, default=100)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -114,15 +118,31 @@ def _workload(args, rank: int):
     return w
 
 
+def _sample_views(w, n_views: int):
+    """One view of each resolution first, then the next views in order."""
+    pick, seen = [], set()
+    for k, v in enumerate(w["views"]):
+        if (v["width"], v["height"]) not in seen:
+            seen.add((v["width"], v["height"]))
+            pick.append(k)
+    for k in range(len(w["views"])):
+        if len(pick) >= n_views:
+            break
+        if k not in pick:
+            pick.append(k)
+    return sorted(pick[:n_views])
+
+
 def _cpu_baseline(w, n_views: int):
-    """The FP64 oracle on a bounded sample: the first `n_views` views of the
-    workload, full forward + L1 + backward, all host cores."""
+    """The FP64 oracle on a bounded sample of the workload's views (one per
+    resolution, then more), full forward + L1 + backward, all host cores."""
     import oracle
     from paper_2410_08743_gb300 import synth
     nthr = os.cpu_count() or 1
     oracle.set_threads(nthr)
-    views = w["views"][:n_views]
-    poses = w["poses"][:n_views]
+    pick = _sample_views(w, n_views)
+    views = [w["views"][k] for k in pick]
+    poses = w["poses"][pick]
     rng = np.random.default_rng(0)
     target = synth.random_image_like(rng, views)
     t0 = time.perf_counter()
@@ -199,9 +219,15 @@ def run_gpu(args):
         r.forward(p, views, P, image=image)
         r.backward(p, views, P, image, l1, grads, pose_grad)
 
-    # warm-up: the first step grows the workspaces, the rest run without syncs
+    # warm-up: the first step grows the workspaces; the autotuner then picks the
+    # result-neutral launch parameters (cached per workload class); the rest of
+    # the warm-up runs without syncs
     step()
     torch.cuda.synchronize()
+    from paper_2410_08743_gb300 import tune
+    tuned = tune.autotune(r, p, views, P, image, l1, grads, pose_grad, repeats=1)
+    for g in grads.values():
+        g.zero_()
     r.set_flags(L.GS_F_NO_SYNC)
     for _ in range(max(0, args.warmup - 1)):
         step()
@@ -278,6 +304,7 @@ def run_gpu(args):
         vl = [L.make_loss(L.GS_LOSS_L1, target=vt[k], w_l1=1.0, loss_out=loss_v[k:k + 1]) for k in range(V)]
         vP = [P[k:k + 1].contiguous() for k in range(V)]
         pr = Renderer(local)
+        L.gs_ctx_set_tuning(pr.ctx, **tuned["tuning"])
         for k in range(V):  # grow workspaces and cache every view's tables
             pr.forward(p, views[k:k + 1], vP[k], image=vimg[k])
             pr.backward(p, views[k:k + 1], vP[k], vimg[k], vl[k], grads, pose_grad[k:k + 1])
@@ -339,6 +366,11 @@ def run_gpu(args):
                         sm_mhz_peak)
     kernels = {k: {"ms_per_step": v[0] / K, "launches_per_step": v[1] / K} for k, v in sorted(prof.items())}
 
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(p, dev, args, 64)
+        serving["plain"] = run_serving(p, dev, args, 1)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -356,7 +388,8 @@ def run_gpu(args):
                                    f"({npix / 1e6:.2f} Mpix/step/GPU), L1 loss, all Gaussian grads + {V} pose grads",
                        "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
                        "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
-            "plain_value": plain_value, "graph_value": graph_value,
+            "plain_value": plain_value, "graph_value": graph_value, "serving": serving,
+            "tuning": tuned,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches * K),
             "roofline": roof, "cpu_baseline": cpu, "kernels": kernels,
             "counters": {"keys": n_keys, "pairs_eval_fwd": counters[0], "pairs_blend_fwd": counters[1],
@@ -373,6 +406,54 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serving(p, dev, args, slots: int):
+    """Replays Poisson arrivals of pose-estimation requests (mixed sizes
+    256..1280 wide) in real time against a server with `slots` slots and
+    returns latency percentiles and throughput."""
+    import threading
+
+    import torch
+
+    from paper_2410_08743_gb300 import _lib as L
+    from paper_2410_08743_gb300 import synth
+    from paper_2410_08743_gb300.render import Renderer
+    reqs = synth.serving_requests(seed=4, n_requests=args.serve_requests, rate_hz=args.serve_rate,
+                                  steps=args.serve_steps)
+    r = Renderer(dev.index or 0)
+    imgs = [r.forward(p, [q["view"]], torch.from_numpy(q["gt_pose"][None]).to(dev)).cpu().numpy() for q in reqs]
+    r.close()
+    sh = L.gs_scene_borrow(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
+    srv = L.gs_server_create(dev.index or 0, sh, L.gs_default_opts(), slots, 1280, 720, 200 * (1 << 30), 1 << 20)
+    # warm the worker (workspaces) with one small solve
+    q0 = reqs[0]
+    L.gs_solve_wait(srv, L.gs_solve_submit(srv, q0["view"], imgs[0], q0["init_pose"], 2, 1e-2, 1e-4), 600000)
+    tickets = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for k, q in enumerate(reqs):
+            dt = t_start + q["arrival"] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[k] = L.gs_solve_submit(srv, q["view"], imgs[k], q["init_pose"], q["steps"], 1e-2, 1e-4)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = [L.gs_solve_wait(srv, t, 3600 * 1000) for t in tickets]
+    t_end = time.perf_counter()
+    st = L.gs_server_stats_get(srv)
+    L.gs_server_destroy(srv)
+    L.gs_scene_free(sh)
+    lat = np.array([x["latency_ms"] for x in res])
+    px = sum(q["view"]["width"] * q["view"]["height"] for q in reqs) * args.serve_steps
+    return {"slots": slots, "requests": len(reqs), "rate_hz": args.serve_rate, "steps": args.serve_steps,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": len(reqs) / (t_end - t_start), "fwd_bwd_mpix_s": px / (t_end - t_start) / 1e6,
+            "views_per_iteration": st["views_per_iteration"],
+            "failed": int(sum(1 for x in res if x["status"] != 0))}
+
+
 # Algorithmic work per unit (see the design notes for the derivation):
 #   blend_fwd: 16 FP32 lane operations per evaluated (pixel, splat) pair
 #              (d = p - mu_hat, the conic quadratic form, the exponent, alpha,
@@ -383,6 +464,11 @@ def run_gpu(args):
 #              background sum, conic/mean/opacity gradients).
 OPS_FWD_EVAL, OPS_FWD_BLEND = 16, 7
 OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
+
+# DRAM bytes (read + write) per unit from one ncu capture of the current
+# kernel on the 4-view small case, scaled to a launch by the run's units
+# (profiles/top_kernels_batched_1M_4views.md).  Re-measure when the kernel changes.
+TRAFFIC_PER_UNIT = {"blend_bwd": (139.2, 5)}   # bytes per list entry read by the backward blend
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
@@ -399,8 +485,10 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
     if kname == "blend_bwd":
         ops = (OPS_BWD_EVAL * counters[2] + OPS_BWD_GRAD * counters[3]) / lps
         a = ops / t / 1e12
+        per, ci = TRAFFIC_PER_UNIT["blend_bwd"]
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+                "frac": a / alu_peak, "traffic": per * counters[ci] / lps,
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (2070 MHz)"}
     if kname == "preprocess_fwd":
         by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 52) / lps
     elif kname == "preprocess_bwd":

@@ -62,6 +62,13 @@ enum {
                                  GS_EOVERFLOW through gs_status() instead of
                                  growing (required inside CUDA-graph capture) */
     GS_F_HOST_IO = 1u << 1,   /* gs_step only: every array argument is host memory */
+    GS_F_RECOMPUTE = 1u << 3, /* gs_render_backward only: rebuild the forward state
+                                 (projection, tile lists, sorted prefixes, per-pixel
+                                 state) of THESE views instead of requiring that `fr`
+                                 still holds it, so one frames object can serve many
+                                 view batches in turn and memory stays bounded by
+                                 one batch's tile lists (the forward is deterministic,
+                                 so the result is the same) */
     GS_F_FULL_SORT = 1u << 2  /* sort every tile's whole list before blending.  By
                                  default a tile is sorted only as far as the forward
                                  blend consumes it (identical image and gradients);
@@ -206,6 +213,29 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* scene, int n_views,
 int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* adam_m, double* adam_v,
                  const double* pose_grad, double lr, double beta1, double beta2, double eps,
                  int step, void* stream);
+
+/* ------------------------------------------------------------ tuning
+ * Launch parameters that change performance but never results: the number of
+ * Gaussians per CTA of the tile counting / key scatter (1024..8192), the run
+ * length of the forward blend's lazy tile sort (1024 or 2048 keys) and the
+ * block size of the forward preprocess (128 or 256 threads). */
+typedef struct {
+    int32_t scatter_chunk;
+    int32_t sort_chunk;
+    int32_t preprocess_threads;
+} gs_tuning;
+
+int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t);
+int gs_ctx_get_tuning(gs_ctx* ctx, gs_tuning* t);
+
+/* Autotuner: times one forward + backward of the given workload (the loss and
+ * gradient targets as for gs_render_backward; grads may be NULL) for every
+ * candidate tuning, `repeats` times each after one warm-up, keeps the fastest
+ * in the context and returns it in *best (and its time in *best_ms).
+ * Synchronous. */
+int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, const gs_view* views,
+                const double* poses, const gs_render_opts* opts, float* image, const gs_loss* loss,
+                gs_grads* grads, double* pose_grad, int repeats, gs_tuning* best, double* best_ms, void* stream);
 
 /* Raw (unactivated) Gaussian parameters optimised in joint refinement
  * (device; layouts as the scene's, log-scales and logit-opacities in place of

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgsplat.so")
 
 GS_OK, GS_PENDING = 0, 1
 GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3, -4, -5, -6
-GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT = 1, 2, 4
+GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT, GS_F_RECOMPUTE = 1, 2, 4, 8
 GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM = 0, 1, 2
 (GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
  GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT) = range(11)
@@ -28,7 +28,7 @@ EXPORTED = (
     "gs_pose_step", "gs_status", "gs_frames_query", "gs_last_error", "gs_version", "gs_ctx_set_profiling",
     "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step", "gs_loss_dssim_static",
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
-    "gs_server_stats_get", "gs_server_destroy",
+    "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
 )
 
 
@@ -61,6 +61,10 @@ class gs_loss(C.Structure):
 class gs_grads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p),
                 ("sh", C.c_void_p)]
+
+
+class gs_tuning(C.Structure):
+    _fields_ = [("scatter_chunk", C.c_int32), ("sort_chunk", C.c_int32), ("preprocess_threads", C.c_int32)]
 
 
 class gs_raw_params(C.Structure):
@@ -128,6 +132,13 @@ def load(path: str | None = None):
     L.gs_step.restype = C.c_int
     L.gs_loss_dssim_static.argtypes = [vp, vp, i32, i32, C.c_float, vp, vp, vp]
     L.gs_loss_dssim_static.restype = C.c_int
+    L.gs_ctx_set_tuning.argtypes = [vp, C.POINTER(gs_tuning)]
+    L.gs_ctx_get_tuning.argtypes = [vp, C.POINTER(gs_tuning)]
+    L.gs_autotune.argtypes = [vp, vp, vp, i32, C.POINTER(gs_view), vp, C.POINTER(gs_render_opts), vp,
+                              C.POINTER(gs_loss), C.POINTER(gs_grads), vp, i32, C.POINTER(gs_tuning),
+                              C.POINTER(C.c_double), vp]
+    for name in ("gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune"):
+        getattr(L, name).restype = C.c_int
     L.gs_gaussian_adam.argtypes = [vp, i64, i32, C.POINTER(gs_raw_params), vp, vp, C.POINTER(gs_grads), vp, vp,
                                    C.POINTER(gs_gaussian_lrs), C.c_float, C.c_float, C.c_float, i32, vp]
     L.gs_gaussian_adam.restype = C.c_int
@@ -355,6 +366,27 @@ def gs_server_stats_get(srv: int) -> dict:
 
 def gs_server_destroy(srv: int) -> None:
     load().gs_server_destroy(C.c_void_p(srv))
+
+
+def gs_ctx_set_tuning(ctx: int, scatter_chunk: int, sort_chunk: int, preprocess_threads: int) -> None:
+    t = gs_tuning(int(scatter_chunk), int(sort_chunk), int(preprocess_threads))
+    _ck(load().gs_ctx_set_tuning(C.c_void_p(ctx), C.byref(t)))
+
+
+def gs_ctx_get_tuning(ctx: int) -> dict:
+    t = gs_tuning()
+    _ck(load().gs_ctx_get_tuning(C.c_void_p(ctx), C.byref(t)))
+    return {k: getattr(t, k) for k, _ in gs_tuning._fields_}
+
+
+def gs_autotune(ctx: int, fr: int, scene: int, views_arr, n_views: int, poses, opts: gs_render_opts, image,
+                loss: gs_loss, grads: gs_grads | None, pose_grad, repeats: int = 2, stream=None):
+    best = gs_tuning()
+    ms = C.c_double(0.0)
+    _ck(load().gs_autotune(C.c_void_p(ctx), C.c_void_p(fr), C.c_void_p(scene), int(n_views), views_arr, _ptr(poses),
+                           C.byref(opts), _ptr(image), C.byref(loss), C.byref(grads) if grads is not None else None,
+                           _ptr(pose_grad), int(repeats), C.byref(best), C.byref(ms), _stream(stream)))
+    return {k: getattr(best, k) for k, _ in gs_tuning._fields_}, ms.value
 
 
 def gs_status(ctx: int, stream=None) -> int:

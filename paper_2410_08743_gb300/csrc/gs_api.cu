@@ -77,6 +77,7 @@ struct gs_ctx {
     double prof_ms[PK_COUNT] = {};
     long long prof_n[PK_COUNT] = {};
     long long launches = 0;         // kernels launched by this context
+    gs_tuning tune{4096, 2048, 256};  // result-neutral launch parameters
 };
 
 static cudaEvent_t pool_event(gs_ctx* c) {
@@ -609,13 +610,13 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
         {
             PROF(PK_PRE_FWD, 1);
-            gs::launch_preprocess_fwd(scene->d, nv, fr->vdev.p + v0, rp, spc, nullptr, s);
+            gs::launch_preprocess_fwd(scene->d, ctx->tune.preprocess_threads, nv, fr->vdev.p + v0, rp, spc, nullptr, s);
         }
         CK_LAUNCH();
     }
     {
         PROF(PK_COUNT_TILES, 1);
-        gs::launch_count_tiles(n, n_views, fr->vdev.p, sp.rect, fr->counts.p, s);
+        gs::launch_count_tiles(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp.rect, fr->counts.p, s);
     }
     CK_LAUNCH();
     {
@@ -633,7 +634,8 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     const uint32_t cap = (uint32_t)std::min<size_t>(fr->keys.cap, 0xffffffffu);
     {
         PROF(PK_SCATTER, 1);
-        gs::launch_scatter_keys(n, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p, fr->keys.p, cap, ctx->status, s);
+        gs::launch_scatter_keys(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p, fr->keys.p, cap,
+                                ctx->status, s);
     }
     CK_LAUNCH();
     fr->full_sort = (opts->flags & GS_F_FULL_SORT) != 0;
@@ -653,7 +655,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         CK_LAUNCH();
     } else {
         PROF(PK_BLEND_FWD, 1);
-        gs::launch_blend_fwd_lazy(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
+        gs::launch_blend_fwd_lazy(T, ctx->tune.sort_chunk, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
                                   fr->tmp_keys.p, fr->sorted_idx.p, fr->sorted_count.p, cap, image, fr->T_final.p,
                                   fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
         CK_LAUNCH();
@@ -674,6 +676,21 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
     if (!ctx || !fr || !opts || !loss) return fail(GS_EINVAL, "NULL ctx/frames/opts/loss");
     int rc;
     if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
+    if (opts->flags & GS_F_RECOMPUTE) {
+        // rebuild the forward state of these views in fr (into scratch image storage)
+        long long n_img = 0;
+        for (int v = 0; v < n_views; v++) {
+            const long long end = (img_offs ? img_offs[v] : n_img) + 3LL * views[v].width * views[v].height;
+            n_img = img_offs ? std::max(n_img, end) : end;
+        }
+        if ((rc = fr->st_image.ensure(std::max<long long>(n_img, 1), !(opts->flags & GS_F_NO_SYNC), "recompute image")))
+            return rc;
+        gs_render_opts o2 = *opts;
+        o2.flags &= ~(uint32_t)GS_F_RECOMPUTE;
+        if ((rc = gs::render_forward_impl(ctx, scene, n_views, views, img_offs, poses, &o2, fr, fr->st_image.p, nullptr,
+                                          nullptr, s)))
+            return rc;
+    }
     if (!fr->have_forward || fr->n_views != n_views || fr->n != scene->d.n || !fr->cur ||
         !same_views(fr->views_host, n_views, views) || !same_offs(fr->cur->offs, n_views, img_offs))
         return fail(GS_EINVAL, "backward does not match the frames' last forward");
@@ -918,6 +935,70 @@ int gs_status(gs_ctx* ctx, void* stream) {
     const int st = *reinterpret_cast<int*>(ctx->pinned);
     if (st & GS_DEV_OVERFLOW) return fail(GS_EOVERFLOW, "a key buffer overflowed in no-sync mode");
     if (st) return fail(GS_ECUDA, "device status 0x%x", st);
+    return GS_OK;
+}
+
+int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
+    if (!ctx || !t) return fail(GS_EINVAL, "NULL argument");
+    if (t->scatter_chunk < 256 || t->scatter_chunk > 65536 || (t->scatter_chunk & (t->scatter_chunk - 1)))
+        return fail(GS_EINVAL, "scatter_chunk must be a power of two in [256, 65536]");
+    if (t->sort_chunk != 1024 && t->sort_chunk != 2048) return fail(GS_EINVAL, "sort_chunk must be 1024 or 2048");
+    if (t->preprocess_threads != 128 && t->preprocess_threads != 256)
+        return fail(GS_EINVAL, "preprocess_threads must be 128 or 256");
+    ctx->tune = *t;
+    return GS_OK;
+}
+
+int gs_ctx_get_tuning(gs_ctx* ctx, gs_tuning* t) {
+    if (!ctx || !t) return fail(GS_EINVAL, "NULL argument");
+    *t = ctx->tune;
+    return GS_OK;
+}
+
+int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, const gs_view* views,
+                const double* poses, const gs_render_opts* opts, float* image, const gs_loss* loss, gs_grads* grads,
+                double* pose_grad, int repeats, gs_tuning* best, double* best_ms, void* stream) {
+    if (!ctx || !fr || !opts || !loss || !best) return fail(GS_EINVAL, "NULL argument");
+    if (repeats < 1) return fail(GS_EINVAL, "repeats must be >= 1");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const gs_tuning saved = ctx->tune;
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int chunks[] = {1024, 2048, 4096, 8192};
+    const int sorts[] = {1024, 2048};
+    const int threads[] = {128, 256};
+    double bms = 1e300;
+    gs_tuning bt = saved;
+    int rc = GS_OK;
+    for (int a : chunks)
+        for (int b : sorts)
+            for (int c : threads) {
+                ctx->tune = gs_tuning{a, b, c};
+                for (int r = 0; r <= repeats && rc == GS_OK; r++) {
+                    if (r == 1) cudaEventRecord(e0, s);
+                    rc = gs_render_forward(ctx, scene, n_views, views, poses, opts, fr, image, nullptr, nullptr, stream);
+                    if (rc == GS_OK)
+                        rc = gs_render_backward(ctx, scene, n_views, views, poses, opts, fr, image, loss, grads,
+                                                pose_grad, stream);
+                }
+                if (rc != GS_OK) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / repeats < bms) { bms = ms / repeats; bt = ctx->tune; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof = prof;
+    if (rc != GS_OK) { ctx->tune = saved; return rc; }
+    ctx->tune = bt;
+    *best = bt;
+    if (best_ms) *best_ms = bms;
     return GS_OK;
 }
 

@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
 // sorted runs is exactly the (depth, index) order, so the image equals the one
 // of a fully sorted list.  The sorted prefix and its length go to sorted_idx /
 // sorted_count for the backward pass, which never reads past it.
-#define LZ_CAP 2048
 #define LZ_NB 1024
 #define LZ_T GS_TILE_PIX
 
+template <int LZ_CAP>
 struct LazySmem {
     union {
         struct {
@@ -216,6 +216,7 @@ struct LazySmem {
     unsigned char wl[LZ_T / 32][BATCH];  // per-warp compacted batch entries
 };
 
+template <int LZ_CAP>
 __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
                                                          const ViewDev* __restrict__ views, RenderParams rp,
                                                          SplatArrays sp, int n, const uint32_t* __restrict__ starts,
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
                                                          float* __restrict__ tile_loss,
                                                          unsigned long long* __restrict__ counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LazySmem& sm = *reinterpret_cast<LazySmem*>(smem_raw);
+    LazySmem<LZ_CAP>& sm = *reinterpret_cast<LazySmem<LZ_CAP>*>(smem_raw);
     __shared__ float s_red[LZ_T / 32];
     __shared__ uint32_t s_warp[LZ_T / 32];
     __shared__ uint32_t s_mm[2];
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
     }
 }
 
-void launch_blend_fwd_lazy(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int n_views, const int* tile_base, const ViewDev* views,
                            const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
                            unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
                            uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
@@ -438,12 +439,20 @@ void launch_blend_fwd_lazy(int n_tiles, int n_views, const int* tile_base, const
     if (n_tiles <= 0) return;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_blend_fwd_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LazySmem));
+        cudaFuncSetAttribute(k_blend_fwd_lazy<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LazySmem<1024>));
+        cudaFuncSetAttribute(k_blend_fwd_lazy<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LazySmem<2048>));
         attr = true;
     }
-    k_blend_fwd_lazy<<<n_tiles, LZ_T, sizeof(LazySmem), s>>>(n_views, tile_base, views, rp, sp, n, starts, keys, tmp,
-                                                             sorted_idx, sorted_count, cap, image, T_final, n_contrib,
-                                                             target, tile_loss, counters);
+    if (sort_chunk <= 1024)
+        k_blend_fwd_lazy<1024><<<n_tiles, LZ_T, sizeof(LazySmem<1024>), s>>>(
+            n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
+            n_contrib, target, tile_loss, counters);
+    else
+        k_blend_fwd_lazy<2048><<<n_tiles, LZ_T, sizeof(LazySmem<2048>), s>>>(
+            n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
+            n_contrib, target, tile_loss, counters);
 }
 
 void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,

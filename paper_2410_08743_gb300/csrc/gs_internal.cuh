@@ -102,17 +102,17 @@ namespace gs {
 void launch_setup_views(const gs_view* dummy, int n_views, const double* poses, ViewDev* views_dev,
                         const RenderParams& rp, cudaStream_t s);
 
-void launch_preprocess_fwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
+void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, uint32_t* tile_counts, cudaStream_t s);
 
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t scan_tmp_bytes(int n);
 
-void launch_scatter_keys(int n, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
+void launch_scatter_keys(int n, int chunk, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
                          uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s);
 
-void launch_count_tiles(int n, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
-                        cudaStream_t s);
+void launch_count_tiles(int n, int chunk, int n_views, const ViewDev* views, const uint2* rect,
+                        uint32_t* tile_counts, cudaStream_t s);
 
 // lists: [3][n_tiles] work lists; counters: 6 words (list lengths, work cursors)
 void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys,
@@ -125,7 +125,7 @@ void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const View
                       uint32_t* n_contrib, const float* target, float* tile_loss, unsigned long long* counters,
                       cudaStream_t s);
 
-void launch_blend_fwd_lazy(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int n_views, const int* tile_base, const ViewDev* views,
                            const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
                            unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
                            uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,

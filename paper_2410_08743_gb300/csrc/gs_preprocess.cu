@@ -325,10 +325,10 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views
     }
 }
 
-void launch_preprocess_fwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
+void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, uint32_t* tile_counts, cudaStream_t s) {
     if (sc.n <= 0 || n_views <= 0) return;
-    const int T = 256;
+    const int T = threads == 128 ? 128 : 256;
     const int grid = (sc.n + T - 1) / T;
     const size_t sm = sizeof(ViewDev) * (size_t)n_views;
     switch (sc.sh_degree) {

@@ -105,14 +105,13 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t
 }
 
 // ------------------------------------------------------------ count + scatter
-// One CTA per (view, chunk of CHUNK Gaussians).  The CTA first builds a
+// One CTA per (view, chunk of `chunk` Gaussians; a tuning knob).  The CTA first builds a
 // shared-memory histogram of its keys over the view's tiles, so that global
 // atomics go per (CTA, tile) instead of per key:
 //   count:   tile_counts[t] += hist[t]
 //   scatter: base = cursor[t] += hist[t]; each key takes starts[t] + base + a
 //            shared-memory slot.
 // Views with more than SMEM_TILES tiles fall back to one global atomic per key.
-#define CHUNK 4096
 #define SMEM_TILES 8192
 #define CS_THREADS 256
 
@@ -144,13 +143,13 @@ __device__ __forceinline__ void chunk_histogram(const uint2* __restrict__ rect, 
     }
 }
 
-__global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, const ViewDev* __restrict__ views,
+__global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, int chunk, const ViewDev* __restrict__ views,
                                                            const uint2* __restrict__ rect,
                                                            uint32_t* __restrict__ tile_counts) {
     __shared__ uint32_t hist[SMEM_TILES];
     const int v = blockIdx.y;
     const int gw = views[v].gw, ntile = gw * views[v].gh, tb = views[v].tile_base;
-    const int i0 = blockIdx.x * CHUNK, i1 = min(n, i0 + CHUNK);
+    const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
     const size_t vb = (size_t)v * n;
     if (ntile > SMEM_TILES) {
         for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS) {
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, const ViewDev
         if (hist[t]) atomicAdd(tile_counts + tb + t, hist[t]);
 }
 
-__global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewDev* __restrict__ views,
+__global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, const ViewDev* __restrict__ views,
                                                              const uint2* __restrict__ rect,
                                                              const float* __restrict__ depth,
                                                              const uint32_t* __restrict__ starts,
@@ -180,7 +179,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewD
     __shared__ int s_over;
     const int v = blockIdx.y;
     const int gw = views[v].gw, ntile = gw * views[v].gh, tb = views[v].tile_base;
-    const int i0 = blockIdx.x * CHUNK, i1 = min(n, i0 + CHUNK);
+    const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
     const size_t vb = (size_t)v * n;
     if (threadIdx.x == 0) s_over = 0;
     if (ntile > SMEM_TILES) {
@@ -237,18 +236,18 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, const ViewD
     if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
 }
 
-void launch_count_tiles(int n, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
+void launch_count_tiles(int n, int chunk, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
                         cudaStream_t s) {
     if (n <= 0 || n_views <= 0) return;
-    dim3 grid((n + CHUNK - 1) / CHUNK, n_views);
-    k_count_tiles<<<grid, CS_THREADS, 0, s>>>(n, views, rect, tile_counts);
+    dim3 grid((n + chunk - 1) / chunk, n_views);
+    k_count_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, rect, tile_counts);
 }
 
-void launch_scatter_keys(int n, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
+void launch_scatter_keys(int n, int chunk, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
                          uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s) {
     if (n <= 0 || n_views <= 0) return;
-    dim3 grid((n + CHUNK - 1) / CHUNK, n_views);
-    k_scatter_tiles<<<grid, CS_THREADS, 0, s>>>(n, views, sp.rect, sp.depth, starts, cursor, keys, cap, status);
+    dim3 grid((n + chunk - 1) / chunk, n_views);
+    k_scatter_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, sp.rect, sp.depth, starts, cursor, keys, cap, status);
 }
 
 // ------------------------------------------------------------ segment sort

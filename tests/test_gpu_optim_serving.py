@@ -241,3 +241,43 @@ def test_cuda_graph_capture_of_fwd_bwd_and_pose_step(R):
     finally:
         r.set_flags(0)
         r.close()
+
+
+def test_tuning_is_result_neutral_and_autotune_caches(R, tmp_path):
+    from paper_2410_08743_gb300 import tune
+    sc = synth.make_scene_box(61, 40000, sh_degree=2, lo=(-1.2, -0.9, 3.0), hi=(1.2, 0.9, 6.0))
+    views = [synth.intrinsics(96, 72), synth.intrinsics(40, 30), synth.intrinsics(160, 120)]
+    rng = np.random.default_rng(61)
+    poses = np.stack([synth.perturb_normal(rng, synth.pose_from_center(np.eye(3), np.zeros(3)), 2.0, 0.05)
+                      for _ in views])
+    p = to_dev(sc)
+    P = poses_dev(poses)
+    n_img = Renderer.image_numel(views)
+    dldc = torch.from_numpy((rng.standard_normal(n_img) * 1e-3).astype(np.float32)).to(DEV)
+    outs = []
+    try:
+        for t in ((4096, 2048, 256), (1024, 1024, 128), (8192, 1024, 256), (2048, 2048, 128)):
+            L.gs_ctx_set_tuning(R.ctx, *t)
+            img = R.forward(p, views, P).clone()
+            g = zero_grads(p)
+            pg = torch.zeros(len(views), 6, dtype=torch.float64, device=DEV)
+            R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_DLDC, dl_dimage=dldc), g, pg)
+            torch.cuda.synchronize()
+            outs.append((img.cpu().numpy(), {k: v.cpu().numpy() for k, v in g.items()}, pg.cpu().numpy()))
+        for img, g, pg in outs[1:]:
+            assert np.array_equal(img, outs[0][0])
+            for k in g:
+                np.testing.assert_allclose(g[k], outs[0][1][k], rtol=1e-4, atol=1e-9)
+            np.testing.assert_allclose(pg, outs[0][2], rtol=1e-6, atol=1e-12)
+        with pytest.raises(L.GsError):
+            L.gs_ctx_set_tuning(R.ctx, 3000, 2048, 256)
+        img = torch.empty(n_img, device=DEV)
+        loss = L.make_loss(L.GS_LOSS_DLDC, dl_dimage=dldc)
+        cache = str(tmp_path / "tuning.json")
+        r1 = tune.autotune(R, p, views, P, img, loss, repeats=1, cache_path=cache)
+        assert not r1["cached"] and r1["tuning"]["sort_chunk"] in (1024, 2048)
+        assert L.gs_ctx_get_tuning(R.ctx) == r1["tuning"]
+        r2 = tune.autotune(R, p, views, P, img, loss, repeats=1, cache_path=cache)
+        assert r2["cached"] and r2["tuning"] == r1["tuning"]
+    finally:
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256)

@@ -376,3 +376,33 @@ def test_invalid_arguments_raise(R):
     with pytest.raises(L.GsError):
         R.backward(p, views, poses_dev(poses), torch.zeros(10, device=DEV),
                    L.make_loss(L.GS_LOSS_L1, target=None), None, None)
+
+
+def test_recompute_in_backward_equals_stored_state(R):
+    """A backward with GS_F_RECOMPUTE after another batch's forward gives the
+    gradients of the plain forward/backward pair."""
+    scA, viewsA, posesA = _ragged_case(71, 4000, 3)
+    viewsB = [dict(fx=70.0, fy=70.0, cx=50.0, cy=40.0, width=100, height=80)]
+    posesB = synth.pose_from_center(np.eye(3), np.array([0.1, 0.0, 0.0]))[None]
+    p = to_dev(scA)
+    PA, PB = poses_dev(posesA), poses_dev(posesB)
+    rng = np.random.default_rng(71)
+    imgA = R.forward(p, viewsA, PA).clone()
+    dldc = torch.from_numpy((rng.standard_normal(imgA.numel()) * 1e-3).astype(np.float32)).to(DEV)
+    loss = L.make_loss(L.GS_LOSS_DLDC, dl_dimage=dldc)
+    g1 = zero_grads(p); pg1 = torch.zeros(len(viewsA), 6, dtype=torch.float64, device=DEV)
+    R.backward(p, viewsA, PA, imgA, loss, g1, pg1)
+    R.forward(p, viewsB, PB)                       # the frames now hold batch B
+    with pytest.raises(L.GsError):                 # a plain backward of A is refused
+        R.backward(p, viewsA, PA, imgA, loss, zero_grads(p), None)
+    g2 = zero_grads(p); pg2 = torch.zeros_like(pg1)
+    R.opts.flags = L.GS_F_RECOMPUTE
+    try:
+        R.backward(p, viewsA, PA, imgA, loss, g2, pg2)
+    finally:
+        R.opts.flags = 0
+    torch.cuda.synchronize()
+    for k in g1:
+        torch.testing.assert_close(g2[k], g1[k], rtol=1e-4, atol=1e-9)
+    # the pose reduction sums float atomics, whose order differs run to run
+    torch.testing.assert_close(pg2, pg1, rtol=1e-4, atol=1e-6 * float(pg1.abs().max()))
