@@ -342,8 +342,10 @@ enum {
     GS_Q_SORTED_IDX = 5,      /* uint32 [keys]: Gaussian index per sorted key */
     GS_Q_T_FINAL = 6,         /* float [pixels]: final transmittance */
     GS_Q_N_CONTRIB = 7,       /* uint32 [pixels]: 1 + last blended list position in the tile */
-    GS_Q_MEAN2D = 8,          /* float [V*N][2]: projected mean (0 where culled) */
-    GS_Q_SPLAT = 9,           /* float [V*N][9]: mu_hat(2), conic(3), opacity, colour(3) */
+    GS_Q_MEAN2D = 8,          /* float [V*N][2]: FP32 key-path projected mean that decides the
+                                 tile rectangle (0 where culled) */
+    GS_Q_SPLAT = 9,           /* float [V*N][9]: mu_hat(2) as blended (exact to ~1e-9 px, then
+                                 rounded to float), conic(3), opacity, colour(3) */
     GS_Q_SORTED_COUNT = 10    /* uint32 [tiles]: length of each tile's sorted prefix */
 };
 int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* size_out);

@@ -193,6 +193,7 @@ struct gs_frames {
     DevBuf<float4> A, B, gA, gB;
     DevBuf<float> Cb, depth, gC;
     DevBuf<uint2> rect;
+    DevBuf<float2> Mlo;
     DevBuf<int> radius;
     // per tile
     DevBuf<uint32_t> counts, starts, cursor, scan_tmp, sort_lists, sort_counters, sorted_count;
@@ -216,7 +217,7 @@ struct gs_frames {
 
     SplatArrays splats() {
         SplatArrays s;
-        s.A = A.p; s.B = B.p; s.Cb = Cb.p; s.rect = rect.p; s.depth = depth.p; s.radius = radius.p;
+        s.A = A.p; s.Mlo = Mlo.p; s.B = B.p; s.Cb = Cb.p; s.rect = rect.p; s.depth = depth.p; s.radius = radius.p;
         return s;
     }
     Grad2DArrays g2d() {
@@ -229,7 +230,7 @@ struct gs_frames {
         for (auto* b : f4) b->release();
         DevBuf<float>* f1[] = {&Cb, &depth, &gC, &tile_loss, &T_final, &dldc_ssim, &ssim_tmp};
         for (auto* b : f1) b->release();
-        rect.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
+        rect.release(); Mlo.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
         sort_lists.release(); sort_counters.release(); sorted_count.release();
         keys.release(); tmp_keys.release(); sorted_idx.release(); n_contrib.release(); pose_partials.release();
         loss_tmp.release(); counters.release();
@@ -378,7 +379,8 @@ static int upload_views(gs_frames* fr, int n_views, const gs_view* views, const 
 
 static int ensure_pair_buffers(gs_frames* fr, size_t vn, bool grow) {
     int rc;
-    if ((rc = fr->A.ensure(vn, grow, "splat A")) || (rc = fr->B.ensure(vn, grow, "splat B")) ||
+    if ((rc = fr->A.ensure(vn, grow, "splat A")) || (rc = fr->Mlo.ensure(vn, grow, "splat Mlo")) ||
+        (rc = fr->B.ensure(vn, grow, "splat B")) ||
         (rc = fr->Cb.ensure(vn, grow, "splat Cb")) || (rc = fr->rect.ensure(vn, grow, "splat rect")) ||
         (rc = fr->depth.ensure(vn, grow, "splat depth")) || (rc = fr->radius.ensure(vn, grow, "splat radius")))
         return rc;
@@ -1126,9 +1128,11 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         return GS_OK;
     }
     std::vector<float4> a(vn), b(vn);
+    std::vector<float2> lo(vn);
     std::vector<float> c(vn);
     if (vn) {
         CK(cudaMemcpy(a.data(), fr->A.p, vn * sizeof(float4), cudaMemcpyDeviceToHost));
+        if (what == GS_Q_SPLAT) CK(cudaMemcpy(lo.data(), fr->Mlo.p, vn * sizeof(float2), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(b.data(), fr->B.p, vn * sizeof(float4), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(c.data(), fr->Cb.p, vn * sizeof(float), cudaMemcpyDeviceToHost));
     }
@@ -1138,7 +1142,7 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         if (what == GS_Q_MEAN2D) {
             o[2 * k] = ok ? a[k].x : 0.f; o[2 * k + 1] = ok ? a[k].y : 0.f;
         } else {
-            float r[9] = {a[k].x, a[k].y, a[k].z, a[k].w, b[k].x, b[k].y, b[k].z, b[k].w, c[k]};
+            float r[9] = {a[k].x + lo[k].x, a[k].y + lo[k].y, a[k].z, a[k].w, b[k].x, b[k].y, b[k].z, b[k].w, c[k]};
             for (int j = 0; j < 9; j++) o[9 * k + j] = ok ? r[j] : 0.f;
         }
     }

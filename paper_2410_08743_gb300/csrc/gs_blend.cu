@@ -31,14 +31,30 @@ struct SplatBatch {
 // ellipse d^T Q d <= R^2 with R^2 = 2 ln(o / alpha_min): |dx| <= R sqrt(Q^-1_xx),
 // |dy| <= R sqrt(Q^-1_yy), widened by 1% + 0.01 px (far above the FP32 error
 // of the alpha test), so a pixel outside the box is certainly skipped by
-// pair_alpha and the box changes no decision.  Near-singular conics get no box.
+// pair_alpha and the box changes no decision.  Conics with det < 1e-4 a c get
+// no box: there FP32 cancellation in det (relative error ~1e-7 a c / det)
+// could approach the 1% margin.
 __device__ __forceinline__ float2 alpha_box(const float4 a, const float4 b, float amin) {
     if (!(b.y >= amin)) return make_float2(-1.0f, -1.0f);
     const float R2 = 2.0f * logf(b.y / amin);
     const float dq = a.z * b.x - a.w * a.w;
-    if (!(dq > 1e-6f * a.z * b.x)) return make_float2(INFINITY, INFINITY);
+    if (!(dq > 1e-4f * a.z * b.x)) return make_float2(INFINITY, INFINITY);
     const float hx = sqrtf(R2 * b.x / dq), hy = sqrtf(R2 * a.z / dq);
     return make_float2(fmaf(hx, 1.01f, 0.01f), fmaf(hy, 1.01f, 0.01f));
+}
+
+// Splat record A of entry k with its projected mean moved to the tile origin
+// (ox, oy) and corrected by the residual Mlo.  A.x - ox is exact whenever the
+// FP32 mean lies within a factor of two of the origin (or ox = 0); otherwise it
+// is off by at most half an ulp of an offset far larger than the tile, where the
+// splat's alpha varies slowly.  So the staged mean keeps ~1e-9 px where it
+// matters, and pixel offsets in the tile are small exact integers.
+__device__ __forceinline__ float4 stage_mean(const SplatArrays& sp, size_t k, float ox, float oy) {
+    float4 a = sp.A[k];
+    const float2 lo = sp.Mlo[k];
+    a.x = __fadd_rn(__fsub_rn(a.x, ox), lo.x);
+    a.y = __fadd_rn(__fsub_rn(a.y, oy), lo.y);
+    return a;
 }
 
 // Per-warp compaction of a staged batch: the entries (in order) whose alpha
@@ -103,7 +119,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
     const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
     const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
     const bool inside = px < W && py < H;
-    const float fpx = (float)px, fpy = (float)py;
+    // tile-relative pixel coordinates (the staged means are moved to the same origin)
+    const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
+    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -117,7 +135,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
         if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)min((uint32_t)BATCH, e - base));
         if (j < e) {
             const size_t k = vbase + sorted_idx[j];
-            const float4 a = sp.A[k], b = sp.B[k];
+            const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
             sb.A[threadIdx.x] = a;
             sb.B[threadIdx.x] = b;
             sb.Cb[threadIdx.x] = sp.Cb[k];
@@ -242,7 +260,9 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
     const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
     const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
     const bool inside = px < W && py < H;
-    const float fpx = (float)px, fpy = (float)py;
+    // tile-relative pixel coordinates (the staged means are moved to the same origin)
+    const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
+    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -262,7 +282,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             n_read += (threadIdx.x == 0) ? min((uint32_t)BATCH, p1 - base) : 0u;
             if (j < p1) {
                 const size_t k = vbase + sorted_idx[s + j];
-                const float4 a = sp.A[k], b = sp.B[k];
+                const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
                 sm.u.sb.A[threadIdx.x] = a;
                 sm.u.sb.B[threadIdx.x] = b;
                 sm.u.sb.Cb[threadIdx.x] = sp.Cb[k];
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             const int cnt = (int)min((uint32_t)BATCH, p1 - base);
             unsigned char* wl = sm.wl[threadIdx.x >> 5];
             const int nw = warp_compact(sm.u.sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
-                                        (float)((lt / gw) * GS_TILE + 2 * ((threadIdx.x >> 5))), wl);
+                                        (float)(2 * (threadIdx.x >> 5)), wl);
             if (!done) {
                 for (int q = 0; q < nw; q++) {
                     const int jj = wl[q];
@@ -496,7 +516,7 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
+__global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
                                                            const ViewDev* __restrict__ views, RenderParams rp,
                                                            SplatArrays sp, int n, const uint32_t* __restrict__ starts,
                                                            const uint32_t* __restrict__ sorted_idx, uint32_t cap,
@@ -520,7 +540,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
     const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
     const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
     const bool inside = px < W && py < H;
-    const float fpx = (float)px, fpy = (float)py;
+    // tile-relative pixel coordinates (the staged means are moved to the same origin)
+    const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
+    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -585,7 +607,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
         if ((int)threadIdx.x < cnt) {
             const uint32_t id = sorted_idx[s + bstart + threadIdx.x];
             const size_t k = vbase + id;
-            const float4 a = sp.A[k], b = sp.B[k];
+            const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
             s_idx[threadIdx.x] = id;
             sb.A[threadIdx.x] = a;
             sb.B[threadIdx.x] = b;
@@ -596,7 +618,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_bwd(int n_views, const in
         __syncthreads();
         unsigned char* wl = s_wl[threadIdx.x >> 5];
         const int nw = warp_compact(sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
-                                    (float)((lt / gw) * GS_TILE + 2 * (threadIdx.x >> 5)), wl);
+                                    (float)(2 * (threadIdx.x >> 5)), wl);
         for (int q = nw - 1; q >= 0; q--) {
             const int jj = wl[q];
             const uint32_t pos = (uint32_t)(bstart + jj);

@@ -23,6 +23,7 @@ struct ViewDev {
     float oc[3];            // camera centre -R^T t (FP32)
     float limx, limy;       // frustum-clamp limits on x/z and y/z
     float inv_npix3;        // 1 / (3 H W)
+    float Rlo[9], tlo[3];   // pose - (Rf, tf): with them the pose is exact to ~2^-48
 };
 
 // Per-(view, Gaussian) splat record written by the forward preprocess.
@@ -31,8 +32,12 @@ struct ViewDev {
 //   Cb = colour.b
 //   rect = (x0 | y0 << 16, x1 | y1 << 16); x1 <= x0 marks a culled splat
 //   depth = key-path camera-space z
+//   Mlo = mu_hat - A.xy: the projected mean to ~1e-9 px is A.xy + Mlo, which
+//         the blends apply in tile-relative coordinates (A.xy itself is the
+//         FP32 key-path value that decides the tile rectangle)
 struct SplatArrays {
     float4* A;
+    float2* Mlo;
     float4* B;
     float* Cb;
     uint2* rect;

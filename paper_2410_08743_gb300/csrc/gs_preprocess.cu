@@ -23,8 +23,14 @@ __global__ void k_setup_views(int n_views, const double* __restrict__ poses, Vie
     if (v >= n_views) return;
     ViewDev vd = views[v];
     const double* P = poses + 12 * v;
-    for (int k = 0; k < 9; k++) vd.Rf[k] = __double2float_rn(P[k]);
-    for (int k = 0; k < 3; k++) vd.tf[k] = __double2float_rn(P[9 + k]);
+    for (int k = 0; k < 9; k++) {
+        vd.Rf[k] = __double2float_rn(P[k]);
+        vd.Rlo[k] = __double2float_rn(P[k] - (double)vd.Rf[k]);
+    }
+    for (int k = 0; k < 3; k++) {
+        vd.tf[k] = __double2float_rn(P[9 + k]);
+        vd.tlo[k] = __double2float_rn(P[9 + k] - (double)vd.tf[k]);
+    }
     for (int a = 0; a < 3; a++)
         vd.oc[a] = __double2float_rn(-(P[0 * 3 + a] * P[9] + P[1 * 3 + a] * P[10] + P[2 * 3 + a] * P[11]));
     if (clamp_factor > 0.0f) {
@@ -254,6 +260,52 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, const float c
     }
 }
 
+// ------------------------------------------------------------ precise mean
+// The projected mean mu_hat = f (x_c / z_c) + c evaluated with FP32 pairs
+// (value = hi + lo) built from the classical error-free transformations:
+// Knuth's TwoSum and the FMA-based TwoProduct (Dekker, Ogita-Rump-Oishi).
+// Relative error about 2^-44, against about 2^-22 for plain FP32: at 1280 px
+// a plain FP32 mu_hat is off by ~1e-4 px, which moves alpha near its 1/255
+// threshold by ~3e-4 relative and flips skip decisions.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// camera coordinate a of mu (exact FP32 inputs) under the split pose
+__device__ __forceinline__ void cam_coord_ff(const ViewDev& vd, int a, const float mu[3], float& hi, float& lo) {
+    float s = vd.tf[a], e = vd.tlo[a];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        float p, pe, se;
+        two_prod(vd.Rf[a * 3 + j], mu[j], p, pe);
+        two_sum(s, p, s, se);
+        e = __fadd_rn(e, __fadd_rn(__fadd_rn(pe, se), __fmul_rn(vd.Rlo[a * 3 + j], mu[j])));
+    }
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// f * (x / z) + c as a pair
+__device__ __forceinline__ void project_ff(float xh, float xl, float zh, float zl, float f, float c, float& hi,
+                                           float& lo) {
+    const float q = __fdiv_rn(xh, zh);
+    float p, pe;
+    two_prod(q, zh, p, pe);
+    const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(xh, p), pe), xl), __fmul_rn(q, zl));
+    const float ql = __fdiv_rn(r, zh);
+    float m, me, s, se;
+    two_prod(f, q, m, me);
+    me = __fmaf_rn(f, ql, me);
+    two_sum(m, c, s, se);
+    const float e = __fadd_rn(se, me);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
 // ------------------------------------------------------------ forward
 template <int D>
 __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
@@ -310,6 +362,15 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views
 #pragma unroll
             for (int b = 0; b < NC; b++) acc = fmaf(f[b * 3 + ch], Y[b], acc);
             col[ch] = fmaxf(acc, 0.0f);
+        }
+        {
+            float xh, xl, yh, yl, zh, zl, mxh, mxl, myh, myl;
+            cam_coord_ff(vd, 0, mu, xh, xl);
+            cam_coord_ff(vd, 1, mu, yh, yl);
+            cam_coord_ff(vd, 2, mu, zh, zl);
+            project_ff(xh, xl, zh, zl, vd.fx, vd.cx, mxh, mxl);
+            project_ff(yh, yl, zh, zl, vd.fy, vd.cy, myh, myl);
+            sp.Mlo[k] = make_float2(__fadd_rn(__fsub_rn(mxh, ko.mx), mxl), __fadd_rn(__fsub_rn(myh, ko.my), myl));
         }
         sp.A[k] = make_float4(ko.mx, ko.my, ca, cb);
         sp.B[k] = make_float4(cc, op, col[0], col[1]);

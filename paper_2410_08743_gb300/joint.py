@@ -1,0 +1,108 @@
+"""Joint refinement of Gaussians and camera poses (Sec. 3.3, Sec. 4.1).
+
+Each iteration renders a batch of views (one in the paper's setting), evaluates
+the photometric loss (w_l1 L1 + w_dssim D-SSIM, Eq. 16), back-propagates to
+every Gaussian parameter and to the views' poses in one fused library call
+(gs_step), then takes an Adam step on the raw Gaussian parameters
+(gs_gaussian_adam) and a tangent-space Adam step on the poses of the rendered
+views (gs_pose_step, T <- Exp(delta) T).  The camera learning rate follows a
+cosine schedule from lr_start to lr_end over the run (Sec. 4.1).
+
+Everything stays on the device; this module only holds the buffers and passes
+pointers (no CPU arithmetic on the path)."""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _lib as L
+from .render import Renderer
+
+DEFAULT_GAUSSIAN_LRS = dict(means=1.6e-4, scales=5e-3, quats=1e-3, opac=5e-2, sh_dc=2.5e-3, sh_rest=1.25e-4)
+
+
+def cosine_lr(it: int, total: int, lr_start: float, lr_end: float) -> float:
+    """Cosine decay from lr_start at it = 0 to lr_end at it = total - 1."""
+    if total <= 1:
+        return lr_start
+    c = 0.5 * (1.0 + math.cos(math.pi * min(it, total - 1) / (total - 1)))
+    return lr_end + (lr_start - lr_end) * c
+
+
+class JointRefiner:
+    """raw: device float32 tensors means [N,3], log_scales [N,3], quats [N,4],
+    logit_opac [N], sh [N,16,3]; poses: device float64 [V,12] (world->camera,
+    updated in place); targets: list of device float32 planar images, one per
+    view."""
+
+    def __init__(self, renderer: Renderer, raw: dict, sh_degree: int, views: list, poses: torch.Tensor,
+                 targets: list, w_l1: float = 0.8, w_dssim: float = 0.2, gaussian_lrs: dict | None = None,
+                 pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True):
+        self.r = renderer
+        self.raw = raw
+        self.deg = int(sh_degree)
+        self.views = views
+        self.poses = poses
+        self.targets = targets
+        self.w_l1, self.w_dssim = float(w_l1), float(w_dssim)
+        self.lrs = dict(DEFAULT_GAUSSIAN_LRS if gaussian_lrs is None else gaussian_lrs)
+        self.pose_lr = pose_lr
+        self.iterations = int(iterations)
+        self.refine_gaussians = refine_gaussians
+        dev = raw["means"].device
+        n = raw["means"].shape[0]
+        self.n = n
+        self.grads = {k: torch.zeros_like(raw[k2]) for k, k2 in
+                      (("means", "means"), ("scales", "log_scales"), ("quats", "quats"), ("opac", "logit_opac"),
+                       ("sh", "sh"))}
+        self.gm = torch.zeros(59 * n, device=dev)
+        self.gv = torch.zeros(59 * n, device=dev)
+        # activated parameters the renderer reads, written by the Adam kernel:
+        # a zero-learning-rate step with zero gradients only activates
+        self.scales = torch.empty_like(raw["log_scales"])
+        self.opac = torch.empty_like(raw["logit_opac"])
+        L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv,
+                           {k: 0.0 for k in self.lrs}, 1, self.deg)
+        V = len(views)
+        self.pm = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+        self.pv = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+        self.pose_steps = [0] * V
+        self.pose_grad = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+        self.loss = torch.zeros(V, dtype=torch.float64, device=dev)
+        self.image = {}
+        self.it = 0
+        self.gstep = 0
+
+    def _desc(self):
+        return L.scene_desc(self.raw["means"], self.scales, self.raw["quats"], self.opac, self.raw["sh"], self.deg)
+
+    def step(self, v: int) -> None:
+        """One iteration on view v: fused forward + loss + backward, then the
+        Gaussian and pose Adam steps.  Asynchronous on the current stream."""
+        view = self.views[v]
+        n3 = 3 * view["width"] * view["height"]
+        img = self.image.get(n3)
+        if img is None:
+            img = self.image[n3] = torch.empty(n3, device=self.raw["means"].device)
+        kind = L.GS_LOSS_L1_DSSIM if self.w_dssim != 0.0 else L.GS_LOSS_L1
+        loss = L.make_loss(kind, target=self.targets[v], w_l1=self.w_l1, w_dssim=self.w_dssim)
+        grads = L.make_grads(**self.grads) if self.refine_gaussians else None
+        pose = self.poses[v:v + 1]
+        pg = self.pose_grad[v:v + 1]
+        L.gs_step(self.r.ctx, self.r.frames, self._desc(), L.views_array([view]), 1, L._ptr(pose), self.r.opts,
+                  loss, L._ptr(img), grads, L._ptr(pg), L._ptr(self.loss[v:v + 1]))
+        if self.refine_gaussians:
+            self.gstep += 1
+            L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv, self.lrs,
+                               self.gstep, self.deg)
+        self.pose_steps[v] += 1
+        lr = cosine_lr(self.it, self.iterations, *self.pose_lr)
+        L.gs_pose_step(self.r.ctx, pose, self.pm[v:v + 1], self.pv[v:v + 1], pg, lr, self.pose_steps[v])
+        self.it += 1
+
+    def run(self, order=None) -> None:
+        """All iterations, cycling through the views (or in `order`)."""
+        V = len(self.views)
+        for k in range(self.iterations - self.it):
+            self.step(order[k % len(order)] if order is not None else (self.it % V))

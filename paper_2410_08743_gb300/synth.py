@@ -167,6 +167,26 @@ def joint_workload(seed: int = 2, n: int = 300_000, n_views: int = 20) -> dict:
                 init_poses=init[:n_views])
 
 
+def perturb_scene_raw(seed: int, scene: dict, means_std: float = 0.02, log_scale_std: float = 0.2,
+                      logit_opac_std: float = 0.5, sh_std: float = 0.05) -> dict:
+    """Raw (pre-activation) parameters of a perturbed copy of `scene`, the
+    starting point of a joint refinement: means + N(0, 0.02), log-scales
+    + N(0, 0.2), logit-opacities + N(0, 0.5), SH coefficients + N(0, 0.05);
+    quaternions unchanged.  Keys: means, log_scales, quats, logit_opac, sh."""
+    rng = _rng(seed)
+    n = len(scene["opac"])
+    o = np.clip(scene["opac"].astype(np.float64), 1e-6, 1 - 1e-6)
+    nc = (int(scene["sh_degree"]) + 1) ** 2
+    sh = scene["sh"].astype(np.float64).copy()
+    sh[:, :nc] += rng.normal(0.0, sh_std, (n, nc, 3))
+    return dict(means=(scene["means"] + rng.normal(0.0, means_std, (n, 3))).astype(np.float32),
+                log_scales=(np.log(scene["scales"].astype(np.float64)) + rng.normal(0.0, log_scale_std, (n, 3))
+                            ).astype(np.float32),
+                quats=scene["quats"].copy(),
+                logit_opac=(np.log(o / (1 - o)) + rng.normal(0.0, logit_opac_std, n)).astype(np.float32),
+                sh=sh.astype(np.float32))
+
+
 def batched_workload(seed: int = 3, n: int = 1_000_000, n_views: int = 64,
                      resolutions=RESOLUTIONS_MIXED, view_seed: int | None = None) -> dict:
     """1M SH3 Gaussians seen by 64 cameras of mixed resolution on a jittered
@@ -182,6 +202,86 @@ def batched_workload(seed: int = 3, n: int = 1_000_000, n_views: int = 64,
     target_poses = np.stack([perturb_normal(rng, p, 1.0, 0.02) for p in poses])
     return dict(scene=scene, views=views[:n_views], poses=poses[:n_views],
                 target_poses=target_poses[:n_views])
+
+
+def _box_surface_points(rng: np.random.Generator, n: int, lo, hi) -> np.ndarray:
+    """n points uniform on the surface of the axis-aligned box [lo, hi]."""
+    lo = np.asarray(lo, np.float64); hi = np.asarray(hi, np.float64)
+    e = hi - lo
+    areas = np.array([e[1] * e[2], e[1] * e[2], e[0] * e[2], e[0] * e[2], e[0] * e[1], e[0] * e[1]])
+    face = rng.choice(6, size=n, p=areas / areas.sum())
+    pts = rng.uniform(lo, hi, (n, 3))
+    axis = face // 2
+    side = np.where(face % 2 == 0, lo[axis], hi[axis])
+    pts[np.arange(n), axis] = side
+    return pts
+
+
+def make_scene_room(seed: int = 5, n: int = 3_000_000, sh_degree: int = 3,
+                    room=(6.0, 3.0, 8.0), n_boxes: int = 6, box_share: float = 0.25) -> dict:
+    """Room-scale scene: Gaussians on the walls, floor and ceiling of a
+    room x*y*z box centred at the origin and on the surfaces of n_boxes
+    furniture-like boxes standing on the floor (y = +room_y/2) near the
+    walls; log-scales N(log 0.006, 0.4)."""
+    rng = _rng(seed)
+    half = np.asarray(room, np.float64) / 2.0
+    n_box = int(n * box_share)
+    n_room = n - n_box
+    parts = [_box_surface_points(rng, n_room, -half, half)]
+    sizes = rng.uniform(0.3, 0.9, (n_boxes, 3))
+    areas = 2 * (sizes[:, 0] * sizes[:, 1] + sizes[:, 1] * sizes[:, 2] + sizes[:, 0] * sizes[:, 2])
+    counts = np.floor(n_box * areas / areas.sum()).astype(int)
+    counts[0] += n_box - counts.sum()
+    for k in range(n_boxes):
+        sx = (1 if k % 2 == 0 else -1) * (half[0] - 0.2 - sizes[k, 0] / 2)
+        cz = rng.uniform(-half[2] + 1.0, half[2] - 1.0)
+        c = np.array([sx, half[1] - sizes[k, 1] / 2, cz])
+        parts.append(_box_surface_points(rng, counts[k], c - sizes[k] / 2, c + sizes[k] / 2))
+    means = np.concatenate(parts)
+    scales = np.exp(rng.normal(math.log(0.006), 0.4, (n, 3)))
+    quats = random_unit_quats(rng, n)
+    opac = sigmoid_normal(rng, n)
+    sh = np.zeros((n, 16, 3), np.float32)
+    sh[:, 0, :] = rng.uniform(-DC_HALF_RANGE, DC_HALF_RANGE, (n, 3))
+    if sh_degree > 0:
+        ncoef = (sh_degree + 1) ** 2
+        sh[:, 1:ncoef, :] = 0.1 * rng.standard_normal((n, ncoef - 1, 3), dtype=np.float32)
+    return dict(means=means.astype(np.float32), scales=scales.astype(np.float32),
+                quats=quats, opac=opac, sh=sh, sh_degree=sh_degree)
+
+
+def spline_trajectory(rng: np.random.Generator, n_frames: int, n_ctrl: int = 8,
+                      xr=(-1.8, 1.8), yr=(-0.4, 0.4), zr=(-3.0, 3.0)) -> np.ndarray:
+    """World->camera poses [n_frames, 12] along a C2 (natural cubic) spline
+    through n_ctrl interior control points, each camera looking along the
+    path's tangent with its y axis close to world +y."""
+    from scipy.interpolate import CubicSpline
+    ctrl = np.stack([rng.uniform(xr[0], xr[1], n_ctrl), rng.uniform(yr[0], yr[1], n_ctrl),
+                     np.linspace(zr[0], zr[1], n_ctrl)], 1)
+    sp = CubicSpline(np.arange(n_ctrl), ctrl, bc_type="natural")
+    u = np.linspace(0.0, n_ctrl - 1, n_frames)
+    pos, tan = sp(u), sp(u, 1)
+    out = []
+    for c, d in zip(pos, tan):
+        z = d / np.linalg.norm(d)
+        x = np.cross(np.array([0.0, 1.0, 0.0]), z)
+        x /= np.linalg.norm(x)
+        y = np.cross(z, x)
+        out.append(pose_from_center(np.stack([x, y, z]), c))
+    return np.stack(out)
+
+
+def trajectory_workload(seed: int = 5, n: int = 3_000_000, n_frames: int = 200,
+                        width: int = 1280, height: int = 720, focal: float = 600.0) -> dict:
+    """Large trajectory refinement: a 3M-Gaussian SH3 room seen by n_frames
+    1280x720 cameras (fx = fy = 600) along a smooth spline; initial poses
+    off by N(0, 1 deg)/N(0, 0.02)."""
+    scene = make_scene_room(seed, n)
+    rng = _rng(seed + 1000)
+    poses = spline_trajectory(rng, n_frames)
+    views = [intrinsics(width, height, fx=focal) for _ in range(n_frames)]
+    init = np.stack([perturb_normal(rng, p, 1.0, 0.02) for p in poses])
+    return dict(scene=scene, views=views, poses=poses, init_poses=init)
 
 
 def serving_requests(seed: int = 4, n_requests: int = 2000, rate_hz: float = 200.0,
