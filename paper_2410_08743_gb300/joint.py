@@ -17,6 +17,7 @@ import math
 import torch
 
 from . import _lib as L
+from . import dist as D
 from .render import Renderer
 
 DEFAULT_GAUSSIAN_LRS = dict(means=1.6e-4, scales=5e-3, quats=1e-3, opac=5e-2, sh_dc=2.5e-3, sh_rest=1.25e-4)
@@ -34,11 +35,14 @@ class JointRefiner:
     """raw: device float32 tensors means [N,3], log_scales [N,3], quats [N,4],
     logit_opac [N], sh [N,16,3]; poses: device float64 [V,12] (world->camera,
     updated in place); targets: list of device float32 planar images, one per
-    view."""
+    view.  With a process group of several ranks each rank passes its own
+    views (dist.shard_views) and the same Gaussians; the Gaussian gradient is
+    summed over the ranks before the (identical) Adam step."""
 
     def __init__(self, renderer: Renderer, raw: dict, sh_degree: int, views: list, poses: torch.Tensor,
                  targets: list, w_l1: float = 0.8, w_dssim: float = 0.2, gaussian_lrs: dict | None = None,
-                 pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True):
+                 pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True,
+                 group=None):
         self.r = renderer
         self.raw = raw
         self.deg = int(sh_degree)
@@ -53,9 +57,11 @@ class JointRefiner:
         dev = raw["means"].device
         n = raw["means"].shape[0]
         self.n = n
-        self.grads = {k: torch.zeros_like(raw[k2]) for k, k2 in
-                      (("means", "means"), ("scales", "log_scales"), ("quats", "quats"), ("opac", "logit_opac"),
-                       ("sh", "sh"))}
+        # gradients in one flat buffer: with several ranks (each rendering its
+        # own views of the replicated Gaussians) it is summed in one all-reduce
+        self.group = group
+        self.flat = D.FlatGrads(n, dev)
+        self.grads = self.flat.as_dict()
         self.gm = torch.zeros(59 * n, device=dev)
         self.gv = torch.zeros(59 * n, device=dev)
         # activated parameters the renderer reads, written by the Adam kernel:
@@ -93,6 +99,7 @@ class JointRefiner:
         L.gs_step(self.r.ctx, self.r.frames, self._desc(), L.views_array([view]), 1, L._ptr(pose), self.r.opts,
                   loss, L._ptr(img), grads, L._ptr(pg), L._ptr(self.loss[v:v + 1]))
         if self.refine_gaussians:
+            D.allreduce_grads(self.flat, self.group)
             self.gstep += 1
             L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv, self.lrs,
                                self.gstep, self.deg)
