@@ -118,8 +118,12 @@ void gs_default_opts(gs_render_opts* opts);
 enum {
     GS_LOSS_DLDC = 0,         /* dl_dimage holds dL/dC directly */
     GS_LOSS_L1 = 1,           /* w_l1 * mean_{3HW} |C - target| per view (Eq. 16, L1 term) */
-    GS_LOSS_L1_DSSIM = 2      /* w_l1 * L1 + w_dssim * (1 - SSIM), 11x11 Gaussian window
+    GS_LOSS_L1_DSSIM = 2,     /* w_l1 * L1 + w_dssim * (1 - SSIM), 11x11 Gaussian window
                                  (Eq. 16 with beta = w_dssim) */
+    GS_LOSS_L1_MASKED = 3     /* confidence-masked L1 of pose estimation (Sec. 3.4, Eq. 20-21):
+                                 w_l1 * mean_{3HW} M |C - target| with the per-pixel mask
+                                 M = [accumulated alpha 1 - T_final > mask_alpha]; the mask is
+                                 piecewise constant, so it carries no gradient */
 };
 
 typedef struct {
@@ -128,6 +132,7 @@ typedef struct {
     const float* target;      /* device, packed like the image (L1 / D-SSIM) */
     const float* dl_dimage;   /* device, packed like the image (GS_LOSS_DLDC) */
     double* loss;             /* device [V], nullable: per-view loss values (written) */
+    float mask_alpha;         /* GS_LOSS_L1_MASKED threshold; 0 means the paper's 0.99 */
 } gs_loss;
 
 /* Per-Gaussian gradient outputs (device, same layouts as the parameters).
@@ -283,6 +288,8 @@ typedef struct {
     int32_t max_height;
     int64_t mem_budget;       /* device bytes the active solves' working set may use (0: no limit) */
     int32_t queue_capacity;   /* pending requests beyond which submit returns GS_EBUSY */
+    float mask_alpha;         /* 0: plain L1; > 0: confidence-masked L1 (GS_LOSS_L1_MASKED)
+                                 with this accumulated-alpha threshold (the paper uses 0.99) */
 } gs_server_config;
 
 typedef struct {

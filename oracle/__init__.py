@@ -65,6 +65,8 @@ def lib():
         L.or_backward.restype = C.c_int
         L.or_loss_l1.argtypes = [C.c_int, I32P, F64P, F32P, C.c_double, F64P, U8P]
         L.or_loss_l1.restype = C.c_double
+        L.or_loss_l1_masked.argtypes = [C.c_int, I32P, F64P, F32P, F64P, C.c_double, C.c_double, F64P, U8P]
+        L.or_loss_l1_masked.restype = C.c_double
         L.or_loss_dssim.argtypes = [C.c_int, I32P, F64P, F32P, C.c_double, F64P, F64P]
         L.or_loss_dssim.restype = C.c_double
         L.or_ssim_filter.argtypes = [F64P, C.c_int, C.c_int, F64P]
@@ -207,6 +209,22 @@ def loss_l1(views, image, target, weight=1.0):
     wh = _wh(views)
     L = lib().or_loss_l1(len(views), _p(wh, I32P), _p(img, F64P), _p(tgt, F32P), float(weight),
                          _p(d, F64P), _p(fr, U8P))
+    return L, d, fr
+
+
+def loss_l1_masked(views, image, target, T_final, mask_alpha=0.99, weight=1.0):
+    """Confidence-masked L1 (Sec. 3.4, Eq. 20-21).  mask_alpha is taken as an
+    FP32 number, the type the library's loss descriptor holds it in.  Returns
+    (loss, dL/dC f64, fragile_px u8)."""
+    img = np.ascontiguousarray(image, np.float64)
+    tgt = np.ascontiguousarray(target, np.float32)
+    T = np.ascontiguousarray(T_final, np.float64)
+    d = np.zeros_like(img)
+    fr = np.zeros(sum(v["width"] * v["height"] for v in views), np.uint8)
+    assert T.size == fr.size
+    wh = _wh(views)
+    L = lib().or_loss_l1_masked(len(views), _p(wh, I32P), _p(img, F64P), _p(tgt, F32P), _p(T, F64P),
+                                float(np.float32(mask_alpha)), float(weight), _p(d, F64P), _p(fr, U8P))
     return L, d, fr
 
 

@@ -1018,6 +1018,43 @@ double or_loss_l1(int V, const int* wh, const double* img, const float* target, 
     return total;
 }
 
+/* Sec. 3.4, Eq. 20-21: confidence-masked L1 for pose estimation.  The mask
+ * keeps a pixel when its accumulated alpha 1 - T_final (the sum of the blend
+ * weights, which the paper calls transmittances) exceeds mask_alpha.  Eq. 21
+ * prints a sum; read as the mean over 3HW with masked-out pixels counting 0,
+ * so that it has the scale of the unmasked L1.  The mask is piecewise
+ * constant in the parameters, so dL/dC = w M sign(C - I) / (3HW).
+ * fragile_px flags pixels whose mask decision lies within 1e-5 of the
+ * threshold, and kept pixels whose sign is in doubt. */
+double or_loss_l1_masked(int V, const int* wh, const double* img, const float* target, const double* T_final,
+                         double mask_alpha, double w, double* dldc, uint8_t* fragile_px) {
+    double total = 0.0;
+    size_t off = 0, poff = 0;
+    for (int v = 0; v < V; v++) {
+        size_t np = (size_t)wh[2 * v] * wh[2 * v + 1];
+        double m = 3.0 * (double)np, acc = 0.0;
+        for (int ch = 0; ch < 3; ch++)
+            for (size_t p = 0; p < np; p++) {
+                const double a = 1.0 - T_final[poff + p];
+                const int keep = a > mask_alpha;
+                if (fragile_px && fabs(a - mask_alpha) <= 1e-5) fragile_px[poff + p] = 1;
+                size_t k = off + ch * np + p;
+                double d = img[k] - (double)target[k];
+                if (!keep) {
+                    if (dldc) dldc[k] = 0.0;
+                    continue;
+                }
+                acc += fabs(d);
+                if (dldc) dldc[k] = d > 0 ? w / m : (d < 0 ? -w / m : 0.0);
+                if (fragile_px && d != 0.0 && fabs(d) < 1e-5) fragile_px[poff + p] = 1;
+            }
+        total += w * acc / m;
+        off += 3 * np;
+        poff += np;
+    }
+    return total;
+}
+
 /* Normalised 11-tap Gaussian window, sigma = 1.5 (the prior art's SSIM window). */
 static void ssim_window(double* g11) {
     double s = 0.0;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgsplat.so")
 GS_OK, GS_PENDING = 0, 1
 GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3, -4, -5, -6
 GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT, GS_F_RECOMPUTE = 1, 2, 4, 8
-GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM = 0, 1, 2
+GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM, GS_LOSS_L1_MASKED = 0, 1, 2, 3
 (GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
  GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT) = range(11)
 
@@ -55,7 +55,7 @@ class gs_render_opts(C.Structure):
 
 class gs_loss(C.Structure):
     _fields_ = [("kind", C.c_int32), ("w_l1", C.c_float), ("w_dssim", C.c_float), ("target", C.c_void_p),
-                ("dl_dimage", C.c_void_p), ("loss", C.c_void_p)]
+                ("dl_dimage", C.c_void_p), ("loss", C.c_void_p), ("mask_alpha", C.c_float)]
 
 
 class gs_grads(C.Structure):
@@ -79,7 +79,7 @@ class gs_gaussian_lrs(C.Structure):
 
 class gs_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_width", C.c_int32), ("max_height", C.c_int32),
-                ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32)]
+                ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32), ("mask_alpha", C.c_float)]
 
 
 class gs_solve_request(C.Structure):
@@ -283,8 +283,10 @@ def gs_step(ctx: int, fr: int, desc: gs_scene_desc, views_arr, n_views: int, pos
                        C.c_void_p(loss_out_ptr), _stream(stream)))
 
 
-def make_loss(kind: int, target=None, dl_dimage=None, w_l1: float = 1.0, w_dssim: float = 0.0, loss_out=None):
-    return gs_loss(int(kind), float(w_l1), float(w_dssim), _ptr(target), _ptr(dl_dimage), _ptr(loss_out))
+def make_loss(kind: int, target=None, dl_dimage=None, w_l1: float = 1.0, w_dssim: float = 0.0, loss_out=None,
+              mask_alpha: float = 0.0):
+    return gs_loss(int(kind), float(w_l1), float(w_dssim), _ptr(target), _ptr(dl_dimage), _ptr(loss_out),
+                   float(mask_alpha))
 
 
 def make_grads(means=None, scales=None, quats=None, opac=None, sh=None) -> gs_grads:
@@ -318,8 +320,9 @@ def gs_gaussian_adam(ctx: int, raw: dict, act_scales, act_opac, grads: dict, m, 
 
 
 def gs_server_create(device: int, scene: int, opts: gs_render_opts, max_slots: int, max_width: int, max_height: int,
-                     mem_budget: int = 0, queue_capacity: int = 65536) -> int:
-    cfg = gs_server_config(int(max_slots), int(max_width), int(max_height), int(mem_budget), int(queue_capacity))
+                     mem_budget: int = 0, queue_capacity: int = 65536, mask_alpha: float = 0.0) -> int:
+    cfg = gs_server_config(int(max_slots), int(max_width), int(max_height), int(mem_budget), int(queue_capacity),
+                           float(mask_alpha))
     h = C.c_void_p()
     _ck(load().gs_server_create(int(device), C.c_void_p(scene), C.byref(opts), C.byref(cfg), C.byref(h)))
     return h.value

@@ -699,9 +699,11 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
     if (n_views == 0) return GS_OK;
     if (!image) return fail(GS_EINVAL, "image is NULL");
     if (loss->kind == GS_LOSS_DLDC && !loss->dl_dimage) return fail(GS_EINVAL, "GS_LOSS_DLDC without dl_dimage");
-    if ((loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM) && !loss->target)
-        return fail(GS_EINVAL, "loss needs a target");
-    if (loss->kind < 0 || loss->kind > 2) return fail(GS_EINVAL, "unknown loss kind %d", loss->kind);
+    if (loss->kind < 0 || loss->kind > 3) return fail(GS_EINVAL, "unknown loss kind %d", loss->kind);
+    const bool l1_kind = loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM || loss->kind == GS_LOSS_L1_MASKED;
+    if (l1_kind && !loss->target) return fail(GS_EINVAL, "loss needs a target");
+    if (loss->kind == GS_LOSS_L1_MASKED && !(loss->mask_alpha >= 0.0f && loss->mask_alpha < 1.0f))
+        return fail(GS_EINVAL, "mask_alpha must lie in [0, 1)");
     const bool grow = !(opts->flags & GS_F_NO_SYNC);
     CK(cudaSetDevice(ctx->device));
     const int n = scene->d.n;
@@ -715,7 +717,12 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
     if ((rc = fr->pose_partials.ensure((size_t)std::max(nblk, 1) * n_views * 6 + 6, grow, "pose partials"))) return rc;
     const RenderParams rp = make_params(opts);
     const float* dldc = loss->dl_dimage;
-    const bool l1_loss = loss->loss && (loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM);
+    const bool l1_loss = loss->loss && l1_kind;
+    // the L1 term counts pixels whose final transmittance is below this bound
+    // (1 - mask_alpha for the masked loss; everything otherwise)
+    const float l1_mask_t = loss->kind == GS_LOSS_L1_MASKED
+                                ? 1.0f - (loss->mask_alpha > 0.0f ? loss->mask_alpha : 0.99f)
+                                : 2.0f;
     if (loss->kind == GS_LOSS_L1_DSSIM) {
         if ((rc = fr->dldc_ssim.ensure(fr->total_image, grow, "dssim grad")) ||
             (rc = fr->ssim_tmp.ensure(fr->total_image * 4, grow, "dssim tmp")))
@@ -742,7 +749,7 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         PROF(PK_BLEND_BWD, 1);
         gs::launch_blend_bwd(fr->total_tiles, n_views, fr->tile_base.p, fr->vdev.p, rp, fr->splats(), n, fr->starts.p,
                              fr->sorted_idx.p, cap, image, fr->T_final.p, fr->n_contrib.p, loss->kind, loss->w_l1,
-                             loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr, fr->counters.p + 2,
+                             l1_mask_t, loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr, fr->counters.p + 2,
                              s);
     }
     CK_LAUNCH();
@@ -797,7 +804,8 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
     const size_t n = (size_t)sd->n;
     long long n_img = 0;
     for (int v = 0; v < n_views; v++) n_img += 3LL * views[v].width * views[v].height;
-    const bool need_target = loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM;
+    const bool need_target =
+        loss->kind == GS_LOSS_L1 || loss->kind == GS_LOSS_L1_DSSIM || loss->kind == GS_LOSS_L1_MASKED;
     const float* in_img = need_target ? loss->target : loss->dl_dimage;
     if (n_views > 0 && (!poses || !in_img)) return fail(GS_EINVAL, "poses or loss input is NULL");
     gs_scene_desc dd = *sd;

@@ -523,7 +523,8 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
                                                            const float* __restrict__ image,
                                                            const float* __restrict__ T_final,
                                                            const uint32_t* __restrict__ n_contrib, int loss_kind,
-                                                           float w_l1, const float* __restrict__ target,
+                                                           float w_l1, float l1_mask_t,
+                                                           const float* __restrict__ target,
                                                            const float* __restrict__ dldc, Grad2DArrays g2d,
                                                            float* __restrict__ tile_loss,
                                                            unsigned long long* __restrict__ counters) {
@@ -560,7 +561,10 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
             const float* d = dldc + vd.img_off;
             g0 = d[p]; g1 = d[np + p]; g2 = d[2 * np + p];
         }
-        if (loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM) {
+        // L1 term (Eq. 16), or its confidence-masked form (Eq. 20-21): pixels whose
+        // accumulated alpha 1 - T is not above the mask threshold contribute nothing
+        if ((loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM || loss_kind == GS_LOSS_L1_MASKED) &&
+            T < l1_mask_t) {
             const float* tg = target + vd.img_off;
             const float sc = w_l1 * vd.inv_npix3;
             const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
@@ -715,11 +719,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
 void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
                       SplatArrays sp, int n, const uint32_t* starts, const uint32_t* sorted_idx, uint32_t cap,
                       const float* image, const float* T_final, const uint32_t* n_contrib, int loss_kind, float w_l1,
-                      const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
+                      float l1_mask_t, const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
                       unsigned long long* counters, cudaStream_t s) {
     if (n_tiles <= 0) return;
     k_blend_bwd<<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap, image,
-                                                 T_final, n_contrib, loss_kind, w_l1, target, dldc, g2d, tile_loss,
+                                                 T_final, n_contrib, loss_kind, w_l1, l1_mask_t, target, dldc, g2d,
+                                                 tile_loss,
                                                  counters);
 }
 

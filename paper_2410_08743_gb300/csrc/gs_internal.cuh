@@ -142,7 +142,7 @@ void launch_loss_finalize(int n_views, const ViewDev* views, const float* tile_l
 void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
                       const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
                       const uint32_t* sorted_idx, uint32_t cap, const float* image, const float* T_final,
-                      const uint32_t* n_contrib, int loss_kind, float w_l1, const float* target,
+                      const uint32_t* n_contrib, int loss_kind, float w_l1, float l1_mask_t, const float* target,
                       const float* dldc, Grad2DArrays g2d, float* tile_loss, unsigned long long* counters,
                       cudaStream_t s);
 

@@ -211,7 +211,8 @@ static void worker_main(gs_server* s) {
         }
         if (rc == GS_OK) {
             gs_loss L{};
-            L.kind = GS_LOSS_L1;
+            L.kind = s->cfg.mask_alpha > 0.0f ? GS_LOSS_L1_MASKED : GS_LOSS_L1;
+            L.mask_alpha = s->cfg.mask_alpha;
             L.w_l1 = 1.0f;
             L.target = s->d_targets;
             L.loss = s->d_loss;
@@ -267,7 +268,7 @@ int gs_server_create(int device, const gs_scene* scene, const gs_render_opts* op
                      gs_server** out) {
     if (!scene || !opts || !cfg || !out) return srv_fail(GS_EINVAL, "gs_server_create: NULL argument");
     if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->max_width < 1 || cfg->max_height < 1 ||
-        cfg->queue_capacity < 1)
+        cfg->queue_capacity < 1 || !(cfg->mask_alpha >= 0.0f && cfg->mask_alpha < 1.0f))
         return srv_fail(GS_EINVAL, "gs_server_create: bad configuration");
     *out = nullptr;
     gs_server* s = new (std::nothrow) gs_server();

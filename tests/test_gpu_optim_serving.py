@@ -86,17 +86,18 @@ def _rot_err_deg(a, b):
     return math.degrees(math.acos(min(1.0, max(-1.0, c))))
 
 
-def _server(p, sc, slots, maxw=256, maxh=192, budget=0, qcap=1024):
+def _server(p, sc, slots, maxw=256, maxh=192, budget=0, qcap=1024, mask_alpha=0.0):
     sh = L.gs_scene_borrow(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
-    srv = L.gs_server_create(0, sh, L.gs_default_opts(), slots, maxw, maxh, budget, qcap)
+    srv = L.gs_server_create(0, sh, L.gs_default_opts(), slots, maxw, maxh, budget, qcap, mask_alpha)
     return sh, srv
 
 
-def test_server_matches_step_by_step_solve(R):
+@pytest.mark.parametrize("mask_alpha", [0.0, 0.99], ids=["l1", "masked_l1"])
+def test_server_matches_step_by_step_solve(R, mask_alpha):
     sc, p, reqs = _scene_and_targets(R, 1, seed=51)
     rq = reqs[0]
     steps, lr0, lr1 = 12, 1e-2, 1e-3
-    sh, srv = _server(p, sc, 4)
+    sh, srv = _server(p, sc, 4, mask_alpha=mask_alpha)
     try:
         t = L.gs_solve_submit(srv, rq["view"], rq["image"], rq["init"], steps, lr0, lr1)
         res = L.gs_solve_wait(srv, t, 60000)
@@ -111,7 +112,8 @@ def test_server_matches_step_by_step_solve(R):
     for k in range(steps):
         img = R.forward(p, [rq["view"]], P)
         pg = torch.zeros(1, 6, dtype=torch.float64, device=DEV)
-        R.backward(p, [rq["view"]], P, img, L.make_loss(L.GS_LOSS_L1, target=tgt, w_l1=1.0), None, pg)
+        kind = L.GS_LOSS_L1_MASKED if mask_alpha > 0 else L.GS_LOSS_L1
+        R.backward(p, [rq["view"]], P, img, L.make_loss(kind, target=tgt, w_l1=1.0, mask_alpha=mask_alpha), None, pg)
         lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * k / steps))
         R.pose_step(P, m, v, pg, lr, k + 1)
     torch.cuda.synchronize()

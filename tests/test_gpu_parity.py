@@ -406,3 +406,50 @@ def test_recompute_in_backward_equals_stored_state(R):
         torch.testing.assert_close(g2[k], g1[k], rtol=1e-4, atol=1e-9)
     # the pose reduction sums float atomics, whose order differs run to run
     torch.testing.assert_close(pg2, pg1, rtol=1e-4, atol=1e-6 * float(pg1.abs().max()))
+
+
+def test_masked_l1_loss_and_gradient(R):
+    """Confidence-masked L1 (Sec. 3.4, Eq. 20-21) fused into the backward blend."""
+    w = synth.tiny_workload(0)
+    sc = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in w["scene"].items()}
+    sc["opac"] = np.maximum(sc["opac"], 0.85).astype(np.float32)
+    views, poses = w["views"], w["poses"]
+    target = oracle.render(sc, views, w["target_poses"])["image"].astype(np.float32)
+    p, P, img, tg, _ = gpu_forward(R, sc, views, poses, target=target)
+    ref = oracle.render(sc, views, poses)
+    kept = (1.0 - ref["T_final"]) > float(np.float32(0.99))
+    assert 0.05 < kept.mean() < 0.95, kept.mean()
+    Lm, dm, frm = oracle.loss_l1_masked(views, ref["image"], target, ref["T_final"], 0.99)
+    frag = ref["fragile"].astype(bool) | frm.astype(bool)
+    npx = frag.size
+    # a near-threshold pixel may fall on either side: bound its share of the loss
+    ad = np.abs(ref["image"] - target).reshape(3, npx).sum(0)
+    slack = ad[frag].sum() / (3 * npx)
+    g = zero_grads(p)
+    pg = torch.zeros(1, 6, dtype=torch.float64, device=DEV)
+    lo = torch.zeros(1, dtype=torch.float64, device=DEV)
+    R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_L1_MASKED, target=tg, loss_out=lo, mask_alpha=0.99), g, pg)
+    torch.cuda.synchronize()
+    assert abs(lo.item() - Lm) <= 1e-6 * max(1.0, Lm) + 1e-7 + slack, (lo.item(), Lm)
+    go = oracle.backward(sc, views, poses, dm)
+    keep = ~go["fragile_g"].astype(bool)
+    pose_slack = np.zeros(6)
+    if frag.any():
+        m = np.tile(frag, 3)
+        sgn = np.sign(ref["image"] - target) / (3 * npx)
+        gf = oracle.backward(sc, views, poses, np.where(m, np.abs(sgn), 0.0))
+        ind = oracle.backward(sc, views, poses, np.where(m, 1.0, 0.0), want_g2d=True)
+        keep &= ~(np.abs(ind["g2d"]).sum(1) > 0)
+        pose_slack = 2.0 * np.abs(gf["pose"][0]) + 1e-12
+    assert keep.mean() > 0.8
+    assert_grad_close(g["means"].cpu().numpy(), go["means"], "means", mask=keep)
+    assert_grad_close(g["opac"].cpu().numpy().reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
+    gp = pg.cpu().numpy()[0]
+    assert np.all(np.abs(gp - go["pose"][0]) <= 1e-3 * np.abs(go["pose"][0]) + 1e-6 + pose_slack), (gp, go["pose"][0])
+    # masked-out pixels carry no gradient: an all-masked threshold gives zero
+    g0 = zero_grads(p)
+    pg0 = torch.zeros(1, 6, dtype=torch.float64, device=DEV)
+    R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_L1_MASKED, target=tg, loss_out=lo, mask_alpha=0.999999),
+               g0, pg0)
+    torch.cuda.synchronize()
+    assert lo.item() == 0.0 and not pg0.any() and all(not v.any() for v in g0.values())
