@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-joint", action="store_true", help="skip the 300k joint-refinement leg")
+    ap.add_argument("--no-traj", action="store_true", help="skip the 3M trajectory leg")
     return ap.parse_args()
 
 
@@ -371,6 +373,19 @@ def run_gpu(args):
         serving = run_serving(p, dev, args, 64)
         serving["plain"] = run_serving(p, dev, args, 1)
 
+    joint = None
+    if not args.no_joint:
+        try:
+            joint = run_joint(dev, args)
+        except Exception as e:  # report, do not hide
+            joint = {"error": str(e)}
+    traj = None
+    if not args.no_traj:
+        try:
+            traj = run_trajectory(dev, args)
+        except Exception as e:
+            traj = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -389,6 +404,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
                        "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
             "plain_value": plain_value, "graph_value": graph_value, "serving": serving,
+            "joint": joint, "trajectory": traj,
             "tuning": tuned,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches * K),
             "roofline": roof, "cpu_baseline": cpu, "kernels": kernels,
@@ -404,6 +420,120 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _time_iters(fn, k):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(k):
+        fn(i)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _pose_errors(P, gt):
+    P = np.asarray(P)
+    rot, cen = [], []
+    for a, b in zip(P, gt):
+        Ra, Rb = a[:9].reshape(3, 3), b[:9].reshape(3, 3)
+        rot.append(math.degrees(math.acos(min(1.0, max(-1.0, (np.trace(Ra @ Rb.T) - 1) / 2)))))
+        cen.append(float(np.linalg.norm(Ra.T @ a[9:] - Rb.T @ b[9:])))
+    return float(np.mean(rot)), float(np.mean(cen))
+
+
+def run_joint(dev, args, iterations: int = 1000):
+    """Joint refinement at the forward-facing workload's size: 300k SH3
+    Gaussians (perturbed from the ground truth), 20 views of 504x378 with
+    poses off by N(0,5 deg)/N(0,0.1), one view per launch, loss 0.8 L1 +
+    0.2 D-SSIM, Gaussian Adam + pose Adam every iteration.  Targets are this
+    library's renders of the ground truth.  Times `iterations` iterations
+    after one warm pass over the views."""
+    import torch
+
+    from paper_2410_08743_gb300 import synth
+    from paper_2410_08743_gb300.joint import JointRefiner
+    from paper_2410_08743_gb300.render import Renderer
+    w = synth.joint_workload()
+    sc, views = w["scene"], w["views"]
+    V = len(views)
+    r = Renderer(dev.index or 0)
+    try:
+        pg = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in ("means", "scales", "quats", "opac", "sh")}
+        pg["sh_degree"] = int(sc["sh_degree"])
+        tg = r.forward(pg, views, torch.from_numpy(w["poses"]).to(dev)).clone()
+        del pg
+        raw = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in synth.perturb_scene_raw(12, sc).items()}
+        P = torch.from_numpy(w["init_poses"]).to(dev)
+        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=iterations + V)
+        for k in range(V):
+            J.step(k)
+        torch.cuda.synchronize()
+        first = float(J.loss.mean().item())
+        ms = _time_iters(lambda i: J.step(J.it % V), iterations)
+        rot0, cen0 = _pose_errors(w["init_poses"], w["poses"])
+        rot1, cen1 = _pose_errors(P.cpu().numpy(), w["poses"])
+        npix = views[0]["width"] * views[0]["height"]
+        return {"workload": f"{len(sc['opac'])} Gaussians SH3, {V} views 504x378, 1 view/launch, 0.8 L1 + 0.2 D-SSIM",
+                "iterations": iterations, "ms_per_iter": ms / iterations,
+                "mpix_s_incl_optimizer": iterations * npix / (ms * 1e-3) / 1e6,
+                "loss_first_pass": first, "loss_last_pass": float(J.loss.mean().item()),
+                "rot_err_deg": [rot0, rot1], "centre_err": [cen0, cen1]}
+    finally:
+        r.close()
+
+
+def run_trajectory(dev, args, batch: int = 8, epochs: int = 1):
+    """Large trajectory refinement: 3M SH3 Gaussians in a room, 200 frames of
+    1280x720 along a spline, 8 frames per launch, joint optimisation of the
+    Gaussians and the 200 poses (0.8 L1 + 0.2 D-SSIM).  Each launch rebuilds
+    its own tile lists; nothing of one batch outlives its step, so device
+    memory is bounded by one batch.  Reports ms per 8-frame step over one
+    timed pass after one warm pass, and the device memory the run holds."""
+    import torch
+
+    from paper_2410_08743_gb300 import synth
+    from paper_2410_08743_gb300.joint import JointRefiner
+    from paper_2410_08743_gb300.render import Renderer
+    free0, total = torch.cuda.mem_get_info(dev)
+    w = synth.trajectory_workload()
+    sc, views = w["scene"], w["views"]
+    V = len(views)
+    nb = (V + batch - 1) // batch
+    r = Renderer(dev.index or 0)
+    try:
+        pg = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in ("means", "scales", "quats", "opac", "sh")}
+        pg["sh_degree"] = int(sc["sh_degree"])
+        offs, _ = synth.image_offsets(views)
+        tg = torch.empty(offs[-1], device=dev)
+        Pgt = torch.from_numpy(w["poses"]).to(dev)
+        for b in range(nb):
+            k0, k1 = b * batch, min(V, (b + 1) * batch)
+            r.forward(pg, views[k0:k1], Pgt[k0:k1], image=tg[offs[k0]:offs[k1]])
+        torch.cuda.synchronize()
+        del pg
+        raw = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+               for k, a in synth.perturb_scene_raw(13, sc, means_std=0.005).items()}
+        P = torch.from_numpy(w["init_poses"]).to(dev)
+        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=(epochs + 1) * nb)
+        for b in range(nb):
+            J.step(b * batch, min(V, (b + 1) * batch))
+        torch.cuda.synchronize()
+        first = float(J.loss.mean().item())
+        ms = _time_iters(lambda i: J.step((i % nb) * batch, min(V, (i % nb + 1) * batch)), epochs * nb)
+        free1, _ = torch.cuda.mem_get_info(dev)
+        npix = sum(v["width"] * v["height"] for v in views) * epochs
+        return {"workload": f"{len(sc['opac'])} Gaussians SH3 room, {V} frames 1280x720 on a spline, "
+                            f"{batch} frames/launch, 0.8 L1 + 0.2 D-SSIM, Gaussian + pose Adam",
+                "ms_per_step": ms / (epochs * nb), "frames_per_step": batch,
+                "mpix_s_incl_optimizer": npix / (ms * 1e-3) / 1e6,
+                "device_gb_held": (free0 - free1) / 1e9,
+                "loss_first_pass": first, "loss_second_pass": float(J.loss.mean().item())}
+    finally:
+        r.close()
 
 
 def run_serving(p, dev, args, slots: int):

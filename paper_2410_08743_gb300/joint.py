@@ -34,8 +34,10 @@ def cosine_lr(it: int, total: int, lr_start: float, lr_end: float) -> float:
 class JointRefiner:
     """raw: device float32 tensors means [N,3], log_scales [N,3], quats [N,4],
     logit_opac [N], sh [N,16,3]; poses: device float64 [V,12] (world->camera,
-    updated in place); targets: list of device float32 planar images, one per
-    view.  With a process group of several ranks each rank passes its own
+    updated in place); targets: device float32, the views' planar images packed
+    in view order (or a list of them, one per view).  An iteration takes a
+    contiguous range of views (one view in the paper's setting; a batch of
+    frames for a trajectory).  With a process group of several ranks each rank passes its own
     views (dist.shard_views) and the same Gaussians; the Gaussian gradient is
     summed over the ranks before the (identical) Adam step."""
 
@@ -48,7 +50,14 @@ class JointRefiner:
         self.deg = int(sh_degree)
         self.views = views
         self.poses = poses
+        if isinstance(targets, (list, tuple)):
+            targets = torch.cat([t.reshape(-1) for t in targets])
         self.targets = targets
+        self.img_off = [0]
+        for vw in views:
+            self.img_off.append(self.img_off[-1] + 3 * vw["width"] * vw["height"])
+        if targets.numel() != self.img_off[-1]:
+            raise ValueError("targets do not match the views")
         self.w_l1, self.w_dssim = float(w_l1), float(w_dssim)
         self.lrs = dict(DEFAULT_GAUSSIAN_LRS if gaussian_lrs is None else gaussian_lrs)
         self.pose_lr = pose_lr
@@ -73,7 +82,7 @@ class JointRefiner:
         V = len(views)
         self.pm = torch.zeros(V, 6, dtype=torch.float64, device=dev)
         self.pv = torch.zeros(V, 6, dtype=torch.float64, device=dev)
-        self.pose_steps = [0] * V
+        self.pose_steps = [0] * V    # per view: Adam steps taken on its pose
         self.pose_grad = torch.zeros(V, 6, dtype=torch.float64, device=dev)
         self.loss = torch.zeros(V, dtype=torch.float64, device=dev)
         self.image = {}
@@ -83,33 +92,48 @@ class JointRefiner:
     def _desc(self):
         return L.scene_desc(self.raw["means"], self.scales, self.raw["quats"], self.opac, self.raw["sh"], self.deg)
 
-    def step(self, v: int) -> None:
-        """One iteration on view v: fused forward + loss + backward, then the
-        Gaussian and pose Adam steps.  Asynchronous on the current stream."""
-        view = self.views[v]
-        n3 = 3 * view["width"] * view["height"]
-        img = self.image.get(n3)
+    def step(self, v0: int, v1: int | None = None) -> None:
+        """One iteration on views [v0, v1) (default: the single view v0): fused
+        forward + loss + backward, then the Gaussian and pose Adam steps.
+        Asynchronous on the current stream."""
+        v1 = v0 + 1 if v1 is None else v1
+        views = self.views[v0:v1]
+        nv = v1 - v0
+        n_img = self.img_off[v1] - self.img_off[v0]
+        img = self.image.get(n_img)
         if img is None:
-            img = self.image[n3] = torch.empty(n3, device=self.raw["means"].device)
+            img = self.image[n_img] = torch.empty(n_img, device=self.raw["means"].device)
         kind = L.GS_LOSS_L1_DSSIM if self.w_dssim != 0.0 else L.GS_LOSS_L1
-        loss = L.make_loss(kind, target=self.targets[v], w_l1=self.w_l1, w_dssim=self.w_dssim)
+        loss = L.make_loss(kind, target=self.targets[self.img_off[v0]:self.img_off[v1]], w_l1=self.w_l1,
+                           w_dssim=self.w_dssim)
         grads = L.make_grads(**self.grads) if self.refine_gaussians else None
-        pose = self.poses[v:v + 1]
-        pg = self.pose_grad[v:v + 1]
-        L.gs_step(self.r.ctx, self.r.frames, self._desc(), L.views_array([view]), 1, L._ptr(pose), self.r.opts,
-                  loss, L._ptr(img), grads, L._ptr(pg), L._ptr(self.loss[v:v + 1]))
+        pose = self.poses[v0:v1]
+        pg = self.pose_grad[v0:v1]
+        L.gs_step(self.r.ctx, self.r.frames, self._desc(), L.views_array(views), nv, L._ptr(pose), self.r.opts,
+                  loss, L._ptr(img), grads, L._ptr(pg), L._ptr(self.loss[v0:v1]))
         if self.refine_gaussians:
             D.allreduce_grads(self.flat, self.group)
             self.gstep += 1
             L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv, self.lrs,
                                self.gstep, self.deg)
-        self.pose_steps[v] += 1
+        steps = self.pose_steps[v0:v1]
+        if min(steps) != max(steps):
+            raise ValueError("a batch's poses must have taken the same number of steps")
+        for k in range(v0, v1):
+            self.pose_steps[k] += 1
         lr = cosine_lr(self.it, self.iterations, *self.pose_lr)
-        L.gs_pose_step(self.r.ctx, pose, self.pm[v:v + 1], self.pv[v:v + 1], pg, lr, self.pose_steps[v])
+        L.gs_pose_step(self.r.ctx, pose, self.pm[v0:v1], self.pv[v0:v1], pg, lr, self.pose_steps[v0])
         self.it += 1
 
-    def run(self, order=None) -> None:
-        """All iterations, cycling through the views (or in `order`)."""
+    def run(self, order=None, batch: int = 1) -> None:
+        """The remaining iterations, cycling through the views in batches of
+        `batch` consecutive views (or through `order`, a list of view indices,
+        one per iteration)."""
         V = len(self.views)
+        nb = (V + batch - 1) // batch
         for k in range(self.iterations - self.it):
-            self.step(order[k % len(order)] if order is not None else (self.it % V))
+            if order is not None:
+                self.step(order[k % len(order)])
+            else:
+                b = self.it % nb
+                self.step(b * batch, min(V, (b + 1) * batch))
