@@ -366,7 +366,13 @@ def run_gpu(args):
     n = len(sc["opac"])
     roof = roofline_for(kname, per_launch_ms, kn // max(1, K), counters, n, V, n_keys, sc["sh_degree"], peaks,
                         sm_mhz_peak)
-    kernels = {k: {"ms_per_step": v[0] / K, "launches_per_step": v[1] / K} for k, v in sorted(prof.items())}
+    kernels = {}
+    for k, v in sorted(prof.items()):
+        kernels[k] = {"ms_per_step": v[0] / K, "launches_per_step": v[1] / K}
+        if k in ("blend_fwd", "blend_bwd", "preprocess_fwd", "preprocess_bwd", "scatter_keys"):
+            rk = roofline_for(k, v[0] / max(1, v[1]), v[1] // max(1, K), counters, n, V, n_keys, sc["sh_degree"],
+                              peaks, sm_mhz_peak)
+            kernels[k]["roofline"] = {x: rk[x] for x in ("bound", "achieved", "unit", "frac")}
 
     serving = None
     if not args.no_serve:
@@ -598,7 +604,7 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # DRAM bytes (read + write) per unit from one ncu capture of the current
 # kernel on the 4-view small case, scaled to a launch by the run's units
 # (profiles/top_kernels_batched_1M_4views.md).  Re-measure when the kernel changes.
-TRAFFIC_PER_UNIT = {"blend_bwd": (139.2, 5)}   # bytes per list entry read by the backward blend
+TRAFFIC_PER_UNIT = {}   # kernel -> (bytes per unit, counter index); empty until re-measured
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
@@ -615,12 +621,12 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
     if kname == "blend_bwd":
         ops = (OPS_BWD_EVAL * counters[2] + OPS_BWD_GRAD * counters[3]) / lps
         a = ops / t / 1e12
-        per, ci = TRAFFIC_PER_UNIT["blend_bwd"]
+        tr = TRAFFIC_PER_UNIT.get("blend_bwd")
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": per * counters[ci] / lps,
+                "frac": a / alu_peak, "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None,
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (2070 MHz)"}
     if kname == "preprocess_fwd":
-        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 52) / lps
+        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 60) / lps
     elif kname == "preprocess_bwd":
         by = (n * (4 * (3 + 3 + 4) + 4 * ncoef) * 2 + n * 4 * 2 + n * V * (36 + 8)) / lps
     elif kname == "segment_sort":
