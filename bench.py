@@ -590,7 +590,7 @@ def run_serving(p, dev, args, slots: int):
             "failed": int(sum(1 for x in res if x["status"] != 0))}
 
 
-# Algorithmic work per unit (see the design notes for the derivation):
+# Algorithmic work per unit (the minimum lane operations each pair needs):
 #   blend_fwd: 16 FP32 lane operations per evaluated (pixel, splat) pair
 #              (d = p - mu_hat, the conic quadratic form, the exponent, alpha,
 #              the two alpha tests) + 7 per blended pair (T update, stop test,

@@ -20,7 +20,7 @@
  *                    Eq. 12-13 d R_c / dT = ([e1]x R_c | [e2]x R_c | [e3]x R_c)
  *                    and the camera-centre term for the SH colour.
  *
- * Readings of points the paper leaves open (each is listed in the design notes):
+ * Readings of points the paper leaves open:
  *   - Eq. 3 is printed without the inverse: read as d^T Sigma_hat^{-1} d.
  *   - Eq. 4's "transmittance" is read as T_i = prod_{j<i}(1 - alpha_j).
  *   - J of the perspective map with the prior-art frustum clamp of x/z, y/z to
