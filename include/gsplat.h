@@ -219,6 +219,57 @@ int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* adam_m, double
                  const double* pose_grad, double lr, double beta1, double beta2, double eps,
                  int step, void* stream);
 
+/* Pose parametrisations of the Adam step. */
+enum {
+    GS_POSE_SE3 = 0,          /* tau = (rho, phi) in se(3), left update T <- Exp(delta) T */
+    GS_POSE_TXSO3 = 1         /* camera centre and rotation stepped separately (Sec. 4.2) */
+};
+
+/* The same step in T x SO(3) (Sec. 4.2 contrasts it with SE(3), whose
+ * exponential couples camera position and orientation): the camera centre
+ * o = -R^T t and the rotation are updated separately, o <- o + d_o and
+ * R <- Exp(d_phi) R (a rotation about the centre), then t = -R o.  pose_grad is
+ * the left-SE(3) gradient gs_render_backward writes; its T x SO(3) form is
+ * (g_o, g_phi) = (-R^T g_rho, g_phi), and the moments m, v [n_views][6] hold
+ * that form (do not mix them with gs_pose_step's). */
+int gs_pose_step_txso3(gs_ctx* ctx, int n_views, double* poses, double* adam_m, double* adam_v,
+                       const double* pose_grad, double lr, double beta1, double beta2, double eps,
+                       int step, void* stream);
+
+/* ------------------------------------------------------------ regularisers and pruning
+ * Joint refinement's extra terms (Sec. 3.3).  gs_regularize ADDS to
+ * grad_scales [n][3] / grad_opacities [n] (device, each nullable) the
+ * gradients of
+ *   lambda_aniso * (1/n) sum_i [max(s_i) / min(s_i) - aniso_r]_+   (Eq. 17)
+ *   + lambda_opacity * (1/n) sum_i o_i      (the opacity L1 the paper adds
+ *                                            during the first 10k steps)
+ * on the ACTIVATED scales s and opacities o, and writes that value to *loss
+ * (device double, nullable; summed in a fixed order).  The ratio's
+ * subgradient goes to the first largest and the first smallest axis; a ratio
+ * exactly at aniso_r, or all axes equal, gives none.  aniso_r >= 1.  Errors:
+ * GS_EINVAL, GS_ENOMEM (scratch), GS_ECUDA.  Asynchronous on `stream`. */
+int gs_regularize(gs_ctx* ctx, int64_t n, const float* scales, const float* opacities, float aniso_r,
+                  float lambda_aniso, float lambda_opacity, float* grad_scales, float* grad_opacities,
+                  double* loss, void* stream);
+
+/* Adaptive opacity threshold (Sec. 3.3: the threshold is adapted so that at
+ * most n_target Gaussians remain): the smallest value t >= min_opacity such
+ * that at most n_target opacities (device [n]) exceed t, namely
+ * max(min_opacity, the (n - n_target)-th smallest opacity) when n > n_target,
+ * else min_opacity.  Writes t and the number of Gaussians with o > t (host
+ * outputs; synchronises `stream`).  Opacities must be positive. */
+int gs_prune_threshold(gs_ctx* ctx, int64_t n, const float* opacities, int64_t n_target, float min_opacity,
+                       float* threshold, int64_t* n_keep, void* stream);
+
+/* Stable out-of-place compaction of n_arrays (<= 24) row-major float arrays
+ * (src[a] device [n][widths[a]]) into dst[a] (device, [n_keep][widths[a]],
+ * allocated by the caller, not aliasing src): row i is kept iff
+ * opacities[i] > threshold, in index order.  Use it to prune every parameter
+ * array and Adam moment of a scene at once.  Writes *n_keep (host;
+ * synchronises `stream`). */
+int gs_compact(gs_ctx* ctx, int64_t n, const float* opacities, float threshold, int n_arrays,
+               const float* const* src, float* const* dst, const int32_t* widths, int64_t* n_keep, void* stream);
+
 /* ------------------------------------------------------------ tuning
  * Launch parameters that change performance but never results: the number of
  * Gaussians per CTA of the tile counting / key scatter (1024..8192), the run
@@ -290,6 +341,7 @@ typedef struct {
     int32_t queue_capacity;   /* pending requests beyond which submit returns GS_EBUSY */
     float mask_alpha;         /* 0: plain L1; > 0: confidence-masked L1 (GS_LOSS_L1_MASKED)
                                  with this accumulated-alpha threshold (the paper uses 0.99) */
+    int32_t pose_param;       /* GS_POSE_SE3 or GS_POSE_TXSO3 */
 } gs_server_config;
 
 typedef struct {

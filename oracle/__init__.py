@@ -76,6 +76,12 @@ def lib():
         L.or_se3_left_update.argtypes = [F64P, F64P]
         L.or_pose_adam.argtypes = [C.c_int, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int]
+        L.or_pose_adam_txso3.argtypes = [C.c_int, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_int]
+        L.or_regularize.argtypes = [C.c_int, F32P, F32P, C.c_double, C.c_double, C.c_double, F64P, F64P]
+        L.or_regularize.restype = C.c_double
+        L.or_prune_threshold.argtypes = [C.c_int, F32P, C.c_longlong, C.c_float, C.POINTER(C.c_longlong)]
+        L.or_prune_threshold.restype = C.c_float
         PP = C.POINTER(F64P)
         L.or_gaussian_adam.argtypes = [C.c_int, C.c_int, PP, PP, PP, PP, F64P, C.c_double, C.c_double, C.c_double,
                                        C.c_int, F64P, F64P]
@@ -274,6 +280,34 @@ def se3_left_update(tau, T):
     x = np.array(T, np.float64)
     lib().or_se3_left_update(_p(t, F64P), _p(x, F64P))
     return x
+
+
+def regularize(scales, opac, r, lam_aniso, lam_opacity):
+    """Eq. 17 anisotropy hinge + opacity L1.  Returns (value, g_scales [n,3],
+    g_opac [n])."""
+    sc = np.ascontiguousarray(scales, np.float32).reshape(-1, 3)
+    op = np.ascontiguousarray(opac, np.float32).reshape(-1)
+    gs_ = np.zeros((len(sc), 3)); go = np.zeros(len(op))
+    val = lib().or_regularize(len(sc), _p(sc, F32P), _p(op, F32P), float(r), float(lam_aniso), float(lam_opacity),
+                              _p(gs_, F64P), _p(go, F64P))
+    return val, gs_, go
+
+
+def prune_threshold(opac, n_target, min_opacity):
+    """Returns (threshold, n_keep) of the adaptive pruning rule."""
+    op = np.ascontiguousarray(opac, np.float32).reshape(-1)
+    nk = C.c_longlong(0)
+    t = lib().or_prune_threshold(len(op), _p(op, F32P), int(n_target), float(min_opacity), C.byref(nk))
+    return float(t), int(nk.value)
+
+
+def pose_adam_txso3(poses, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    """T x SO(3) step (Sec. 4.2) in place on poses [V,12], m, v [V,6]; grad is
+    the left-SE(3) gradient [V,6]."""
+    V = len(poses)
+    g = np.ascontiguousarray(grad, np.float64)
+    lib().or_pose_adam_txso3(V, _p(poses, F64P), _p(m, F64P), _p(v, F64P), _p(g, F64P), float(lr), float(b1),
+                             float(b2), float(eps), int(step))
 
 
 def pose_adam(poses, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-8):

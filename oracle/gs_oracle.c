@@ -1239,6 +1239,99 @@ void or_pose_adam(int V, double* poses, double* m, double* v, const double* grad
     }
 }
 
+/* T x SO(3) variant (Sec. 4.2 names it as the parametrisation free of the
+ * SE(3) coupling of camera position and orientation): the camera centre
+ * o = -R^T t and the rotation are stepped separately, o <- o + d_o and
+ * R <- Exp_SO3(d_phi) R (a rotation about the centre), then t = -R o.  The
+ * input gradient is the left-SE(3) one (g_rho, g_phi).  Moving the centre by
+ * d_o is the left step rho = -R d_o, so the gradient in these coordinates is
+ * g_o = -R^T g_rho; a left step with rho = 0 rotates about the centre, so
+ * g_phi carries over.  Adam moments are kept in (g_o, g_phi). */
+void or_pose_adam_txso3(int V, double* poses, double* m, double* v, const double* grad, double lr,
+                        double b1, double b2, double eps, int step) {
+    double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    for (int i = 0; i < V; i++) {
+        double* P = poses + 12 * i;
+        const double* g_se3 = grad + 6 * i;
+        double g[6];
+        for (int a = 0; a < 3; a++)
+            g[a] = -(P[0 * 3 + a] * g_se3[0] + P[1 * 3 + a] * g_se3[1] + P[2 * 3 + a] * g_se3[2]);
+        for (int a = 3; a < 6; a++) g[a] = g_se3[a];
+        double d[6];
+        for (int k = 0; k < 6; k++) {
+            m[6 * i + k] = b1 * m[6 * i + k] + (1.0 - b1) * g[k];
+            v[6 * i + k] = b2 * v[6 * i + k] + (1.0 - b2) * g[k] * g[k];
+            double mh = m[6 * i + k] / c1, vh = v[6 * i + k] / c2;
+            d[k] = -lr * mh / (sqrt(vh) + eps);
+        }
+        double o[3];
+        for (int a = 0; a < 3; a++) o[a] = -(P[0 * 3 + a] * P[9] + P[1 * 3 + a] * P[10] + P[2 * 3 + a] * P[11]) + d[a];
+        double rot[6] = {0.0, 0.0, 0.0, d[3], d[4], d[5]}, E[12], R[9];
+        or_se3_exp(rot, E);
+        mat3_mul(E, P, R);
+        memcpy(P, R, sizeof(R));
+        for (int a = 0; a < 3; a++) P[9 + a] = -(R[a * 3 + 0] * o[0] + R[a * 3 + 1] * o[1] + R[a * 3 + 2] * o[2]);
+    }
+}
+
+/* Joint refinement's regularisers (Sec. 3.3) on activated scales [n][3] and
+ * opacities [n]: lam_an * (1/n) sum_i [max(s_i)/min(s_i) - r]_+ (Eq. 17) plus
+ * lam_op * (1/n) sum_i o_i.  Adds the gradients into g_scales / g_opac
+ * (nullable) and returns the value.  The ratio's subgradient goes to the
+ * first largest and the first smallest axis; no gradient when the ratio is
+ * exactly r or all axes are equal. */
+double or_regularize(int n, const float* scales, const float* opac, double r, double lam_an, double lam_op,
+                     double* g_scales, double* g_opac) {
+    double total = 0.0;
+    if (n <= 0) return 0.0;
+    const double w_an = lam_an / n, w_op = lam_op / n;
+    for (int i = 0; i < n; i++) {
+        const double s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+        int imax = 0, imin = 0;
+        for (int k = 1; k < 3; k++) {
+            if (s[k] > s[imax]) imax = k;
+            if (s[k] < s[imin]) imin = k;
+        }
+        const double ratio = s[imax] / s[imin];
+        if (lam_an != 0.0 && ratio > r && imax != imin) {
+            total += w_an * (ratio - r);
+            if (g_scales) {
+                g_scales[3 * i + imax] += w_an / s[imin];
+                g_scales[3 * i + imin] -= w_an * ratio / s[imin];
+            }
+        }
+        if (lam_op != 0.0) {
+            total += w_op * opac[i];
+            if (g_opac) g_opac[i] += w_op;
+        }
+    }
+    return total;
+}
+
+static int cmp_float(const void* a, const void* b) {
+    const float x = *(const float*)a, y = *(const float*)b;
+    return (x > y) - (x < y);
+}
+
+/* The adaptive pruning threshold (Sec. 3.3: at most n_target Gaussians stay):
+ * max(min_opacity, the (n - n_target)-th smallest opacity) when n > n_target,
+ * else min_opacity; *n_keep = #{o > threshold}. */
+float or_prune_threshold(int n, const float* opac, long long n_target, float min_opacity, long long* n_keep) {
+    float thr = min_opacity;
+    if ((long long)n > n_target) {
+        float* sorted = (float*)malloc(sizeof(float) * (size_t)n);
+        memcpy(sorted, opac, sizeof(float) * (size_t)n);
+        qsort(sorted, (size_t)n, sizeof(float), cmp_float);
+        const float kth = sorted[(size_t)(n - n_target - 1)];
+        free(sorted);
+        if (kth > thr) thr = kth;
+    }
+    long long kept = 0;
+    for (int i = 0; i < n; i++) kept += opac[i] > thr;
+    *n_keep = kept;
+    return thr;
+}
+
 /* Adam on the raw Gaussian parameters of joint refinement (Sec. 3.3).  The
  * renderer's gradients are w.r.t. the activated scales s = exp(log s) and
  * opacities o = 1/(1 + exp(-logit)); the chain rule gives the raw gradients

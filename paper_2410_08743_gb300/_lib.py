@@ -29,7 +29,9 @@ EXPORTED = (
     "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step", "gs_loss_dssim_static",
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
     "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
+    "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact",
 )
+GS_POSE_SE3, GS_POSE_TXSO3 = 0, 1
 
 
 class GsError(RuntimeError):
@@ -79,7 +81,8 @@ class gs_gaussian_lrs(C.Structure):
 
 class gs_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_width", C.c_int32), ("max_height", C.c_int32),
-                ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32), ("mask_alpha", C.c_float)]
+                ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32), ("mask_alpha", C.c_float),
+                ("pose_param", C.c_int32)]
 
 
 class gs_solve_request(C.Structure):
@@ -154,6 +157,15 @@ def load(path: str | None = None):
                  "gs_server_stats_get"):
         getattr(L, name).restype = C.c_int
     L.gs_pose_step.argtypes = [vp, i32, vp, vp, vp, vp, f64, f64, f64, f64, i32, vp]
+    L.gs_pose_step_txso3.argtypes = [vp, i32, vp, vp, vp, vp, f64, f64, f64, f64, i32, vp]
+    L.gs_pose_step_txso3.restype = C.c_int
+    L.gs_regularize.argtypes = [vp, C.c_int64, vp, vp, C.c_float, C.c_float, C.c_float, vp, vp, vp, vp]
+    L.gs_regularize.restype = C.c_int
+    L.gs_prune_threshold.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_float, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_int64), vp]
+    L.gs_prune_threshold.restype = C.c_int
+    L.gs_compact.argtypes = [vp, C.c_int64, vp, C.c_float, C.c_int, vp, vp, vp, C.POINTER(C.c_int64), vp]
+    L.gs_compact.restype = C.c_int
     L.gs_status.argtypes = [vp, vp]
     L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.gs_ctx_set_profiling.argtypes = [vp, i32]
@@ -294,9 +306,41 @@ def make_grads(means=None, scales=None, quats=None, opac=None, sh=None) -> gs_gr
 
 
 def gs_pose_step(ctx: int, poses, m, v, grad, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8,
-                 stream=None) -> None:
-    _ck(load().gs_pose_step(C.c_void_p(ctx), int(poses.shape[0]), _ptr(poses), _ptr(m), _ptr(v), _ptr(grad),
+                 stream=None, param: int = GS_POSE_SE3) -> None:
+    fn = load().gs_pose_step_txso3 if param == GS_POSE_TXSO3 else load().gs_pose_step
+    _ck(fn(C.c_void_p(ctx), int(poses.shape[0]), _ptr(poses), _ptr(m), _ptr(v), _ptr(grad),
                             float(lr), float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def gs_regularize(ctx: int, scales, opac, aniso_r: float, lambda_aniso: float, lambda_opacity: float,
+                  grad_scales=None, grad_opac=None, loss=None, stream=None) -> None:
+    """Anisotropy hinge (Eq. 17) and opacity L1 on activated parameters;
+    gradients are ADDED into grad_scales / grad_opac."""
+    n = int(scales.shape[0]) if scales is not None else int(opac.shape[0])
+    _ck(load().gs_regularize(C.c_void_p(ctx), n, _ptr(scales), _ptr(opac), float(aniso_r), float(lambda_aniso),
+                             float(lambda_opacity), _ptr(grad_scales), _ptr(grad_opac), _ptr(loss), _stream(stream)))
+
+
+def gs_prune_threshold(ctx: int, opac, n_target: int, min_opacity: float = 0.005, stream=None):
+    """Returns (threshold, n_keep)."""
+    thr = C.c_float(0.0)
+    nk = C.c_int64(0)
+    _ck(load().gs_prune_threshold(C.c_void_p(ctx), int(opac.shape[0]), _ptr(opac), int(n_target),
+                                  float(min_opacity), C.byref(thr), C.byref(nk), _stream(stream)))
+    return float(thr.value), int(nk.value)
+
+
+def gs_compact(ctx: int, opac, threshold: float, src: list, dst: list, widths: list, stream=None) -> int:
+    """Out-of-place stable compaction of row arrays; returns n_keep."""
+    k = len(src)
+    s_arr = (C.c_void_p * max(k, 1))(*[_ptr(a) for a in src])
+    d_arr = (C.c_void_p * max(k, 1))(*[_ptr(a) for a in dst])
+    w_arr = (C.c_int32 * max(k, 1))(*[int(w) for w in widths])
+    nk = C.c_int64(0)
+    _ck(load().gs_compact(C.c_void_p(ctx), int(opac.shape[0]), _ptr(opac), float(threshold), k,
+                          C.cast(s_arr, C.c_void_p), C.cast(d_arr, C.c_void_p), C.cast(w_arr, C.c_void_p),
+                          C.byref(nk), _stream(stream)))
+    return int(nk.value)
 
 
 def gs_loss_dssim_static(image, target, width: int, height: int, w_dssim: float, dl_dimage, loss=None,
@@ -320,9 +364,10 @@ def gs_gaussian_adam(ctx: int, raw: dict, act_scales, act_opac, grads: dict, m, 
 
 
 def gs_server_create(device: int, scene: int, opts: gs_render_opts, max_slots: int, max_width: int, max_height: int,
-                     mem_budget: int = 0, queue_capacity: int = 65536, mask_alpha: float = 0.0) -> int:
+                     mem_budget: int = 0, queue_capacity: int = 65536, mask_alpha: float = 0.0,
+                     pose_param: int = GS_POSE_SE3) -> int:
     cfg = gs_server_config(int(max_slots), int(max_width), int(max_height), int(mem_budget), int(queue_capacity),
-                           float(mask_alpha))
+                           float(mask_alpha), int(pose_param))
     h = C.c_void_p()
     _ck(load().gs_server_create(int(device), C.c_void_p(scene), C.byref(opts), C.byref(cfg), C.byref(h)))
     return h.value

@@ -56,11 +56,12 @@ int set_error(int code, const char* msg) {
 // Kernel kinds reported by the profiler.
 enum ProfKind {
     PK_SETUP = 0, PK_PRE_FWD, PK_SCAN, PK_SCATTER, PK_SORT, PK_BLEND_FWD, PK_LOSS, PK_DSSIM, PK_BLEND_BWD,
-    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT_TILES, PK_COUNT
+    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT_TILES, PK_GAUSS_ADAM, PK_REG, PK_PRUNE, PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"setup_views", "preprocess_fwd", "scan_tiles", "scatter_keys",
                                            "segment_sort", "blend_fwd", "loss_finalize", "dssim", "blend_bwd",
-                                           "preprocess_bwd", "pose_reduce", "pose_adam", "memset", "count_tiles"};
+                                           "preprocess_bwd", "pose_reduce", "pose_adam", "memset", "count_tiles",
+                                           "gaussian_adam", "regularize", "prune"};
 
 struct ProfRec {
     int kind;
@@ -78,6 +79,9 @@ struct gs_ctx {
     long long prof_n[PK_COUNT] = {};
     long long launches = 0;         // kernels launched by this context
     gs_tuning tune{4096, 2048, 256};  // result-neutral launch parameters
+    // scratch of the regularisers and the pruning select/compaction
+    void* reg_scratch = nullptr;
+    size_t reg_cap = 0;
 };
 
 static cudaEvent_t pool_event(gs_ctx* c) {
@@ -456,6 +460,7 @@ void gs_ctx_destroy(gs_ctx* c) {
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->status) cudaFree(c->status);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->reg_scratch) cudaFree(c->reg_scratch);
     delete c;
 }
 
@@ -913,15 +918,15 @@ int gs_gaussian_adam(gs_ctx* ctx, int64_t n, int sh_degree, gs_raw_params* raw, 
     G[4] = {raw->sh, grads->sh, m + 11 * N, v + 11 * N, nullptr, 48, 3 * (sh_degree + 1) * (sh_degree + 1), 0,
             lrs->sh_dc, lrs->sh_rest, 3};
     {
-        PROF(PK_POSE_ADAM, 5);
+        PROF(PK_GAUSS_ADAM, 5);
         gs::launch_gaussian_adam(N, G, 5, b1, b2, eps, step, s);
     }
     CK_LAUNCH();
     return GS_OK;
 }
 
-int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, const double* g, double lr, double b1,
-                 double b2, double eps, int step, void* stream) {
+static int pose_step_param(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, const double* g, double lr,
+                           double b1, double b2, double eps, int step, int param, void* stream) {
     if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
     if (n_views < 0 || step < 1) return fail(GS_EINVAL, "bad n_views or step");
     if (n_views > 0 && (!poses || !m || !v || !g)) return fail(GS_EINVAL, "NULL pose/moment/gradient array");
@@ -929,9 +934,131 @@ int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         PROF(PK_POSE_ADAM, 1);
-        gs::launch_pose_adam(n_views, poses, m, v, g, lr, b1, b2, eps, step, s);
+        gs::launch_pose_adam(n_views, poses, m, v, g, lr, b1, b2, eps, step, param, s);
     }
     CK_LAUNCH();
+    return GS_OK;
+}
+
+int gs_pose_step(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, const double* g, double lr, double b1,
+                 double b2, double eps, int step, void* stream) {
+    return pose_step_param(ctx, n_views, poses, m, v, g, lr, b1, b2, eps, step, GS_POSE_SE3, stream);
+}
+
+int gs_pose_step_txso3(gs_ctx* ctx, int n_views, double* poses, double* m, double* v, const double* g, double lr,
+                       double b1, double b2, double eps, int step, void* stream) {
+    return pose_step_param(ctx, n_views, poses, m, v, g, lr, b1, b2, eps, step, GS_POSE_TXSO3, stream);
+}
+
+// Grows the context's regulariser scratch to `bytes` (not during capture).
+static int reg_scratch(gs_ctx* ctx, size_t bytes) {
+    if (ctx->reg_cap >= bytes) return GS_OK;
+    if (ctx->reg_scratch) cudaFree(ctx->reg_scratch);
+    ctx->reg_scratch = nullptr;
+    ctx->reg_cap = 0;
+    size_t cap = std::max<size_t>(bytes, 4096);
+    if (cudaMalloc(&ctx->reg_scratch, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GS_ENOMEM, "regulariser scratch (%zu bytes)", cap);
+    }
+    ctx->reg_cap = cap;
+    return GS_OK;
+}
+
+int gs_regularize(gs_ctx* ctx, int64_t n, const float* scales, const float* opacities, float aniso_r,
+                  float lambda_aniso, float lambda_opacity, float* grad_scales, float* grad_opacities, double* loss,
+                  void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(GS_EINVAL, "bad n");
+    if (n > 0 && ((lambda_aniso != 0.0f && !scales) || (lambda_opacity != 0.0f && !opacities)))
+        return fail(GS_EINVAL, "NULL scales or opacities");
+    if (!(aniso_r >= 1.0f)) return fail(GS_EINVAL, "aniso_r must be >= 1");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int nb = gs::regularize_blocks((int)n);
+    if (loss && (rc = reg_scratch(ctx, sizeof(double) * (size_t)std::max(nb, 1)))) return rc;
+    const float inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
+    {
+        PROF(PK_REG, loss ? 2 : 1);
+        gs::launch_regularize((int)n, scales, opacities, aniso_r, lambda_aniso * inv_n, lambda_opacity * inv_n,
+                              grad_scales, grad_opacities, static_cast<double*>(ctx->reg_scratch), loss, s);
+    }
+    CK_LAUNCH();
+    return GS_OK;
+}
+
+int gs_prune_threshold(gs_ctx* ctx, int64_t n, const float* opacities, int64_t n_target, float min_opacity,
+                       float* threshold, int64_t* n_keep, void* stream) {
+    if (!ctx || !threshold || !n_keep) return fail(GS_EINVAL, "NULL argument");
+    if (n < 0 || n > INT32_MAX || n_target < 0) return fail(GS_EINVAL, "bad n or n_target");
+    if (n > 0 && !opacities) return fail(GS_EINVAL, "opacities is NULL");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int nb = gs::regularize_blocks((int)n);
+    const size_t bytes = sizeof(uint32_t) * (2 + 256 + (size_t)std::max(nb, 1) + 1);
+    if ((rc = reg_scratch(ctx, bytes))) return rc;
+    uint32_t* state = static_cast<uint32_t*>(ctx->reg_scratch);
+    uint32_t* hist = state + 2;
+    uint32_t* counts = hist + 256;
+    uint32_t* total = counts + std::max(nb, 1);
+    float thr = min_opacity;
+    if (n > n_target) {
+        PROF(PK_PRUNE, 9);
+        gs::launch_select_kth((int)n, opacities, (uint32_t)(n - n_target - 1), state, hist, s);
+        uint32_t st[2];
+        CK(cudaMemcpyAsync(st, state, sizeof(st), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float kth;
+        memcpy(&kth, &st[0], sizeof(float));
+        thr = std::max(thr, kth);
+    }
+    gs::CompactArrays none{};
+    {
+        PROF(PK_PRUNE, 2);
+        // counting only: a compaction with no arrays
+        gs::launch_compact((int)n, opacities, thr, none, counts, total, s);
+    }
+    CK_LAUNCH();
+    uint32_t kept = 0;
+    CK(cudaMemcpyAsync(&kept, total, sizeof(kept), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *threshold = thr;
+    *n_keep = (int64_t)kept;
+    return GS_OK;
+}
+
+int gs_compact(gs_ctx* ctx, int64_t n, const float* opacities, float threshold, int n_arrays, const float* const* src,
+               float* const* dst, const int32_t* widths, int64_t* n_keep, void* stream) {
+    if (!ctx || !n_keep) return fail(GS_EINVAL, "NULL argument");
+    if (n < 0 || n > INT32_MAX) return fail(GS_EINVAL, "bad n");
+    if (n_arrays < 0 || n_arrays > GS_COMPACT_MAX) return fail(GS_EINVAL, "at most %d arrays", GS_COMPACT_MAX);
+    if (n > 0 && !opacities) return fail(GS_EINVAL, "opacities is NULL");
+    if (n_arrays > 0 && (!src || !dst || !widths)) return fail(GS_EINVAL, "NULL array lists");
+    gs::CompactArrays ca{};
+    ca.count = n_arrays;
+    for (int a = 0; a < n_arrays; a++) {
+        if (!src[a] || !dst[a] || widths[a] < 1) return fail(GS_EINVAL, "bad array %d", a);
+        if (src[a] == dst[a]) return fail(GS_EINVAL, "array %d: compaction is out of place", a);
+        ca.src[a] = src[a]; ca.dst[a] = dst[a]; ca.width[a] = widths[a];
+    }
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int nb = gs::regularize_blocks((int)n);
+    if ((rc = reg_scratch(ctx, sizeof(uint32_t) * ((size_t)std::max(nb, 1) + 1)))) return rc;
+    uint32_t* counts = static_cast<uint32_t*>(ctx->reg_scratch);
+    uint32_t* total = counts + std::max(nb, 1);
+    {
+        PROF(PK_PRUNE, 3);
+        gs::launch_compact((int)n, opacities, threshold, ca, counts, total, s);
+    }
+    CK_LAUNCH();
+    uint32_t kept = 0;
+    CK(cudaMemcpyAsync(&kept, total, sizeof(kept), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_keep = (int64_t)kept;
     return GS_OK;
 }
 

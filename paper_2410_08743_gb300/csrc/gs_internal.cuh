@@ -154,14 +154,30 @@ int preprocess_bwd_blocks(int n);
 void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* pose_grad, cudaStream_t s);
 
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr,
-                      double b1, double b2, double eps, int step, cudaStream_t s);
+                      double b1, double b2, double eps, int step, int param, cudaStream_t s);
 
 void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
-                            const double* lrs, double b1, double b2, double eps, cudaStream_t s);
+                            const double* lrs, double b1, double b2, double eps, int param, cudaStream_t s);
 
 void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s);
 void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m, double* v, const double* grad,
-                            const int* steps, const double* lrs, double b1, double b2, double eps, cudaStream_t s);
+                            const int* steps, const double* lrs, double b1, double b2, double eps, int param,
+                            cudaStream_t s);
+
+// Row arrays moved together by the opacity compaction (gs_reg.cu).
+#define GS_COMPACT_MAX 24
+struct CompactArrays {
+    int count;
+    const float* src[GS_COMPACT_MAX];
+    float* dst[GS_COMPACT_MAX];
+    int width[GS_COMPACT_MAX];
+};
+int regularize_blocks(int n);
+void launch_regularize(int n, const float* scales, const float* opac, float r, float w_an, float w_op,
+                       float* g_scales, float* g_opac, double* partial, double* loss, cudaStream_t s);
+void launch_select_kth(int n, const float* x, uint32_t k, uint32_t* state, uint32_t* hist, cudaStream_t s);
+void launch_compact(int n, const float* opac, float thr, const CompactArrays& ca, uint32_t* counts,
+                    uint32_t* total, cudaStream_t s);
 
 // One parameter group of the Gaussian Adam update (gs_pose.cu).
 struct AdamGroup {

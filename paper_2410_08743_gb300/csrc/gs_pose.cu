@@ -1,8 +1,10 @@
 // gs_pose.cu - pose optimisation step (Sec. 3.2: T = Exp(tau), gradients on
 // the tangent space; Sec. 4.1: the camera learning rate schedule is the
 // caller's).  Adam keeps its moments in the tangent space of each view's
-// current pose; the step is applied on the left, T <- Exp(delta) T, matching
-// the left-perturbation pose gradient.  FP64 throughout (one thread per view).
+// current pose; the SE(3) step is applied on the left, T <- Exp(delta) T,
+// matching the left-perturbation pose gradient; the T x SO(3) step moves the
+// camera centre and the rotation separately (Sec. 4.2).  FP64 throughout (one
+// thread per view).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -42,37 +44,64 @@ __device__ void se3_exp(const double tau[6], double E[9], double te[3]) {
     for (int a = 0; a < 3; a++) te[a] = Vm[a * 3 + 0] * tau[0] + Vm[a * 3 + 1] * tau[1] + Vm[a * 3 + 2] * tau[2];
 }
 
-__global__ void k_pose_adam(int n_views, double* __restrict__ poses, double* __restrict__ m, double* __restrict__ v,
-                            const double* __restrict__ g, double lr, double b1, double b2, double eps, double c1,
-                            double c2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_views) return;
+// One Adam step on one pose.  g is the left-SE(3) tangent gradient the
+// backward produces.  param GS_POSE_SE3: moments on tau = (rho, phi), update
+// T <- Exp(delta) T.  param GS_POSE_TXSO3 (Sec. 4.2 names T x SO(3) as the
+// parametrisation without the SE(3) coupling of position and orientation):
+// the camera centre o = -R^T t and the rotation are stepped separately,
+// o <- o + d_o and R <- Exp(d_phi) R (a rotation about the centre), t = -R o.
+// A step (d_o, d_phi) equals the left step (rho, phi) = (-R d_o, d_phi) to
+// first order, so its gradient is (g_o, g_phi) = (-R^T g_rho, g_phi); the
+// moments live in those coordinates.
+__device__ void pose_adam_one(double* P, double* m, double* v, const double* g_in, double lr, double b1, double b2,
+                              double eps, double c1, double c2, int param) {
+    double g[6];
+    for (int k = 0; k < 6; k++) g[k] = g_in[k];
+    if (param == GS_POSE_TXSO3) {
+        for (int a = 0; a < 3; a++) g[a] = -(P[0 * 3 + a] * g_in[0] + P[1 * 3 + a] * g_in[1] + P[2 * 3 + a] * g_in[2]);
+    }
     double d[6];
     for (int k = 0; k < 6; k++) {
-        const double gk = g[6 * i + k];
-        const double mk = b1 * m[6 * i + k] + (1.0 - b1) * gk;
-        const double vk = b2 * v[6 * i + k] + (1.0 - b2) * gk * gk;
-        m[6 * i + k] = mk;
-        v[6 * i + k] = vk;
+        const double mk = b1 * m[k] + (1.0 - b1) * g[k];
+        const double vk = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+        m[k] = mk;
+        v[k] = vk;
         d[k] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
     }
-    double E[9], te[3];
-    se3_exp(d, E, te);
-    double* P = poses + 12 * i;
-    double R[9], t[3];
-    for (int a = 0; a < 3; a++) {
-        for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
-        t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
+    double E[9], te[3], R[9], t[3];
+    if (param == GS_POSE_TXSO3) {
+        double o[3];
+        for (int a = 0; a < 3; a++)
+            o[a] = -(P[0 * 3 + a] * P[9] + P[1 * 3 + a] * P[10] + P[2 * 3 + a] * P[11]) + d[a];
+        const double rot[6] = {0.0, 0.0, 0.0, d[3], d[4], d[5]};
+        se3_exp(rot, E, te);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
+        for (int a = 0; a < 3; a++) t[a] = -(R[a * 3 + 0] * o[0] + R[a * 3 + 1] * o[1] + R[a * 3 + 2] * o[2]);
+    } else {
+        se3_exp(d, E, te);
+        for (int a = 0; a < 3; a++) {
+            for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
+            t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
+        }
     }
     for (int k = 0; k < 9; k++) P[k] = R[k];
     for (int k = 0; k < 3; k++) P[9 + k] = t[k];
 }
 
+__global__ void k_pose_adam(int n_views, double* __restrict__ poses, double* __restrict__ m, double* __restrict__ v,
+                            const double* __restrict__ g, double lr, double b1, double b2, double eps, double c1,
+                            double c2, int param) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_views) return;
+    pose_adam_one(poses + 12 * i, m + 6 * i, v + 6 * i, g + 6 * i, lr, b1, b2, eps, c1, c2, param);
+}
+
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr, double b1,
-                      double b2, double eps, int step, cudaStream_t s) {
+                      double b2, double eps, int step, int param, cudaStream_t s) {
     if (n_views <= 0) return;
     const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    k_pose_adam<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, lr, b1, b2, eps, c1, c2);
+    k_pose_adam<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, lr, b1, b2, eps, c1, c2, param);
 }
 
 // Per-view variant: every view has its own step count (1-based, <= 0 means
@@ -80,38 +109,19 @@ void launch_pose_adam(int n_views, double* poses, double* m, double* v, const do
 // pose solves that started at different times.
 __global__ void k_pose_adam_multi(int n_views, double* __restrict__ poses, double* __restrict__ m,
                                   double* __restrict__ v, const double* __restrict__ g, const int* __restrict__ steps,
-                                  const double* __restrict__ lrs, double b1, double b2, double eps) {
+                                  const double* __restrict__ lrs, double b1, double b2, double eps, int param) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_views) return;
     const int step = steps[i];
     if (step <= 0) return;
     const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    const double lr = lrs[i];
-    double d[6];
-    for (int k = 0; k < 6; k++) {
-        const double gk = g[6 * i + k];
-        const double mk = b1 * m[6 * i + k] + (1.0 - b1) * gk;
-        const double vk = b2 * v[6 * i + k] + (1.0 - b2) * gk * gk;
-        m[6 * i + k] = mk;
-        v[6 * i + k] = vk;
-        d[k] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
-    }
-    double E[9], te[3];
-    se3_exp(d, E, te);
-    double* P = poses + 12 * i;
-    double R[9], t[3];
-    for (int a = 0; a < 3; a++) {
-        for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
-        t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
-    }
-    for (int k = 0; k < 9; k++) P[k] = R[k];
-    for (int k = 0; k < 3; k++) P[9 + k] = t[k];
+    pose_adam_one(poses + 12 * i, m + 6 * i, v + 6 * i, g + 6 * i, lrs[i], b1, b2, eps, c1, c2, param);
 }
 
 void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
-                            const double* lrs, double b1, double b2, double eps, cudaStream_t s) {
+                            const double* lrs, double b1, double b2, double eps, int param, cudaStream_t s) {
     if (n_views <= 0) return;
-    k_pose_adam_multi<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2, eps);
+    k_pose_adam_multi<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2, eps, param);
 }
 
 // Slot-indexed variants for a batch of independent solves whose state lives
@@ -126,33 +136,15 @@ __global__ void k_gather_poses(int n, const int* __restrict__ slot_of, const dou
 __global__ void k_pose_adam_slots(int n, const int* __restrict__ slot_of, double* __restrict__ poses,
                                   double* __restrict__ m, double* __restrict__ v, const double* __restrict__ g,
                                   const int* __restrict__ steps, const double* __restrict__ lrs, double b1, double b2,
-                                  double eps) {
+                                  double eps, int param) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = slot_of[k];
     const int step = steps[k];
     if (step <= 0) return;
     const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    const double lr = lrs[k];
-    double d[6];
-    for (int c = 0; c < 6; c++) {
-        const double gk = g[6 * k + c];
-        const double mk = b1 * m[6 * i + c] + (1.0 - b1) * gk;
-        const double vk = b2 * v[6 * i + c] + (1.0 - b2) * gk * gk;
-        m[6 * i + c] = mk;
-        v[6 * i + c] = vk;
-        d[c] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
-    }
-    double E[9], te[3];
-    se3_exp(d, E, te);
-    double* P = poses + 12 * (size_t)i;
-    double R[9], t[3];
-    for (int a = 0; a < 3; a++) {
-        for (int b = 0; b < 3; b++) R[a * 3 + b] = E[a * 3 + 0] * P[0 * 3 + b] + E[a * 3 + 1] * P[1 * 3 + b] + E[a * 3 + 2] * P[2 * 3 + b];
-        t[a] = E[a * 3 + 0] * P[9] + E[a * 3 + 1] * P[10] + E[a * 3 + 2] * P[11] + te[a];
-    }
-    for (int c = 0; c < 9; c++) P[c] = R[c];
-    for (int c = 0; c < 3; c++) P[9 + c] = t[c];
+    pose_adam_one(poses + 12 * (size_t)i, m + 6 * (size_t)i, v + 6 * (size_t)i, g + 6 * k, lrs[k], b1, b2, eps, c1,
+                  c2, param);
 }
 
 void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s) {
@@ -161,9 +153,10 @@ void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, do
 }
 
 void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m, double* v, const double* grad,
-                            const int* steps, const double* lrs, double b1, double b2, double eps, cudaStream_t s) {
+                            const int* steps, const double* lrs, double b1, double b2, double eps, int param,
+                            cudaStream_t s) {
     if (n <= 0) return;
-    k_pose_adam_slots<<<(n + 63) / 64, 64, 0, s>>>(n, slot_of, poses, m, v, grad, steps, lrs, b1, b2, eps);
+    k_pose_adam_slots<<<(n + 63) / 64, 64, 0, s>>>(n, slot_of, poses, m, v, grad, steps, lrs, b1, b2, eps, param);
 }
 
 // ------------------------------------------------------------ Gaussian Adam

@@ -221,7 +221,7 @@ static void worker_main(gs_server* s) {
         }
         if (rc == GS_OK) {
             gs::launch_pose_adam_slots(A, s->d_slot_of, s->d_pose_slot, s->d_m, s->d_v, s->d_grad, s->d_steps,
-                                       s->d_lrs, 0.9, 0.999, 1e-8, s->stream);
+                                       s->d_lrs, 0.9, 0.999, 1e-8, s->cfg.pose_param, s->stream);
             e = cudaGetLastError();
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(s->h_loss, s->d_loss, sizeof(double) * A, cudaMemcpyDeviceToHost, s->stream);
@@ -268,7 +268,8 @@ int gs_server_create(int device, const gs_scene* scene, const gs_render_opts* op
                      gs_server** out) {
     if (!scene || !opts || !cfg || !out) return srv_fail(GS_EINVAL, "gs_server_create: NULL argument");
     if (cfg->max_slots < 1 || cfg->max_slots > 4096 || cfg->max_width < 1 || cfg->max_height < 1 ||
-        cfg->queue_capacity < 1 || !(cfg->mask_alpha >= 0.0f && cfg->mask_alpha < 1.0f))
+        cfg->queue_capacity < 1 || !(cfg->mask_alpha >= 0.0f && cfg->mask_alpha < 1.0f) ||
+        (cfg->pose_param != GS_POSE_SE3 && cfg->pose_param != GS_POSE_TXSO3))
         return srv_fail(GS_EINVAL, "gs_server_create: bad configuration");
     *out = nullptr;
     gs_server* s = new (std::nothrow) gs_server();

@@ -44,7 +44,8 @@ class JointRefiner:
     def __init__(self, renderer: Renderer, raw: dict, sh_degree: int, views: list, poses: torch.Tensor,
                  targets: list, w_l1: float = 0.8, w_dssim: float = 0.2, gaussian_lrs: dict | None = None,
                  pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True,
-                 group=None):
+                 group=None, aniso_r: float | None = None, lambda_aniso: float = 0.0, lambda_opacity: float = 0.0,
+                 opacity_l1_iters: int = 10000):
         self.r = renderer
         self.raw = raw
         self.deg = int(sh_degree)
@@ -63,6 +64,12 @@ class JointRefiner:
         self.pose_lr = pose_lr
         self.iterations = int(iterations)
         self.refine_gaussians = refine_gaussians
+        # Sec. 3.3 regularisers: anisotropy hinge (Eq. 17) and, for the first
+        # opacity_l1_iters iterations, an L1 term on the opacities
+        self.aniso_r = aniso_r
+        self.lambda_aniso = float(lambda_aniso) if aniso_r is not None else 0.0
+        self.lambda_opacity = float(lambda_opacity)
+        self.opacity_l1_iters = int(opacity_l1_iters)
         dev = raw["means"].device
         n = raw["means"].shape[0]
         self.n = n
@@ -113,6 +120,10 @@ class JointRefiner:
                   loss, L._ptr(img), grads, L._ptr(pg), L._ptr(self.loss[v0:v1]))
         if self.refine_gaussians:
             D.allreduce_grads(self.flat, self.group)
+            lam_op = self.lambda_opacity if self.it < self.opacity_l1_iters else 0.0
+            if self.lambda_aniso != 0.0 or lam_op != 0.0:
+                L.gs_regularize(self.r.ctx, self.scales, self.opac, self.aniso_r or 1.0, self.lambda_aniso, lam_op,
+                                self.grads["scales"], self.grads["opac"])
             self.gstep += 1
             L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv, self.lrs,
                                self.gstep, self.deg)
@@ -124,6 +135,41 @@ class JointRefiner:
         lr = cosine_lr(self.it, self.iterations, *self.pose_lr)
         L.gs_pose_step(self.r.ctx, pose, self.pm[v0:v1], self.pv[v0:v1], pg, lr, self.pose_steps[v0])
         self.it += 1
+
+    def prune(self, n_target: int, min_opacity: float = 0.005) -> int:
+        """Adaptive opacity pruning (Sec. 3.3): removes the Gaussians whose
+        opacity is at or below the threshold that leaves at most n_target of
+        them (and at least min_opacity), from the parameters, their activated
+        copies and both Adam moments.  Returns the new count."""
+        thr, keep = L.gs_prune_threshold(self.r.ctx, self.opac, n_target, min_opacity)
+        if keep == self.n:
+            return keep
+        n, k = self.n, keep
+        dev = self.raw["means"].device
+        widths = [("means", 3), ("log_scales", 3), ("quats", 4), ("logit_opac", 1), ("sh", 48)]
+        src, dst, w = [], [], []
+        new_raw = {}
+        for name, wd in widths:
+            t = self.raw[name]
+            new_raw[name] = torch.empty((k,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+            src.append(t); dst.append(new_raw[name]); w.append(wd)
+        new_scales = torch.empty(k, 3, device=dev)
+        new_opac = torch.empty(k, device=dev)
+        src += [self.scales, self.opac]; dst += [new_scales, new_opac]; w += [3, 1]
+        gm = torch.empty(59 * k, device=dev)
+        gv = torch.empty(59 * k, device=dev)
+        off = 0
+        for _, wd in widths:       # the moments are group-major: [3n | 3n | 4n | n | 48n]
+            src += [self.gm[off * n:(off + wd) * n], self.gv[off * n:(off + wd) * n]]
+            dst += [gm[off * k:(off + wd) * k], gv[off * k:(off + wd) * k]]
+            w += [wd, wd]
+            off += wd
+        got = L.gs_compact(self.r.ctx, self.opac, thr, src, dst, w)
+        assert got == k
+        self.raw, self.scales, self.opac, self.gm, self.gv, self.n = new_raw, new_scales, new_opac, gm, gv, k
+        self.flat = D.FlatGrads(k, dev)
+        self.grads = self.flat.as_dict()
+        return k
 
     def run(self, order=None, batch: int = 1) -> None:
         """The remaining iterations, cycling through the views in batches of

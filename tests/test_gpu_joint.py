@@ -110,3 +110,39 @@ def test_joint_refinement_converges(R, workload):
     assert np.all(np.isfinite(last))
     assert last.mean() < 0.6 * first.mean()
     assert rot1 < 0.75 * rot0 and tr1 < 0.75 * tr0
+
+
+def test_joint_with_regularisers_and_pruning(R, workload):
+    """Sec. 3.3's objective: the anisotropy hinge (Eq. 17) and the opacity L1
+    join the photometric loss, and adaptive pruning mid-run leaves at most
+    N_tgt Gaussians; the run continues from the compacted state."""
+    w, targets, raw = workload
+    views = w["views"]
+    offs, _ = synth.image_offsets(views)
+    rd = {k: torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for k, a in raw.items()}
+    P = poses_dev(w["init_poses"])
+    J = JointRefiner(R, rd, w["scene"]["sh_degree"], views, P, torch.from_numpy(targets).to(DEV), iterations=300,
+                     aniso_r=3.0, lambda_aniso=0.1, lambda_opacity=0.01, opacity_l1_iters=200)
+    V = len(views)
+    for k in range(V):
+        J.step(k)
+    first = J.loss.cpu().numpy().copy()
+    J.it = 0
+    for _ in range(100):
+        J.step(J.it % V)
+    torch.cuda.synchronize()
+    n0 = J.n
+    opac_before = J.opac.cpu().numpy()
+    means_before = J.raw["means"].cpu().numpy()
+    keep_n = J.prune(250_000)
+    assert keep_n <= 250_000 and J.n == keep_n
+    t, _ = oracle.prune_threshold(opac_before, 250_000, 0.005)
+    assert keep_n == int((opac_before > t).sum())
+    assert np.array_equal(J.raw["means"].cpu().numpy(), means_before[opac_before > t])
+    for _ in range(200):
+        J.step(J.it % V)
+    torch.cuda.synchronize()
+    last = J.loss.cpu().numpy()
+    assert n0 == 300_000
+    assert np.all(np.isfinite(last)) and last.mean() < first.mean()
+    assert torch.isfinite(J.gm).all() and torch.isfinite(J.raw["means"]).all()

@@ -86,18 +86,18 @@ def _rot_err_deg(a, b):
     return math.degrees(math.acos(min(1.0, max(-1.0, c))))
 
 
-def _server(p, sc, slots, maxw=256, maxh=192, budget=0, qcap=1024, mask_alpha=0.0):
+def _server(p, sc, slots, maxw=256, maxh=192, budget=0, qcap=1024, mask_alpha=0.0, pose_param=0):
     sh = L.gs_scene_borrow(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
-    srv = L.gs_server_create(0, sh, L.gs_default_opts(), slots, maxw, maxh, budget, qcap, mask_alpha)
+    srv = L.gs_server_create(0, sh, L.gs_default_opts(), slots, maxw, maxh, budget, qcap, mask_alpha, pose_param)
     return sh, srv
 
 
-@pytest.mark.parametrize("mask_alpha", [0.0, 0.99], ids=["l1", "masked_l1"])
-def test_server_matches_step_by_step_solve(R, mask_alpha):
+@pytest.mark.parametrize("mask_alpha,param", [(0.0, 0), (0.99, 0), (0.0, 1)], ids=["l1", "masked_l1", "txso3"])
+def test_server_matches_step_by_step_solve(R, mask_alpha, param):
     sc, p, reqs = _scene_and_targets(R, 1, seed=51)
     rq = reqs[0]
     steps, lr0, lr1 = 12, 1e-2, 1e-3
-    sh, srv = _server(p, sc, 4, mask_alpha=mask_alpha)
+    sh, srv = _server(p, sc, 4, mask_alpha=mask_alpha, pose_param=param)
     try:
         t = L.gs_solve_submit(srv, rq["view"], rq["image"], rq["init"], steps, lr0, lr1)
         res = L.gs_solve_wait(srv, t, 60000)
@@ -115,7 +115,7 @@ def test_server_matches_step_by_step_solve(R, mask_alpha):
         kind = L.GS_LOSS_L1_MASKED if mask_alpha > 0 else L.GS_LOSS_L1
         R.backward(p, [rq["view"]], P, img, L.make_loss(kind, target=tgt, w_l1=1.0, mask_alpha=mask_alpha), None, pg)
         lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * k / steps))
-        R.pose_step(P, m, v, pg, lr, k + 1)
+        R.pose_step(P, m, v, pg, lr, k + 1, param=param)
     torch.cuda.synchronize()
     np.testing.assert_allclose(np.array(res["pose"]), P.cpu().numpy()[0], atol=1e-6)
 
@@ -283,3 +283,47 @@ def test_tuning_is_result_neutral_and_autotune_caches(R, tmp_path):
         assert r2["cached"] and r2["tuning"] == r1["tuning"]
     finally:
         L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256)
+
+
+def test_regularize_prune_compact_match_oracle(R):
+    """Eq. 17 anisotropy hinge + opacity L1 (Sec. 3.3), the adaptive pruning
+    threshold and the stable compaction, against the oracle / numpy."""
+    rng = np.random.default_rng(60)
+    n = 200_003
+    sc = np.exp(rng.normal(-3, 0.8, (n, 3))).astype(np.float32)
+    sc[:50] = 0.02                                     # isotropic rows
+    op = rng.uniform(0.001, 0.999, n).astype(np.float32)
+    op[100:400] = op[400]                              # ties
+    r, la, lo = 2.5, 0.3, 0.05
+    v_ref, gs_ref, go_ref = oracle.regularize(sc, op, r, la, lo)
+    ds, do = torch.from_numpy(sc).to(DEV), torch.from_numpy(op).to(DEV)
+    gs_ = torch.zeros(n, 3, device=DEV)
+    go = torch.zeros(n, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    L.gs_regularize(R.ctx, ds, do, r, la, lo, gs_, go, loss)
+    torch.cuda.synchronize()
+    g1s, g1o = gs_.clone(), go.clone()
+    L.gs_regularize(R.ctx, ds, do, r, la, lo, gs_, go, None)   # gradients are added
+    torch.cuda.synchronize()
+    assert torch.equal(gs_, 2 * g1s) and torch.equal(go, 2 * g1o)
+    gs_, go = g1s, g1o
+    ratio = sc.max(1).astype(np.float64) / sc.min(1)
+    clear = np.abs(ratio - r) > 1e-5 * r               # FP32 and FP64 agree on the hinge there
+    assert clear.mean() > 0.999
+    assert abs(loss.item() - v_ref) <= 1e-5 * abs(v_ref) + 1e-3 * la / n * (~clear).sum()
+    np.testing.assert_allclose(gs_.cpu().numpy()[clear], gs_ref[clear], rtol=2e-5, atol=1e-12)
+    np.testing.assert_allclose(go.cpu().numpy(), go_ref, rtol=1e-5)
+    for target, mn in ((60_000, 0.005), (300_000, 0.005), (150_000, 0.9)):
+        t_ref, k_ref = oracle.prune_threshold(op, target, mn)
+        t, k = L.gs_prune_threshold(R.ctx, do, target, mn)
+        assert t == t_ref and k == k_ref
+    t, k = L.gs_prune_threshold(R.ctx, do, 60_000, 0.005)
+    keep = op > t
+    means = rng.standard_normal((n, 3)).astype(np.float32)
+    shv = rng.standard_normal((n, 48)).astype(np.float32)
+    src = [torch.from_numpy(means).to(DEV), do, torch.from_numpy(shv).to(DEV)]
+    dst = [torch.empty(k, 3, device=DEV), torch.empty(k, device=DEV), torch.empty(k, 48, device=DEV)]
+    assert L.gs_compact(R.ctx, do, t, src, dst, [3, 1, 48]) == k
+    assert np.array_equal(dst[0].cpu().numpy(), means[keep])
+    assert np.array_equal(dst[1].cpu().numpy(), op[keep])
+    assert np.array_equal(dst[2].cpu().numpy(), shv[keep])

@@ -250,7 +250,8 @@ def test_fused_l1_loss_and_gradient(R):
     assert np.all(np.abs(gp - go["pose"][0]) <= 1e-3 * np.abs(go["pose"][0]) + 1e-6 + pose_slack), (gp, go["pose"][0])
 
 
-def test_pose_adam_step_matches_oracle(R):
+@pytest.mark.parametrize("param", ["se3", "txso3"])
+def test_pose_adam_step_matches_oracle(R, param):
     rng = np.random.default_rng(3)
     V = 5
     poses = np.stack([oracle.se3_exp(rng.standard_normal(6) * 0.4) for _ in range(V)])
@@ -259,8 +260,12 @@ def test_pose_adam_step_matches_oracle(R):
     pr = poses.copy()
     for step in range(1, 6):
         g = rng.standard_normal((V, 6))
-        oracle.pose_adam(pr, m, v, g, 1e-2, step)
-        R.pose_step(Pd, md, vd, torch.from_numpy(g).to(DEV), 1e-2, step)
+        if param == "se3":
+            oracle.pose_adam(pr, m, v, g, 1e-2, step)
+            R.pose_step(Pd, md, vd, torch.from_numpy(g).to(DEV), 1e-2, step)
+        else:
+            oracle.pose_adam_txso3(pr, m, v, g, 1e-2, step)
+            R.pose_step(Pd, md, vd, torch.from_numpy(g).to(DEV), 1e-2, step, param=L.GS_POSE_TXSO3)
     torch.cuda.synchronize()
     np.testing.assert_allclose(Pd.cpu().numpy(), pr, atol=1e-12)
     np.testing.assert_allclose(md.cpu().numpy(), m, atol=1e-14)
