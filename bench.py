@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-joint", action="store_true", help="skip the 300k joint-refinement leg")
     ap.add_argument("--no-traj", action="store_true", help="skip the 3M trajectory leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip the masked-L1 / regulariser / pruning timings")
     return ap.parse_args()
 
 
@@ -379,6 +380,13 @@ def run_gpu(args):
         serving = run_serving(p, dev, args, 64)
         serving["plain"] = run_serving(p, dev, args, 1)
 
+    extras = None
+    if not args.no_extras:
+        try:
+            extras = run_extras(r, p, views, P, image, tgt, grads, pose_grad, npix, dev, K)
+        except Exception as e:
+            extras = {"error": str(e)}
+
     joint = None
     if not args.no_joint:
         try:
@@ -410,7 +418,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
                        "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
             "plain_value": plain_value, "graph_value": graph_value, "serving": serving,
-            "joint": joint, "trajectory": traj,
+            "joint": joint, "trajectory": traj, "extras": extras,
             "tuning": tuned,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches * K),
             "roofline": roof, "cpu_baseline": cpu, "kernels": kernels,
@@ -426,6 +434,46 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_extras(r, p, views, P, image, tgt, grads, pose_grad, npix, dev, K):
+    """Timings of the pose-estimation and joint-refinement extras on the
+    batched workload's scene and views: the pose-only fwd+bwd with the
+    confidence-masked L1 (Sec. 3.4), the T x SO(3) pose step of 64 views, and
+    the Eq. 17 regulariser, pruning threshold and compaction of 1M Gaussians."""
+    import torch
+
+    from paper_2410_08743_gb300 import _lib as L
+    out = {}
+    V = len(views)
+    lm = L.make_loss(L.GS_LOSS_L1_MASKED, target=tgt, w_l1=1.0, mask_alpha=0.99)
+
+    def pose_only(i):
+        r.forward(p, views, P, image=image)
+        r.backward(p, views, P, image, lm, None, pose_grad)
+
+    pose_only(0)
+    ms = _time_iters(pose_only, K)
+    out["masked_l1_pose_only_mpix_s"] = npix / (ms / K * 1e-3) / 1e6
+    m = torch.zeros(V, 6, dtype=torch.float64, device=dev); v = torch.zeros_like(m)
+    Pc = P.clone()
+    ms = _time_iters(lambda i: r.pose_step(Pc, m, v, pose_grad, 1e-4, i + 1, param=L.GS_POSE_TXSO3), 20)
+    out["txso3_pose_step_us_64_views"] = 1e3 * ms / 20
+    n = p["means"].shape[0]
+    gs_ = torch.zeros_like(p["scales"]); go = torch.zeros_like(p["opac"])
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    ms = _time_iters(lambda i: L.gs_regularize(r.ctx, p["scales"], p["opac"], 3.0, 0.1, 0.01, gs_, go, loss), 20)
+    out["regularize_us_1M"] = 1e3 * ms / 20
+    t0 = time.perf_counter()
+    thr, keep = L.gs_prune_threshold(r.ctx, p["opac"], n // 2, 0.005)
+    out["prune_threshold_ms_1M"] = 1e3 * (time.perf_counter() - t0)
+    arrays = [(p["means"], 3), (p["scales"], 3), (p["quats"], 4), (p["opac"], 1), (p["sh"], 48)]
+    dst = [torch.empty((keep,) + tuple(a.shape[1:]), device=dev) for a, _ in arrays]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.gs_compact(r.ctx, p["opac"], thr, [a for a, _ in arrays], dst, [w for _, w in arrays])
+    out["compact_ms_1M_to_500k"] = 1e3 * (time.perf_counter() - t0)
+    return out
 
 
 def _time_iters(fn, k):

@@ -322,6 +322,39 @@ int gs_gaussian_adam(gs_ctx* ctx, int64_t n, int sh_degree, gs_raw_params* raw, 
                      float* opacities_out, const gs_grads* grads, float* adam_m, float* adam_v,
                      const gs_gaussian_lrs* lrs, float beta1, float beta2, float eps, int step, void* stream);
 
+/* ------------------------------------------------------------ Gaussians from a depth map
+ * The initialisation of relative pose estimation (Sec. 3.4): a subset of a
+ * frame's pixels is unprojected with the intrinsics and a depth map into a
+ * point cloud, and every point becomes an isotropic Gaussian with the pixel's
+ * colour and a scale equal to the mean 3D distance to its three nearest
+ * neighbours.
+ *
+ * gs_unproject: the pixels (u, v) = (i * stride, j * stride) with z-depth
+ * d = depth[v][u] > 0 (device [H][W]; <= 0 or NaN = no depth) become camera
+ * points ((u - cx) / fx * d, (v - cy) / fy * d, d), in pixel order, with the
+ * colours image[c][v][u] (device planar [3][H][W], nullable -> colours not
+ * written).  points / colours: device [capacity][3] with capacity >=
+ * ceil(W / stride) * ceil(H / stride).  Writes the point count to *n_out (host;
+ * synchronises `stream`). */
+int gs_unproject(gs_ctx* ctx, const gs_view* view, const float* depth, const float* image, int stride,
+                 float* points, float* colours, int64_t capacity, int64_t* n_out, void* stream);
+
+/* Mean Euclidean distance of each of n points (device [n][3]) to its k
+ * (1..8) nearest other points (exhaustive search; coincident points count at
+ * distance 0), into mean_dist (device [n]).  Asynchronous. */
+int gs_knn_mean_dist(gs_ctx* ctx, int64_t n, const float* points, int k, float* mean_dist, void* stream);
+
+/* Raw parameters (gs_raw_params, device arrays of n rows) of isotropic
+ * Gaussians at the points: log-scale = log(max(mean_dist, min_scale)) on all
+ * three axes, identity quaternion, logit(opacity), SH DC = (colour - 0.5) / C0
+ * (the renderer's colour is C0 f0 + 0.5), every other SH coefficient 0.  The
+ * paper gives no initial opacity (the prior art uses 0.1; a per-frame fit for
+ * the confidence-masked pose loss needs accumulated alpha above 0.99, reached
+ * in ~100 steps from 0.5).  Asynchronous. */
+int gs_init_from_points(gs_ctx* ctx, int64_t n, const float* points, const float* colours, const float* mean_dist,
+                        float min_scale, float opacity, gs_raw_params* raw, void* stream);
+
+
 /* ------------------------------------------------------------ pose serving
  * A request loop of 6-DoF pose-estimation solves against a device-resident
  * scene (Sec. 3.4 / Sec. 4.2: estimate the camera pose of a query image from a

@@ -78,6 +78,10 @@ def lib():
                                    C.c_double, C.c_int]
         L.or_pose_adam_txso3.argtypes = [C.c_int, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_int]
+        L.or_unproject.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, F32P, F32P,
+                                   C.c_int, F64P, F64P]
+        L.or_unproject.restype = C.c_int
+        L.or_knn_mean_dist.argtypes = [C.c_int, F64P, C.c_int, F64P]
         L.or_regularize.argtypes = [C.c_int, F32P, F32P, C.c_double, C.c_double, C.c_double, F64P, F64P]
         L.or_regularize.restype = C.c_double
         L.or_prune_threshold.argtypes = [C.c_int, F32P, C.c_longlong, C.c_float, C.POINTER(C.c_longlong)]
@@ -280,6 +284,25 @@ def se3_left_update(tau, T):
     x = np.array(T, np.float64)
     lib().or_se3_left_update(_p(t, F64P), _p(x, F64P))
     return x
+
+
+def unproject(view, depth, image, stride):
+    """Sec. 3.4 unprojection.  Returns (points [n,3] f64, colours [n,3] f64)."""
+    W, H = view["width"], view["height"]
+    dp = np.ascontiguousarray(depth, np.float32).reshape(-1)
+    im = np.ascontiguousarray(image, np.float32).reshape(-1) if image is not None else None
+    cap = ((W + stride - 1) // stride) * ((H + stride - 1) // stride)
+    pts = np.zeros((cap, 3)); cols = np.zeros((cap, 3))
+    n = lib().or_unproject(W, H, float(view["fx"]), float(view["fy"]), float(view["cx"]), float(view["cy"]),
+                           _p(dp, F32P), _p(im, F32P), int(stride), _p(pts, F64P), _p(cols, F64P))
+    return pts[:n], cols[:n]
+
+
+def knn_mean_dist(points, k=3):
+    p = np.ascontiguousarray(points, np.float64).reshape(-1, 3)
+    out = np.zeros(len(p))
+    lib().or_knn_mean_dist(len(p), _p(p, F64P), int(k), _p(out, F64P))
+    return out
 
 
 def regularize(scales, opac, r, lam_aniso, lam_opacity):

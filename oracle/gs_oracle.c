@@ -1332,6 +1332,55 @@ float or_prune_threshold(int n, const float* opac, long long n_target, float min
     return thr;
 }
 
+/* Sec. 3.4, relative pose initialisation: the pixels (u, v) = (i s, j s) of
+ * the stride grid with z-depth d > 0 become camera points
+ * ((u - cx) / fx d, (v - cy) / fy d, d) in pixel order (the pixel samples the
+ * point (u, v)), with their colours (planar image, nullable).  Returns the
+ * count; points / colours hold ceil(W/s) ceil(H/s) rows. */
+int or_unproject(int W, int H, double fx, double fy, double cx, double cy, const float* depth, const float* image,
+                 int stride, double* points, double* colours) {
+    int n = 0;
+    const size_t np = (size_t)W * H;
+    for (int v = 0; v < H; v += stride)
+        for (int u = 0; u < W; u += stride) {
+            const double d = depth[(size_t)v * W + u];
+            if (!(d > 0.0)) continue;
+            points[3 * n + 0] = (u - cx) / fx * d;
+            points[3 * n + 1] = (v - cy) / fy * d;
+            points[3 * n + 2] = d;
+            if (colours && image)
+                for (int c = 0; c < 3; c++) colours[3 * n + c] = image[c * np + (size_t)v * W + u];
+            n++;
+        }
+    return n;
+}
+
+/* Mean distance of every point to its k nearest other points (exhaustive,
+ * FP64; coincident points count at distance 0), for the Gaussian scales of
+ * Sec. 3.4. */
+void or_knn_mean_dist(int n, const double* pts, int k, double* out) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; i++) {
+        double best[16];
+        for (int j = 0; j < k; j++) best[j] = INFINITY;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            const double dx = pts[3 * j] - pts[3 * i], dy = pts[3 * j + 1] - pts[3 * i + 1],
+                         dz = pts[3 * j + 2] - pts[3 * i + 2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 >= best[k - 1]) continue;
+            int p = k - 1;
+            while (p > 0 && best[p - 1] > d2) { best[p] = best[p - 1]; p--; }
+            best[p] = d2;
+        }
+        double acc = 0.0;
+        int cnt = 0;
+        for (int j = 0; j < k; j++)
+            if (best[j] < INFINITY) { acc += sqrt(best[j]); cnt++; }
+        out[i] = cnt ? acc / cnt : 0.0;
+    }
+}
+
 /* Adam on the raw Gaussian parameters of joint refinement (Sec. 3.3).  The
  * renderer's gradients are w.r.t. the activated scales s = exp(log s) and
  * opacities o = 1/(1 + exp(-logit)); the chain rule gives the raw gradients

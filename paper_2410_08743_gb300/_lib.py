@@ -29,7 +29,8 @@ EXPORTED = (
     "gs_ctx_profile", "gs_frames_counters", "gs_ctx_launch_count", "gs_step", "gs_loss_dssim_static",
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
     "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
-    "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact",
+    "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact", "gs_unproject", "gs_knn_mean_dist",
+    "gs_init_from_points",
 )
 GS_POSE_SE3, GS_POSE_TXSO3 = 0, 1
 
@@ -166,6 +167,12 @@ def load(path: str | None = None):
     L.gs_prune_threshold.restype = C.c_int
     L.gs_compact.argtypes = [vp, C.c_int64, vp, C.c_float, C.c_int, vp, vp, vp, C.POINTER(C.c_int64), vp]
     L.gs_compact.restype = C.c_int
+    L.gs_unproject.argtypes = [vp, C.POINTER(gs_view), vp, vp, C.c_int, vp, vp, C.c_int64, C.POINTER(C.c_int64), vp]
+    L.gs_unproject.restype = C.c_int
+    L.gs_knn_mean_dist.argtypes = [vp, C.c_int64, vp, C.c_int, vp, vp]
+    L.gs_knn_mean_dist.restype = C.c_int
+    L.gs_init_from_points.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_float, C.c_float, C.POINTER(gs_raw_params), vp]
+    L.gs_init_from_points.restype = C.c_int
     L.gs_status.argtypes = [vp, vp]
     L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.gs_ctx_set_profiling.argtypes = [vp, i32]
@@ -341,6 +348,30 @@ def gs_compact(ctx: int, opac, threshold: float, src: list, dst: list, widths: l
                           C.cast(s_arr, C.c_void_p), C.cast(d_arr, C.c_void_p), C.cast(w_arr, C.c_void_p),
                           C.byref(nk), _stream(stream)))
     return int(nk.value)
+
+
+def gs_unproject(ctx: int, view: dict, depth, image, stride: int, points, colours=None, stream=None) -> int:
+    """Camera points of the stride grid's pixels with positive depth (Sec. 3.4);
+    points / colours: device [capacity, 3].  Returns the count."""
+    v = views_array([view])
+    n = C.c_int64(0)
+    _ck(load().gs_unproject(C.c_void_p(ctx), v, _ptr(depth), _ptr(image), int(stride), _ptr(points), _ptr(colours),
+                            int(points.shape[0]), C.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+def gs_knn_mean_dist(ctx: int, points, k: int, out, n: int | None = None, stream=None) -> None:
+    n = int(points.shape[0]) if n is None else int(n)
+    _ck(load().gs_knn_mean_dist(C.c_void_p(ctx), n, _ptr(points), int(k), _ptr(out), _stream(stream)))
+
+
+def gs_init_from_points(ctx: int, points, colours, mean_dist, raw: dict, n: int | None = None, min_scale: float = 1e-4,
+                        opacity: float = 0.1, stream=None) -> None:
+    n = int(points.shape[0]) if n is None else int(n)
+    rp = gs_raw_params(_ptr(raw["means"]), _ptr(raw["log_scales"]), _ptr(raw["quats"]), _ptr(raw["logit_opac"]),
+                       _ptr(raw["sh"]))
+    _ck(load().gs_init_from_points(C.c_void_p(ctx), n, _ptr(points), _ptr(colours), _ptr(mean_dist),
+                                   float(min_scale), float(opacity), C.byref(rp), _stream(stream)))
 
 
 def gs_loss_dssim_static(image, target, width: int, height: int, w_dssim: float, dl_dimage, loss=None,

@@ -56,12 +56,13 @@ int set_error(int code, const char* msg) {
 // Kernel kinds reported by the profiler.
 enum ProfKind {
     PK_SETUP = 0, PK_PRE_FWD, PK_SCAN, PK_SCATTER, PK_SORT, PK_BLEND_FWD, PK_LOSS, PK_DSSIM, PK_BLEND_BWD,
-    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT_TILES, PK_GAUSS_ADAM, PK_REG, PK_PRUNE, PK_COUNT
+    PK_PRE_BWD, PK_POSE_REDUCE, PK_POSE_ADAM, PK_MEMSET, PK_COUNT_TILES, PK_GAUSS_ADAM, PK_REG, PK_PRUNE, PK_INIT,
+    PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"setup_views", "preprocess_fwd", "scan_tiles", "scatter_keys",
                                            "segment_sort", "blend_fwd", "loss_finalize", "dssim", "blend_bwd",
                                            "preprocess_bwd", "pose_reduce", "pose_adam", "memset", "count_tiles",
-                                           "gaussian_adam", "regularize", "prune"};
+                                           "gaussian_adam", "regularize", "prune", "init_gaussians"};
 
 struct ProfRec {
     int kind;
@@ -1026,6 +1027,78 @@ int gs_prune_threshold(gs_ctx* ctx, int64_t n, const float* opacities, int64_t n
     CK(cudaStreamSynchronize(s));
     *threshold = thr;
     *n_keep = (int64_t)kept;
+    return GS_OK;
+}
+
+int gs_unproject(gs_ctx* ctx, const gs_view* view, const float* depth, const float* image, int stride, float* points,
+                 float* colours, int64_t capacity, int64_t* n_out, void* stream) {
+    if (!ctx || !view || !depth || !points || !n_out) return fail(GS_EINVAL, "NULL argument");
+    if (view->width < 1 || view->height < 1 || stride < 1) return fail(GS_EINVAL, "bad view size or stride");
+    if (!(view->fx > 0.0f) || !(view->fy > 0.0f)) return fail(GS_EINVAL, "bad focal length");
+    const int gw = (view->width + stride - 1) / stride, gh = (view->height + stride - 1) / stride;
+    const int64_t ng = (int64_t)gw * gh;
+    if (capacity < ng) return fail(GS_EINVAL, "capacity %lld < %lld grid pixels", (long long)capacity, (long long)ng);
+    if (ng > INT32_MAX / 8) return fail(GS_EINVAL, "too many grid pixels");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int nb = gs::regularize_blocks((int)ng);
+    const size_t fl = (size_t)ng * 7;
+    if ((rc = reg_scratch(ctx, sizeof(float) * fl + sizeof(uint32_t) * ((size_t)nb + 2)))) return rc;
+    float* pts = static_cast<float*>(ctx->reg_scratch);
+    float* cols = pts + 3 * ng;
+    float* key = cols + 3 * ng;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(key + ng);
+    uint32_t* total = counts + nb + 1;
+    gs::CompactArrays ca{};
+    ca.count = colours ? 2 : 1;
+    ca.src[0] = pts; ca.dst[0] = points; ca.width[0] = 3;
+    if (colours) { ca.src[1] = cols; ca.dst[1] = colours; ca.width[1] = 3; }
+    {
+        PROF(PK_INIT, 4);
+        gs::launch_unproject(view->width, view->height, stride, view->fx, view->fy, view->cx, view->cy, depth, image,
+                             pts, cols, key, s);
+        gs::launch_compact((int)ng, key, 0.0f, ca, counts, total, s);
+    }
+    CK_LAUNCH();
+    uint32_t kept = 0;
+    CK(cudaMemcpyAsync(&kept, total, sizeof(kept), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_out = (int64_t)kept;
+    return GS_OK;
+}
+
+int gs_knn_mean_dist(gs_ctx* ctx, int64_t n, const float* points, int k, float* mean_dist, void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    if (n < 0 || n > INT32_MAX || k < 1 || k > 8) return fail(GS_EINVAL, "bad n or k (1..8)");
+    if (n > 0 && (!points || !mean_dist)) return fail(GS_EINVAL, "NULL points or output");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        PROF(PK_INIT, 1);
+        gs::launch_knn_mean((int)n, points, k, mean_dist, s);
+    }
+    CK_LAUNCH();
+    return GS_OK;
+}
+
+int gs_init_from_points(gs_ctx* ctx, int64_t n, const float* points, const float* colours, const float* mean_dist,
+                        float min_scale, float opacity, gs_raw_params* raw, void* stream) {
+    if (!ctx || !raw) return fail(GS_EINVAL, "NULL argument");
+    if (n < 0 || n > INT32_MAX) return fail(GS_EINVAL, "bad n");
+    if (!(opacity > 0.0f && opacity < 1.0f) || !(min_scale > 0.0f)) return fail(GS_EINVAL, "bad opacity or min_scale");
+    if (n > 0 && (!points || !colours || !mean_dist || !raw->means || !raw->log_scales || !raw->quats ||
+                  !raw->logit_opacities || !raw->sh))
+        return fail(GS_EINVAL, "NULL array");
+    CK(cudaSetDevice(ctx->device));
+    const float logit_o = logf(opacity / (1.0f - opacity));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        PROF(PK_INIT, 1);
+        gs::launch_init_raw((int)n, points, colours, mean_dist, min_scale, logit_o, raw->means, raw->log_scales,
+                            raw->quats, raw->logit_opacities, raw->sh, s);
+    }
+    CK_LAUNCH();
     return GS_OK;
 }
 

@@ -179,6 +179,13 @@ void launch_select_kth(int n, const float* x, uint32_t k, uint32_t* state, uint3
 void launch_compact(int n, const float* opac, float thr, const CompactArrays& ca, uint32_t* counts,
                     uint32_t* total, cudaStream_t s);
 
+// Gaussians from a depth map (gs_init.cu).
+void launch_unproject(int W, int H, int stride, float fx, float fy, float cx, float cy, const float* depth,
+                      const float* image, float* pts, float* cols, float* key, cudaStream_t s);
+void launch_knn_mean(int n, const float* pts, int k, float* out, cudaStream_t s);
+void launch_init_raw(int n, const float* pts, const float* cols, const float* dist, float min_scale, float logit_o,
+                     float* means, float* log_scales, float* quats, float* logit_opac, float* sh, cudaStream_t s);
+
 // One parameter group of the Gaussian Adam update (gs_pose.cu).
 struct AdamGroup {
     float* p;          // raw parameter

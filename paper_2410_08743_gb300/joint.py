@@ -45,7 +45,7 @@ class JointRefiner:
                  targets: list, w_l1: float = 0.8, w_dssim: float = 0.2, gaussian_lrs: dict | None = None,
                  pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True,
                  group=None, aniso_r: float | None = None, lambda_aniso: float = 0.0, lambda_opacity: float = 0.0,
-                 opacity_l1_iters: int = 10000):
+                 opacity_l1_iters: int = 10000, refine_poses: bool = True):
         self.r = renderer
         self.raw = raw
         self.deg = int(sh_degree)
@@ -64,6 +64,7 @@ class JointRefiner:
         self.pose_lr = pose_lr
         self.iterations = int(iterations)
         self.refine_gaussians = refine_gaussians
+        self.refine_poses = refine_poses
         # Sec. 3.3 regularisers: anisotropy hinge (Eq. 17) and, for the first
         # opacity_l1_iters iterations, an L1 term on the opacities
         self.aniso_r = aniso_r
@@ -127,13 +128,14 @@ class JointRefiner:
             self.gstep += 1
             L.gs_gaussian_adam(self.r.ctx, self.raw, self.scales, self.opac, self.grads, self.gm, self.gv, self.lrs,
                                self.gstep, self.deg)
-        steps = self.pose_steps[v0:v1]
-        if min(steps) != max(steps):
-            raise ValueError("a batch's poses must have taken the same number of steps")
-        for k in range(v0, v1):
-            self.pose_steps[k] += 1
-        lr = cosine_lr(self.it, self.iterations, *self.pose_lr)
-        L.gs_pose_step(self.r.ctx, pose, self.pm[v0:v1], self.pv[v0:v1], pg, lr, self.pose_steps[v0])
+        if self.refine_poses:
+            steps = self.pose_steps[v0:v1]
+            if min(steps) != max(steps):
+                raise ValueError("a batch's poses must have taken the same number of steps")
+            for k in range(v0, v1):
+                self.pose_steps[k] += 1
+            lr = cosine_lr(self.it, self.iterations, *self.pose_lr)
+            L.gs_pose_step(self.r.ctx, pose, self.pm[v0:v1], self.pv[v0:v1], pg, lr, self.pose_steps[v0])
         self.it += 1
 
     def prune(self, n_target: int, min_opacity: float = 0.005) -> int:

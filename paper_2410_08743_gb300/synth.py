@@ -217,28 +217,42 @@ def _box_surface_points(rng: np.random.Generator, n: int, lo, hi) -> np.ndarray:
     return pts
 
 
-def make_scene_room(seed: int = 5, n: int = 3_000_000, sh_degree: int = 3,
-                    room=(6.0, 3.0, 8.0), n_boxes: int = 6, box_share: float = 0.25) -> dict:
-    """Room-scale scene: Gaussians on the walls, floor and ceiling of a
-    room x*y*z box centred at the origin and on the surfaces of n_boxes
-    furniture-like boxes standing on the floor (y = +room_y/2) near the
-    walls; log-scales N(log 0.006, 0.4)."""
-    rng = _rng(seed)
+def room_geometry(seed: int = 5, room=(6.0, 3.0, 8.0), n_boxes: int = 6) -> dict:
+    """The room of the trajectory workload: a room x*y*z box centred at the
+    origin (floor at y = +room_y/2) and n_boxes furniture boxes standing on
+    the floor near the side walls.  Returns dict(half [3], boxes [(lo, hi)])."""
+    rng = _rng(seed + 17)
     half = np.asarray(room, np.float64) / 2.0
-    n_box = int(n * box_share)
-    n_room = n - n_box
-    parts = [_box_surface_points(rng, n_room, -half, half)]
     sizes = rng.uniform(0.3, 0.9, (n_boxes, 3))
-    areas = 2 * (sizes[:, 0] * sizes[:, 1] + sizes[:, 1] * sizes[:, 2] + sizes[:, 0] * sizes[:, 2])
-    counts = np.floor(n_box * areas / areas.sum()).astype(int)
-    counts[0] += n_box - counts.sum()
+    boxes = []
     for k in range(n_boxes):
         sx = (1 if k % 2 == 0 else -1) * (half[0] - 0.2 - sizes[k, 0] / 2)
         cz = rng.uniform(-half[2] + 1.0, half[2] - 1.0)
         c = np.array([sx, half[1] - sizes[k, 1] / 2, cz])
-        parts.append(_box_surface_points(rng, counts[k], c - sizes[k] / 2, c + sizes[k] / 2))
+        boxes.append((c - sizes[k] / 2, c + sizes[k] / 2))
+    return dict(half=half, boxes=boxes)
+
+
+def make_scene_room(seed: int = 5, n: int = 3_000_000, sh_degree: int = 3,
+                    room=(6.0, 3.0, 8.0), n_boxes: int = 6, box_share: float = 0.25,
+                    scale: float = 0.006) -> dict:
+    """Room-scale scene: Gaussians on the walls, floor and ceiling of the
+    room and on the surfaces of its furniture boxes (room_geometry);
+    log-scales N(log scale, 0.4)."""
+    geo = room_geometry(seed, room, n_boxes)
+    rng = _rng(seed)
+    half = geo["half"]
+    n_box = int(n * box_share)
+    n_room = n - n_box
+    parts = [_box_surface_points(rng, n_room, -half, half)]
+    ext = np.array([hi - lo for lo, hi in geo["boxes"]])
+    areas = 2 * (ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 0] * ext[:, 2])
+    counts = np.floor(n_box * areas / areas.sum()).astype(int)
+    counts[0] += n_box - counts.sum()
+    for k, (lo, hi) in enumerate(geo["boxes"]):
+        parts.append(_box_surface_points(rng, counts[k], lo, hi))
     means = np.concatenate(parts)
-    scales = np.exp(rng.normal(math.log(0.006), 0.4, (n, 3)))
+    scales = np.exp(rng.normal(math.log(scale), 0.4, (n, 3)))
     quats = random_unit_quats(rng, n)
     opac = sigmoid_normal(rng, n)
     sh = np.zeros((n, 16, 3), np.float32)
@@ -248,6 +262,34 @@ def make_scene_room(seed: int = 5, n: int = 3_000_000, sh_degree: int = 3,
         sh[:, 1:ncoef, :] = 0.1 * rng.standard_normal((n, ncoef - 1, 3), dtype=np.float32)
     return dict(means=means.astype(np.float32), scales=scales.astype(np.float32),
                 quats=quats, opac=opac, sh=sh, sh_degree=sh_degree)
+
+
+def room_depth(geo: dict, view: dict, pose: np.ndarray) -> np.ndarray:
+    """Ground-truth z-depth [H, W] (float32) of the room's surfaces seen by a
+    pinhole camera (world->camera pose [12]): per pixel, the nearest hit of
+    the ray through the pixel's sample point with the furniture boxes (slab
+    test) or the room's inner walls.  This is the input stand-in for a
+    monocular depth estimate."""
+    W, H = view["width"], view["height"]
+    R = np.asarray(pose[:9], np.float64).reshape(3, 3)
+    t = np.asarray(pose[9:], np.float64)
+    c = -R.T @ t
+    u, v = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
+    dc = np.stack([(u - view["cx"]) / view["fx"], (v - view["cy"]) / view["fy"], np.ones_like(u)], -1)
+    d = dc @ R                       # world directions (rows of R^T dc), camera z component 1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        half = geo["half"]
+        t_exit = np.min(np.where(d > 0, (half - c) * inv, np.where(d < 0, (-half - c) * inv, np.inf)), -1)
+        best = t_exit
+        for lo, hi in geo["boxes"]:
+            t1 = (lo - c) * inv
+            t2 = (hi - c) * inv
+            tn = np.max(np.minimum(t1, t2), -1)
+            tf = np.min(np.maximum(t1, t2), -1)
+            hit = (tn <= tf) & (tn > 0)
+            best = np.where(hit & (tn < best), tn, best)
+    return best.astype(np.float32)     # the ray parameter is the z-depth (camera z of d is 1)
 
 
 def spline_trajectory(rng: np.random.Generator, n_frames: int, n_ctrl: int = 8,
@@ -272,16 +314,16 @@ def spline_trajectory(rng: np.random.Generator, n_frames: int, n_ctrl: int = 8,
 
 
 def trajectory_workload(seed: int = 5, n: int = 3_000_000, n_frames: int = 200,
-                        width: int = 1280, height: int = 720, focal: float = 600.0) -> dict:
+                        width: int = 1280, height: int = 720, focal: float = 600.0, scale: float = 0.006) -> dict:
     """Large trajectory refinement: a 3M-Gaussian SH3 room seen by n_frames
     1280x720 cameras (fx = fy = 600) along a smooth spline; initial poses
     off by N(0, 1 deg)/N(0, 0.02)."""
-    scene = make_scene_room(seed, n)
+    scene = make_scene_room(seed, n, scale=scale)
     rng = _rng(seed + 1000)
     poses = spline_trajectory(rng, n_frames)
     views = [intrinsics(width, height, fx=focal) for _ in range(n_frames)]
     init = np.stack([perturb_normal(rng, p, 1.0, 0.02) for p in poses])
-    return dict(scene=scene, views=views, poses=poses, init_poses=init)
+    return dict(scene=scene, views=views, poses=poses, init_poses=init, geometry=room_geometry(seed))
 
 
 def serving_requests(seed: int = 4, n_requests: int = 2000, rate_hz: float = 200.0,
