@@ -426,6 +426,8 @@ def run_gpu(args):
                          "pairs_eval_bwd": counters[2], "pairs_grad_bwd": counters[3],
                          "entries_read_fwd": counters[4], "entries_read_bwd": counters[5],
                          "entries_sorted": counters[6],
+                         "warp_entries_fwd": counters[7], "warp_entries_bwd_box": counters[8],
+                         "warp_entries_bwd_used": counters[9],
                          "keys_per_gaussian_view": n_keys / (n * V)},
             "status": st,
         }

@@ -461,8 +461,12 @@ int64_t gs_ctx_launch_count(gs_ctx* ctx);
  * alpha the backward blend evaluated, out[3] pairs that
  * contributed gradients in the backward, out[4] sorted-list entries read by
  * the forward blend, out[5] sorted-list entries read by the backward blend,
- * out[6] list entries the forward sorted (all keys with GS_F_FULL_SORT). */
-int gs_frames_counters(gs_frames* fr, int64_t out[7]);
+ * out[6] list entries the forward sorted (all keys with GS_F_FULL_SORT),
+ * out[7] (warp, splat) entries the forward blend walked (after the per-warp
+ * compaction), out[8] / out[9] (warp, splat) entries of the backward blend with
+ * a pixel in the splat's alpha box / with a contributing pixel. */
+#define GS_N_COUNTERS 10
+int gs_frames_counters(gs_frames* fr, int64_t out[GS_N_COUNTERS]);
 
 /* D-SSIM loss term and its image gradient for ONE view, allocating nothing.
  * (The paper has no counterpart: this is a deployment variant of the D-SSIM

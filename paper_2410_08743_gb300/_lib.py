@@ -507,8 +507,11 @@ def gs_ctx_launch_count(ctx: int) -> int:
     return int(load().gs_ctx_launch_count(C.c_void_p(ctx)))
 
 
+GS_N_COUNTERS = 10
+
+
 def gs_frames_counters(fr: int):
-    out = (C.c_int64 * 7)()
+    out = (C.c_int64 * GS_N_COUNTERS)()
     _ck(load().gs_frames_counters(C.c_void_p(fr), out))
     return [int(x) for x in out]
 

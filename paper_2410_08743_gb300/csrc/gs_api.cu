@@ -599,7 +599,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     if (n_views == 0) { fr->have_forward = true; return GS_OK; }
     const RenderParams rp = make_params(opts);
     SplatArrays sp = fr->splats();
-    if ((rc = fr->counters.ensure(8, grow, "counters"))) return rc;
+    if ((rc = fr->counters.ensure(12, grow, "counters"))) return rc;
     {
         PROF(PK_SETUP, 1);
         gs::launch_setup_views(views, n_views, poses, fr->vdev.p, rp, s);
@@ -609,7 +609,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         PROF(PK_MEMSET, 0);
         CK(cudaMemsetAsync(fr->counts.p, 0, sizeof(uint32_t) * (T + 1), s));
         CK(cudaMemsetAsync(fr->cursor.p, 0, sizeof(uint32_t) * (T + 1), s));
-        CK(cudaMemsetAsync(fr->counters.p, 0, sizeof(unsigned long long) * 8, s));
+        CK(cudaMemsetAsync(fr->counters.p, 0, sizeof(unsigned long long) * 12, s));
     }
     for (int v0 = 0; v0 < n_views; v0 += kViewChunk) {
         const int nv = std::min(kViewChunk, n_views - v0);
@@ -1250,17 +1250,20 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 
 int64_t gs_ctx_launch_count(gs_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
-int gs_frames_counters(gs_frames* fr, int64_t out[7]) {
+int gs_frames_counters(gs_frames* fr, int64_t out[GS_N_COUNTERS]) {
     if (!fr || !out) return fail(GS_EINVAL, "NULL argument");
-    for (int k = 0; k < 7; k++) out[k] = 0;
+    for (int k = 0; k < GS_N_COUNTERS; k++) out[k] = 0;
     if (!fr->counters.p) return GS_OK;
     CK(cudaSetDevice(fr->ctx->device));
-    unsigned long long c[8];
+    unsigned long long c[12];
     CK(cudaMemcpy(c, fr->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 4; k++) out[k] = (int64_t)c[k];
     out[4] = (int64_t)c[4];
     out[5] = (int64_t)c[6];
     out[6] = fr->full_sort ? (int64_t)fr->n_keys : (int64_t)c[5];
+    out[7] = (int64_t)c[8];
+    out[8] = (int64_t)c[9];
+    out[9] = (int64_t)c[10];
     return GS_OK;
 }
 

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
     const uint32_t n_list = e - s;
     const size_t vbase = (size_t)v * n;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0, n_eval = 0, n_blend = 0, n_read = 0;
+    uint32_t last = 0, n_eval = 0, n_blend = 0, n_read = 0, n_went = 0;
     bool done = !inside;
     uint32_t n_sorted = 0;
 
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             unsigned char* wl = sm.wl[threadIdx.x >> 5];
             const int nw = warp_compact(sm.u.sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
                                         (float)(2 * (threadIdx.x >> 5)), wl);
+            if (__any_sync(0xffffffffu, !done)) n_went += (uint32_t)nw;
             if (!done) {
                 for (int q = 0; q < nw; q++) {
                     const int jj = wl[q];
@@ -443,7 +444,11 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             ce += __shfl_xor_sync(0xffffffffu, ce, o);
             cbl += __shfl_xor_sync(0xffffffffu, cbl, o);
         }
-        if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cbl); }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(counters, ce);
+            atomicAdd(counters + 1, cbl);
+            atomicAdd(counters + 8, (unsigned long long)n_went);   // warp-entries walked
+        }
         if (threadIdx.x == 0) {
             atomicAdd(counters + 4, (unsigned long long)n_read);
             atomicAdd(counters + 5, (unsigned long long)n_sorted);
@@ -600,7 +605,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
     if (tile_last > e - s) tile_last = e - s;
     if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
     const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
-    uint32_t n_eval = 0, n_used = 0;
+    uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
     const int lane = threadIdx.x & 31;
     // component held by this lane after the transposed reduction
     const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
@@ -633,11 +638,13 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
             use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
             n_eval += use;
             if (!__any_sync(0xffffffffu, use)) continue;
+            n_w1++;
             const float4 b = sb.B[jj];
             float G = 0.f, alpha = 0.f;
             bool cl = false;
             if (use) use = pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl);
             if (!__any_sync(0xffffffffu, use)) continue;
+            n_w2++;
             n_used += use;
             float r[8], r8 = 0.0f;
 #pragma unroll
@@ -712,7 +719,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
             ce += __shfl_xor_sync(0xffffffffu, ce, o);
             cu += __shfl_xor_sync(0xffffffffu, cu, o);
         }
-        if ((threadIdx.x & 31) == 0) { atomicAdd(counters, ce); atomicAdd(counters + 1, cu); }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(counters, ce);
+            atomicAdd(counters + 1, cu);
+            atomicAdd(counters + 7, (unsigned long long)n_w1);   // warp-entries with a pixel in the box
+            atomicAdd(counters + 8, (unsigned long long)n_w2);   // warp-entries with a contributing pixel
+        }
     }
 }
 

@@ -465,21 +465,23 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
 #pragma unroll
     for (int k = 0; k < NC * 3; k++) sgf[k * blockDim.x + threadIdx.x] = 0.0f;
 
+    // The 2D gradients are zero for every culled (view, Gaussian) pair (the
+    // buffers are cleared before the backward blend), so they are read without
+    // consulting the tile rectangle, one view ahead of their use.
+    float4 na4 = make_float4(0, 0, 0, 0), nb4 = make_float4(0, 0, 0, 0);
+    float nc1 = 0.0f;
+    if (live && n_views > 0) { na4 = g2d.gA[i]; nb4 = g2d.gB[i]; nc1 = g2d.gC[i]; }
     for (int v = 0; v < n_views; v++) {
         const ViewDev& vd = sv[v];
         float pr[6] = {0, 0, 0, 0, 0, 0};
-        const size_t k = (size_t)v * sc.n + i;
-        bool act = false;
-        float4 a4 = make_float4(0, 0, 0, 0), b4 = make_float4(0, 0, 0, 0);
-        float c1 = 0.0f;
-        if (live) {
-            uint2 rc = sp.rect[k];
-            if ((rc.y & 0xffff) > (rc.x & 0xffff)) {
-                a4 = g2d.gA[k]; b4 = g2d.gB[k]; c1 = g2d.gC[k];
-                act = (a4.x != 0.f) | (a4.y != 0.f) | (a4.z != 0.f) | (a4.w != 0.f) | (b4.x != 0.f) |
-                      (b4.y != 0.f) | (b4.z != 0.f) | (b4.w != 0.f) | (c1 != 0.f);
-            }
+        const float4 a4 = na4, b4 = nb4;
+        const float c1 = nc1;
+        if (live && v + 1 < n_views) {
+            const size_t kn = (size_t)(v + 1) * sc.n + i;
+            na4 = g2d.gA[kn]; nb4 = g2d.gB[kn]; nc1 = g2d.gC[kn];
         }
+        const bool act = (a4.x != 0.f) | (a4.y != 0.f) | (a4.z != 0.f) | (a4.w != 0.f) | (b4.x != 0.f) |
+                         (b4.y != 0.f) | (b4.z != 0.f) | (b4.w != 0.f) | (c1 != 0.f);
         if (act) {
             const float* Rc = vd.Rf;
             const float fx = vd.fx, fy = vd.fy;
