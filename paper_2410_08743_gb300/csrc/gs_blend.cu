@@ -57,9 +57,19 @@ __device__ __forceinline__ float4 stage_mean(const SplatArrays& sp, size_t k, fl
     return a;
 }
 
+// Pixel of thread tid within its 16x16 tile.  Each warp covers an 8x4 block
+// (the 8 warps tile the 16x16 pixels as 2 columns x 4 rows), which a small
+// splat's alpha box overlaps in fewer warps than a 16x2 strip would.
+#define WARP_W 8
+#define WARP_H 4
+__device__ __forceinline__ int tile_px(int tid) { return ((tid >> 5) & 1) * WARP_W + (tid & (WARP_W - 1)); }
+__device__ __forceinline__ int tile_py(int tid) { return (tid >> 6) * WARP_H + ((tid & 31) >> 3); }
+__device__ __forceinline__ float warp_x0(int tid) { return (float)(((tid >> 5) & 1) * WARP_W); }
+__device__ __forceinline__ float warp_y0(int tid) { return (float)((tid >> 6) * WARP_H); }
+
 // Per-warp compaction of a staged batch: the entries (in order) whose alpha
-// box can touch a pixel of this warp's 16x2 footprint (x in [fx0, fx0+15],
-// y in [fy0, fy0+1]).  The test is conservative (0.01 px slack over the
+// box can touch a pixel of this warp's 8x4 footprint (x in [fx0, fx0+7],
+// y in [fy0, fy0+3]).  The test is conservative (0.01 px slack over the
 // per-pixel box test), so skipping the other entries changes no decision.
 // Returns the number of entries written to wl.
 __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float fx0, float fy0,
@@ -72,8 +82,8 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
         if (e < cnt) {
             const float4 a = sb.A[e];
             const float2 h = sb.H[e];
-            hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx0 + (GS_TILE - 1)) &&
-                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy0 + 1.0f);
+            hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx0 + (float)(WARP_W - 1)) &&
+                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy0 + (float)(WARP_H - 1));
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) wl[n + __popc(m & ((1u << lane) - 1u))] = (unsigned char)e;
@@ -116,12 +126,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
     const ViewDev& vd = views[v];
     const int W = vd.W, H = vd.H, gw = vd.gw;
     const int lt = t - vd.tile_base;
-    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
-    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const int px = (lt % gw) * GS_TILE + tile_px(threadIdx.x);
+    const int py = (lt / gw) * GS_TILE + tile_py(threadIdx.x);
     const bool inside = px < W && py < H;
     // tile-relative pixel coordinates (the staged means are moved to the same origin)
     const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
-    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
+    const float fpx = (float)tile_px(threadIdx.x), fpy = (float)tile_py(threadIdx.x);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -235,7 +245,7 @@ struct LazySmem {
 };
 
 template <int LZ_CAP>
-__global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
+__global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
                                                          const ViewDev* __restrict__ views, RenderParams rp,
                                                          SplatArrays sp, int n, const uint32_t* __restrict__ starts,
                                                          unsigned long long* __restrict__ keys,
@@ -257,12 +267,12 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
     const ViewDev& vd = views[v];
     const int W = vd.W, H = vd.H, gw = vd.gw;
     const int lt = t - vd.tile_base;
-    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
-    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const int px = (lt % gw) * GS_TILE + tile_px(threadIdx.x);
+    const int py = (lt / gw) * GS_TILE + tile_py(threadIdx.x);
     const bool inside = px < W && py < H;
     // tile-relative pixel coordinates (the staged means are moved to the same origin)
     const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
-    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
+    const float fpx = (float)tile_px(threadIdx.x), fpy = (float)tile_py(threadIdx.x);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -291,8 +301,7 @@ __global__ void __launch_bounds__(LZ_T) k_blend_fwd_lazy(int n_views, const int*
             __syncthreads();
             const int cnt = (int)min((uint32_t)BATCH, p1 - base);
             unsigned char* wl = sm.wl[threadIdx.x >> 5];
-            const int nw = warp_compact(sm.u.sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
-                                        (float)(2 * (threadIdx.x >> 5)), wl);
+            const int nw = warp_compact(sm.u.sb, cnt, warp_x0(threadIdx.x), warp_y0(threadIdx.x), wl);
             if (__any_sync(0xffffffffu, !done)) n_went += (uint32_t)nw;
             if (!done) {
                 for (int q = 0; q < nw; q++) {
@@ -543,12 +552,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
     const ViewDev& vd = views[v];
     const int W = vd.W, H = vd.H, gw = vd.gw;
     const int lt = t - vd.tile_base;
-    const int px = (lt % gw) * GS_TILE + (threadIdx.x % GS_TILE);
-    const int py = (lt / gw) * GS_TILE + (threadIdx.x / GS_TILE);
+    const int px = (lt % gw) * GS_TILE + tile_px(threadIdx.x);
+    const int py = (lt / gw) * GS_TILE + tile_py(threadIdx.x);
     const bool inside = px < W && py < H;
     // tile-relative pixel coordinates (the staged means are moved to the same origin)
     const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
-    const float fpx = (float)(threadIdx.x % GS_TILE), fpy = (float)(threadIdx.x / GS_TILE);
+    const float fpx = (float)tile_px(threadIdx.x), fpy = (float)tile_py(threadIdx.x);
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
@@ -626,8 +635,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
         for (int q = threadIdx.x; q < BATCH * 9; q += GS_TILE_PIX) s_acc[q] = 0.0f;
         __syncthreads();
         unsigned char* wl = s_wl[threadIdx.x >> 5];
-        const int nw = warp_compact(sb, cnt, fpx - (float)(threadIdx.x % GS_TILE),
-                                    (float)(2 * (threadIdx.x >> 5)), wl);
+        const int nw = warp_compact(sb, cnt, warp_x0(threadIdx.x), warp_y0(threadIdx.x), wl);
         for (int q = nw - 1; q >= 0; q--) {
             const int jj = wl[q];
             const uint32_t pos = (uint32_t)(bstart + jj);
