@@ -601,8 +601,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
         }
         __syncthreads();
     }
-    // colour accumulated behind the current splat, starting with the background
-    float S0 = T * rp.bg[0], S1 = T * rp.bg[1], S2 = T * rp.bg[2];
+    // dL/dC . (colour accumulated behind the current splat), starting with the
+    // background: sg = sum_{behind} w_j (c_j . g) + T_final (bg . g)
+    float sg = T * (rp.bg[0] * g0 + rp.bg[1] * g1 + rp.bg[2] * g2);
     // longest list prefix used by any pixel of the tile
     uint32_t mx = last;
 #pragma unroll
@@ -614,6 +615,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
     if (tile_last > e - s) tile_last = e - s;
     if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
     const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
+    // list positions below lim take part (none for pixels outside the image
+    // or without an upstream gradient)
+    const uint32_t lim = (inside && any_grad) ? last : 0u;
     uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
     const int lane = threadIdx.x & 31;
     // component held by this lane after the transposed reduction
@@ -641,7 +645,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
             const uint32_t pos = (uint32_t)(bstart + jj);
             const float4 a = sb.A[jj];
             const float2 h = sb.H[jj];
-            bool use = inside && any_grad && pos < last;
+            bool use = pos < lim;
             const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
             use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
             n_eval += use;
@@ -663,8 +667,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
                 const float Ti = T * inv_om;
                 const float wgt = alpha * Ti;
                 r[6] = wgt * g0; r[7] = wgt * g1; r8 = wgt * g2;
-                const float dLda = Ti * (b.z * g0 + b.w * g1 + cb * g2) - (S0 * g0 + S1 * g1 + S2 * g2) * inv_om;
-                S0 = fmaf(b.z, wgt, S0); S1 = fmaf(b.w, wgt, S1); S2 = fmaf(cb, wgt, S2);
+                const float cg = b.z * g0 + b.w * g1 + cb * g2;
+                const float dLda = Ti * cg - sg * inv_om;
+                sg = fmaf(wgt, cg, sg);
                 T = Ti;
                 if (!cl) {
                     r[5] = G * dLda;
