@@ -530,7 +530,7 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
+__global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
                                                            const ViewDev* __restrict__ views, RenderParams rp,
                                                            SplatArrays sp, int n, const uint32_t* __restrict__ starts,
                                                            const uint32_t* __restrict__ sorted_idx, uint32_t cap,
@@ -615,9 +615,6 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
     if (tile_last > e - s) tile_last = e - s;
     if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
     const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
-    // list positions below lim take part (none for pixels outside the image
-    // or without an upstream gradient)
-    const uint32_t lim = (inside && any_grad) ? last : 0u;
     uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
     const int lane = threadIdx.x & 31;
     // component held by this lane after the transposed reduction
@@ -645,7 +642,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 5) k_blend_bwd(int n_views, const
             const uint32_t pos = (uint32_t)(bstart + jj);
             const float4 a = sb.A[jj];
             const float2 h = sb.H[jj];
-            bool use = pos < lim;
+            bool use = inside && any_grad && pos < last;
             const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
             use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
             n_eval += use;
