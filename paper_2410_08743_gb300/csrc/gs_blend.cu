@@ -384,33 +384,54 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
                 for (int k = 0; k < LZ_NB / LZ_T; k++) {
                     const int b = threadIdx.x * (LZ_NB / LZ_T) + k;
                     sm.bstart[b] = off;
-                    sm.hist[b] = off;
                     off += c[k];
                 }
                 if (threadIdx.x == 0) sm.bstart[LZ_NB] = n_list;
             }
             __syncthreads();
-            for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
-                const unsigned long long x = keys[s + j];
-                const uint32_t pos = atomicAdd(&sm.hist[((uint32_t)(x >> 32) - lo) >> shift], 1u);
-                tmp[s + pos] = x;
-            }
-            __syncthreads();
-            int cb = 0;
+            // The first runs of buckets are gathered straight into shared memory
+            // by a filtering pass over the tile's keys (most tiles stop within
+            // them, and the rest of the list is never moved).  From the third run
+            // on, or for a bucket larger than the shared buffer, every key is
+            // scattered once into bucket order in global memory instead.
+            bool scattered = false;
+            int cb = 0, run = 0;
             while (cb < LZ_NB) {
                 const uint32_t c0 = sm.bstart[cb];
                 if (c0 >= n_list) break;
                 int cb1 = cb + 1;
                 while (cb1 < LZ_NB && sm.bstart[cb1 + 1] - c0 <= (uint32_t)LZ_CAP) cb1++;
                 const int m = (int)(sm.bstart[cb1] - c0);
+                if (!scattered && (m > LZ_CAP || run >= 2)) {
+                    for (int b = threadIdx.x; b < LZ_NB; b += LZ_T) sm.hist[b] = sm.bstart[b];
+                    __syncthreads();
+                    for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+                        const unsigned long long x = keys[s + j];
+                        const uint32_t pos = atomicAdd(&sm.hist[((uint32_t)(x >> 32) - lo) >> shift], 1u);
+                        tmp[s + pos] = x;
+                    }
+                    __syncthreads();
+                    scattered = true;
+                }
                 if (m > LZ_CAP) {
                     sort_write(tmp + s + c0, keys + s + c0, c0, m);  // one oversized bucket
-                } else {
+                } else if (scattered) {
                     for (int j = threadIdx.x; j < m; j += LZ_T) sm.u.srt.b0[j] = tmp[s + c0 + j];
+                    __syncthreads();
+                    sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
+                } else {
+                    if (threadIdx.x == 0) s_mm[0] = 0u;
+                    __syncthreads();
+                    for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+                        const unsigned long long x = keys[s + j];
+                        const int b = (int)(((uint32_t)(x >> 32) - lo) >> shift);
+                        if (b >= cb && b < cb1) sm.u.srt.b0[atomicAdd(&s_mm[0], 1u)] = x;
+                    }
                     __syncthreads();
                     sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
                 }
                 n_sorted = c0 + (uint32_t)m;
+                run++;
                 if (blend_range(c0, c0 + (uint32_t)m)) break;
                 cb = cb1;
             }
