@@ -208,6 +208,9 @@ def run_gpu(args):
     p["sh_degree"] = int(sc["sh_degree"])
     P = torch.from_numpy(poses).to(dev)
     r = Renderer(local)
+    # scene load: Gaussians stored in Morton order of their means (gs_spatial_order)
+    p, _ = L.spatially_ordered(r.ctx, p)
+    torch.cuda.synchronize()
     # targets: renders of the same scene at slightly different poses (untimed)
     tgt = r.forward(p, views, torch.from_numpy(w["target_poses"]).to(dev)).clone()
     grads = {k: torch.zeros_like(p[k]) for k in ("means", "scales", "quats", "opac", "sh")}
@@ -332,7 +335,7 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         r.set_flags(L.GS_F_HOST_IO)
-        hp = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
+        hp = {k: p[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
         hposes = torch.from_numpy(poses).pin_memory()
         htgt = tgt.cpu().pin_memory()
         hg = {k: torch.zeros_like(hp[k]).pin_memory() for k in hp}
@@ -416,6 +419,7 @@ def run_gpu(args):
             "config": {"workload": f"batched fwd+bwd: {n} Gaussians SH3, {V} views mixed 256x192/504x378/1008x756 "
                                    f"({npix / 1e6:.2f} Mpix/step/GPU), L1 loss, all Gaussian grads + {V} pose grads",
                        "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
+                       "layout": "Gaussians in Morton order of their means (gs_spatial_order at scene load)",
                        "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
             "plain_value": plain_value, "graph_value": graph_value, "serving": serving,
             "joint": joint, "trajectory": traj, "extras": extras,
@@ -524,7 +528,7 @@ def run_joint(dev, args, iterations: int = 1000):
         del pg
         raw = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in synth.perturb_scene_raw(12, sc).items()}
         P = torch.from_numpy(w["init_poses"]).to(dev)
-        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=iterations + V)
+        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=iterations + V, spatial_order=True)
         for k in range(V):
             J.step(k)
         torch.cuda.synchronize()
@@ -574,7 +578,7 @@ def run_trajectory(dev, args, batch: int = 8, epochs: int = 1):
         raw = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
                for k, a in synth.perturb_scene_raw(13, sc, means_std=0.005).items()}
         P = torch.from_numpy(w["init_poses"]).to(dev)
-        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=(epochs + 1) * nb)
+        J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=(epochs + 1) * nb, spatial_order=True)
         for b in range(nb):
             J.step(b * batch, min(V, (b + 1) * batch))
         torch.cuda.synchronize()

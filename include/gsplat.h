@@ -270,6 +270,24 @@ int gs_prune_threshold(gs_ctx* ctx, int64_t n, const float* opacities, int64_t n
 int gs_compact(gs_ctx* ctx, int64_t n, const float* opacities, float threshold, int n_arrays,
                const float* const* src, float* const* dst, const int32_t* widths, int64_t* n_keep, void* stream);
 
+/* ------------------------------------------------------------ spatial order
+ * (No counterpart in the paper: a data-layout step.)  The renderer's passes
+ * over (view, Gaussian) pairs run in Gaussian index order, so Gaussians that
+ * are close in space but far apart in memory scatter every block's keys over
+ * many tiles and its gathers over many cache lines.  gs_spatial_order writes
+ * to perm (device uint32 [n]) the order of the Gaussians by the Morton
+ * (Z-order) code of their means (device [n][3]) on a 1024^3 grid over the
+ * means' bounding box, ties by index; gs_gather_rows then writes
+ * dst[a][j] = src[a][perm[j]] (rows of widths[a] floats, out of place, up to
+ * 24 arrays), e.g. every parameter array of a scene before it is loaded.
+ * Rendering a reordered scene gives the same image (up to the order of
+ * Gaussians at exactly equal depth) and the gradients in the new order.
+ * Errors: GS_EINVAL, GS_ENOMEM (scratch of 16 bytes per Gaussian), GS_ECUDA.
+ * Asynchronous. */
+int gs_spatial_order(gs_ctx* ctx, int64_t n, const float* means, uint32_t* perm, void* stream);
+int gs_gather_rows(gs_ctx* ctx, int64_t n, const uint32_t* perm, int n_arrays, const float* const* src,
+                   float* const* dst, const int32_t* widths, void* stream);
+
 /* ------------------------------------------------------------ tuning
  * Launch parameters that change performance but never results: the number of
  * Gaussians per CTA of the tile counting / key scatter (1024..8192), the run

@@ -30,7 +30,7 @@ EXPORTED = (
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
     "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
     "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact", "gs_unproject", "gs_knn_mean_dist",
-    "gs_init_from_points",
+    "gs_init_from_points", "gs_spatial_order", "gs_gather_rows",
 )
 GS_POSE_SE3, GS_POSE_TXSO3 = 0, 1
 
@@ -173,6 +173,10 @@ def load(path: str | None = None):
     L.gs_knn_mean_dist.restype = C.c_int
     L.gs_init_from_points.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_float, C.c_float, C.POINTER(gs_raw_params), vp]
     L.gs_init_from_points.restype = C.c_int
+    L.gs_spatial_order.argtypes = [vp, C.c_int64, vp, vp, vp]
+    L.gs_spatial_order.restype = C.c_int
+    L.gs_gather_rows.argtypes = [vp, C.c_int64, vp, C.c_int, vp, vp, vp, vp]
+    L.gs_gather_rows.restype = C.c_int
     L.gs_status.argtypes = [vp, vp]
     L.gs_frames_query.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.gs_ctx_set_profiling.argtypes = [vp, i32]
@@ -372,6 +376,35 @@ def gs_init_from_points(ctx: int, points, colours, mean_dist, raw: dict, n: int 
                        _ptr(raw["sh"]))
     _ck(load().gs_init_from_points(C.c_void_p(ctx), n, _ptr(points), _ptr(colours), _ptr(mean_dist),
                                    float(min_scale), float(opacity), C.byref(rp), _stream(stream)))
+
+
+def gs_spatial_order(ctx: int, means, perm, stream=None) -> None:
+    """perm (device int32 [n], read as uint32): the Morton order of the means."""
+    _ck(load().gs_spatial_order(C.c_void_p(ctx), int(means.shape[0]), _ptr(means), _ptr(perm), _stream(stream)))
+
+
+def gs_gather_rows(ctx: int, perm, src: list, dst: list, widths: list, stream=None) -> None:
+    k = len(src)
+    s_arr = (C.c_void_p * max(k, 1))(*[_ptr(a) for a in src])
+    d_arr = (C.c_void_p * max(k, 1))(*[_ptr(a) for a in dst])
+    w_arr = (C.c_int32 * max(k, 1))(*[int(w) for w in widths])
+    _ck(load().gs_gather_rows(C.c_void_p(ctx), int(perm.shape[0]), _ptr(perm), k, C.cast(s_arr, C.c_void_p),
+                              C.cast(d_arr, C.c_void_p), C.cast(w_arr, C.c_void_p), _stream(stream)))
+
+
+def spatially_ordered(ctx: int, params: dict, stream=None):
+    """Returns (params in Morton order, perm) for a scene dict of device
+    tensors (means, scales, quats, opac, sh, sh_degree)."""
+    import torch
+    n = int(params["means"].shape[0])
+    perm = torch.empty(n, dtype=torch.int32, device=params["means"].device)
+    gs_spatial_order(ctx, params["means"], perm, stream)
+    names = [("means", 3), ("scales", 3), ("quats", 4), ("opac", 1), ("sh", 48)]
+    out = {k: torch.empty_like(params[k]) for k, _ in names}
+    gs_gather_rows(ctx, perm, [params[k] for k, _ in names], [out[k] for k, _ in names], [w for _, w in names],
+                   stream)
+    out["sh_degree"] = params["sh_degree"]
+    return out, perm
 
 
 def gs_loss_dssim_static(image, target, width: int, height: int, w_dssim: float, dl_dimage, loss=None,

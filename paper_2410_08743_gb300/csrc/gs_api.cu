@@ -1102,6 +1102,57 @@ int gs_init_from_points(gs_ctx* ctx, int64_t n, const float* points, const float
     return GS_OK;
 }
 
+int gs_spatial_order(gs_ctx* ctx, int64_t n, const float* means, uint32_t* perm, void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    if (n < 0 || n > INT32_MAX / 4) return fail(GS_EINVAL, "bad n");
+    if (n == 0) return GS_OK;
+    if (!means || !perm) return fail(GS_EINVAL, "NULL means or perm");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    const int nb = gs::spatial_order_blocks((int)n);
+    const size_t key_bytes = sizeof(unsigned long long) * (size_t)n;
+    const size_t bytes = 2 * key_bytes + sizeof(float) * 6 * (size_t)nb + sizeof(uint32_t) * 16;
+    if ((rc = reg_scratch(ctx, bytes))) return rc;
+    unsigned long long* keys = static_cast<unsigned long long*>(ctx->reg_scratch);
+    unsigned long long* tmp = keys + n;
+    float* part = reinterpret_cast<float*>(tmp + n);
+    uint32_t* small = reinterpret_cast<uint32_t*>(part + 6 * nb);
+    uint32_t* starts = small;          // [2]
+    uint32_t* lists = small + 2;       // [3]
+    uint32_t* counters = small + 5;    // [8]
+    {
+        PROF(PK_INIT, 7);
+        gs::launch_spatial_keys((int)n, means, part, keys, starts, s);
+        gs::launch_segment_sort(1, starts, keys, tmp, perm, (uint32_t)n, lists, counters, s);
+    }
+    CK_LAUNCH();
+    return GS_OK;
+}
+
+int gs_gather_rows(gs_ctx* ctx, int64_t n, const uint32_t* perm, int n_arrays, const float* const* src,
+                   float* const* dst, const int32_t* widths, void* stream) {
+    if (!ctx) return fail(GS_EINVAL, "ctx is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(GS_EINVAL, "bad n");
+    if (n_arrays < 0 || n_arrays > GS_COMPACT_MAX) return fail(GS_EINVAL, "at most %d arrays", GS_COMPACT_MAX);
+    if (n > 0 && (!perm || (n_arrays > 0 && (!src || !dst || !widths)))) return fail(GS_EINVAL, "NULL argument");
+    gs::CompactArrays ca{};
+    ca.count = n_arrays;
+    for (int a = 0; a < n_arrays; a++) {
+        if (!src[a] || !dst[a] || widths[a] < 1) return fail(GS_EINVAL, "bad array %d", a);
+        if (src[a] == dst[a]) return fail(GS_EINVAL, "array %d: the gather is out of place", a);
+        ca.src[a] = src[a]; ca.dst[a] = dst[a]; ca.width[a] = widths[a];
+    }
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        PROF(PK_INIT, 1);
+        gs::launch_gather_rows((int)n, perm, ca, s);
+    }
+    CK_LAUNCH();
+    return GS_OK;
+}
+
 int gs_compact(gs_ctx* ctx, int64_t n, const float* opacities, float threshold, int n_arrays, const float* const* src,
                float* const* dst, const int32_t* widths, int64_t* n_keep, void* stream) {
     if (!ctx || !n_keep) return fail(GS_EINVAL, "NULL argument");

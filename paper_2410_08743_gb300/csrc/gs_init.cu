@@ -1,8 +1,11 @@
-// gs_init.cu - Gaussians initialised from one frame and a depth map, the
-// first stage of relative pose estimation (Sec. 3.4): a subset of the pixels
-// is unprojected with the intrinsics into a point cloud, every point becomes
-// an isotropic Gaussian with the pixel's colour, and its scale is the mean
-// 3D distance to its three nearest neighbours.
+// gs_init.cu - preparing Gaussians.
+//  * From one frame and a depth map, the first stage of relative pose
+//    estimation (Sec. 3.4): a subset of the pixels is unprojected with the
+//    intrinsics into a point cloud, every point becomes an isotropic Gaussian
+//    with the pixel's colour, and its scale is the mean 3D distance to its
+//    three nearest neighbours.
+//  * A spatial (Morton) order of a scene's Gaussians and the row gather that
+//    applies it.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -137,6 +140,108 @@ void launch_init_raw(int n, const float* pts, const float* cols, const float* di
     if (n <= 0) return;
     k_init_raw<<<(n + INIT_T - 1) / INIT_T, INIT_T, 0, s>>>(n, pts, cols, dist, min_scale, logit_o, means,
                                                              log_scales, quats, logit_opac, sh);
+}
+
+// ------------------------------------------------------------ spatial order
+// Morton (Z-order) code of every Gaussian mean on a 1024^3 grid over the
+// means' bounding box; sorting by it places Gaussians that are close in space
+// close in memory, so the per-(view, Gaussian) passes of the renderer touch
+// few tiles per block of Gaussians and read their records coherently.
+__global__ void __launch_bounds__(INIT_T) k_bbox_partial(int n, const float* __restrict__ means,
+                                                         float* __restrict__ part) {
+    __shared__ float red[6][INIT_T / 32];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * INIT_T + threadIdx.x; i < n; i += gridDim.x * INIT_T)
+        for (int a = 0; a < 3; a++) {
+            const float x = means[3 * i + a];
+            mn[a] = fminf(mn[a], x);
+            mx[a] = fmaxf(mx[a], x);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 3; a++) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; a++) { red[a][threadIdx.x >> 5] = mn[a]; red[3 + a][threadIdx.x >> 5] = mx[a]; }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = red[threadIdx.x][0];
+        for (int w = 1; w < INIT_T / 32; w++)
+            v = threadIdx.x < 3 ? fminf(v, red[threadIdx.x][w]) : fmaxf(v, red[threadIdx.x][w]);
+        part[6 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    // bits b0..b9 of v to positions 0, 3, 6, ..., 27
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// key = morton << 32 | index; the box comes from nb partial boxes.  The grid
+// coordinate is floor((x - lo) * (1024 / (hi - lo))) in FP32 with every
+// operation rounded (no contraction), clamped to [0, 1023].
+__global__ void k_morton_keys(int n, int nb, const float* __restrict__ means, const float* __restrict__ part,
+                              unsigned long long* __restrict__ keys) {
+    __shared__ float lo[3], sc[3];
+    if (threadIdx.x < 3) {
+        float a = INFINITY, b = -INFINITY;
+        for (int k = 0; k < nb; k++) {
+            a = fminf(a, part[6 * k + threadIdx.x]);
+            b = fmaxf(b, part[6 * k + 3 + threadIdx.x]);
+        }
+        const float ext = __fsub_rn(b, a);
+        lo[threadIdx.x] = a;
+        sc[threadIdx.x] = ext > 0.0f ? __fdiv_rn(1024.0f, ext) : 0.0f;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * INIT_T + threadIdx.x;
+    if (i >= n) return;
+    uint32_t code = 0;
+    for (int a = 0; a < 3; a++) {
+        float q = floorf(__fmul_rn(__fsub_rn(means[3 * i + a], lo[a]), sc[a]));
+        q = fminf(fmaxf(q, 0.0f), 1023.0f);
+        code |= spread3((uint32_t)q) << a;
+    }
+    keys[i] = ((unsigned long long)code << 32) | (uint32_t)i;
+}
+
+__global__ void k_one_segment(uint32_t n, uint32_t* __restrict__ starts) {
+    if (threadIdx.x == 0) { starts[0] = 0u; starts[1] = n; }
+}
+
+int spatial_order_blocks(int n) { return max(1, min((n + INIT_T - 1) / INIT_T, 4 * 152)); }
+
+void launch_spatial_keys(int n, const float* means, float* part, unsigned long long* keys, uint32_t* starts,
+                         cudaStream_t s) {
+    const int nb = spatial_order_blocks(n);
+    k_bbox_partial<<<nb, INIT_T, 0, s>>>(n, means, part);
+    k_morton_keys<<<(n + INIT_T - 1) / INIT_T, INIT_T, 0, s>>>(n, nb, means, part, keys);
+    k_one_segment<<<1, 32, 0, s>>>((uint32_t)n, starts);
+}
+
+// dst[j] = src[perm[j]] for row arrays (gather by a permutation).
+__global__ void k_gather_rows(int n, const uint32_t* __restrict__ perm, CompactArrays ca) {
+    const int j = blockIdx.x * INIT_T + threadIdx.x;
+    if (j >= n) return;
+    const size_t i = perm[j];
+    for (int a = 0; a < ca.count; a++) {
+        const int w = ca.width[a];
+        const float* src = ca.src[a] + i * w;
+        float* dst = ca.dst[a] + (size_t)j * w;
+        for (int c = 0; c < w; c++) dst[c] = src[c];
+    }
+}
+
+void launch_gather_rows(int n, const uint32_t* perm, const CompactArrays& ca, cudaStream_t s) {
+    if (n <= 0) return;
+    k_gather_rows<<<(n + INIT_T - 1) / INIT_T, INIT_T, 0, s>>>(n, perm, ca);
 }
 
 }  // namespace gs

@@ -186,6 +186,11 @@ void launch_knn_mean(int n, const float* pts, int k, float* out, cudaStream_t s)
 void launch_init_raw(int n, const float* pts, const float* cols, const float* dist, float min_scale, float logit_o,
                      float* means, float* log_scales, float* quats, float* logit_opac, float* sh, cudaStream_t s);
 
+int spatial_order_blocks(int n);
+void launch_spatial_keys(int n, const float* means, float* part, unsigned long long* keys, uint32_t* starts,
+                         cudaStream_t s);
+void launch_gather_rows(int n, const uint32_t* perm, const CompactArrays& ca, cudaStream_t s);
+
 // One parameter group of the Gaussian Adam update (gs_pose.cu).
 struct AdamGroup {
     float* p;          // raw parameter

@@ -45,8 +45,21 @@ class JointRefiner:
                  targets: list, w_l1: float = 0.8, w_dssim: float = 0.2, gaussian_lrs: dict | None = None,
                  pose_lr: tuple = (1e-2, 1e-4), iterations: int = 1000, refine_gaussians: bool = True,
                  group=None, aniso_r: float | None = None, lambda_aniso: float = 0.0, lambda_opacity: float = 0.0,
-                 opacity_l1_iters: int = 10000, refine_poses: bool = True):
+                 opacity_l1_iters: int = 10000, refine_poses: bool = True, spatial_order: bool = False):
         self.r = renderer
+        self.perm = None
+        if spatial_order:
+            # Gaussians in Morton order of their means (a layout step: the same
+            # scene, better locality in every per-(view, Gaussian) pass);
+            # self.perm[j] is the caller's index of row j
+            n0 = raw["means"].shape[0]
+            self.perm = torch.empty(n0, dtype=torch.int32, device=raw["means"].device)
+            L.gs_spatial_order(renderer.ctx, raw["means"], self.perm)
+            names = [("means", 3), ("log_scales", 3), ("quats", 4), ("logit_opac", 1), ("sh", 48)]
+            out = {k: torch.empty_like(raw[k]) for k, _ in names}
+            L.gs_gather_rows(renderer.ctx, self.perm, [raw[k] for k, _ in names], [out[k] for k, _ in names],
+                             [w for _, w in names])
+            raw = out
         self.raw = raw
         self.deg = int(sh_degree)
         self.views = views
