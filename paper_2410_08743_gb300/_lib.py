@@ -67,7 +67,8 @@ class gs_grads(C.Structure):
 
 
 class gs_tuning(C.Structure):
-    _fields_ = [("scatter_chunk", C.c_int32), ("sort_chunk", C.c_int32), ("preprocess_threads", C.c_int32)]
+    _fields_ = [("scatter_chunk", C.c_int32), ("sort_chunk", C.c_int32), ("preprocess_threads", C.c_int32),
+                ("bwd_pixels_per_thread", C.c_int32)]
 
 
 class gs_raw_params(C.Structure):
@@ -480,8 +481,9 @@ def gs_server_destroy(srv: int) -> None:
     load().gs_server_destroy(C.c_void_p(srv))
 
 
-def gs_ctx_set_tuning(ctx: int, scatter_chunk: int, sort_chunk: int, preprocess_threads: int) -> None:
-    t = gs_tuning(int(scatter_chunk), int(sort_chunk), int(preprocess_threads))
+def gs_ctx_set_tuning(ctx: int, scatter_chunk: int, sort_chunk: int, preprocess_threads: int,
+                      bwd_pixels_per_thread: int = 1) -> None:
+    t = gs_tuning(int(scatter_chunk), int(sort_chunk), int(preprocess_threads), int(bwd_pixels_per_thread))
     _ck(load().gs_ctx_set_tuning(C.c_void_p(ctx), C.byref(t)))
 
 

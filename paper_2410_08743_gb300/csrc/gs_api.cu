@@ -79,7 +79,7 @@ struct gs_ctx {
     double prof_ms[PK_COUNT] = {};
     long long prof_n[PK_COUNT] = {};
     long long launches = 0;         // kernels launched by this context
-    gs_tuning tune{4096, 2048, 256};  // result-neutral launch parameters
+    gs_tuning tune{4096, 2048, 256, 1};  // result-neutral launch parameters
     // scratch of the regularisers and the pruning select/compaction
     void* reg_scratch = nullptr;
     size_t reg_cap = 0;
@@ -756,7 +756,7 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         gs::launch_blend_bwd(fr->total_tiles, n_views, fr->tile_base.p, fr->vdev.p, rp, fr->splats(), n, fr->starts.p,
                              fr->sorted_idx.p, cap, image, fr->T_final.p, fr->n_contrib.p, loss->kind, loss->w_l1,
                              l1_mask_t, loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr, fr->counters.p + 2,
-                             s);
+                             ctx->tune.bwd_pixels_per_thread, s);
     }
     CK_LAUNCH();
     if (l1_loss) {
@@ -1206,6 +1206,8 @@ int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
     if (t->sort_chunk != 1024 && t->sort_chunk != 2048) return fail(GS_EINVAL, "sort_chunk must be 1024 or 2048");
     if (t->preprocess_threads != 128 && t->preprocess_threads != 256)
         return fail(GS_EINVAL, "preprocess_threads must be 128 or 256");
+    if (t->bwd_pixels_per_thread != 1 && t->bwd_pixels_per_thread != 2)
+        return fail(GS_EINVAL, "bwd_pixels_per_thread must be 1 or 2");
     ctx->tune = *t;
     return GS_OK;
 }
@@ -1232,13 +1234,15 @@ int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, 
     const int chunks[] = {1024, 2048, 4096, 8192};
     const int sorts[] = {1024, 2048};
     const int threads[] = {128, 256};
+    const int bwd_px[] = {1, 2};
     double bms = 1e300;
     gs_tuning bt = saved;
     int rc = GS_OK;
     for (int a : chunks)
         for (int b : sorts)
-            for (int c : threads) {
-                ctx->tune = gs_tuning{a, b, c};
+            for (int c : threads)
+              for (int d : bwd_px) {
+                ctx->tune = gs_tuning{a, b, c, d};
                 for (int r = 0; r <= repeats && rc == GS_OK; r++) {
                     if (r == 1) cudaEventRecord(e0, s);
                     rc = gs_render_forward(ctx, scene, n_views, views, poses, opts, fr, image, nullptr, nullptr, stream);
@@ -1252,7 +1256,7 @@ int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, 
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms / repeats < bms) { bms = ms / repeats; bt = ctx->tune; }
-            }
+              }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->prof = prof;

@@ -68,12 +68,12 @@ __device__ __forceinline__ float warp_x0(int tid) { return (float)(((tid >> 5) &
 __device__ __forceinline__ float warp_y0(int tid) { return (float)((tid >> 6) * WARP_H); }
 
 // Per-warp compaction of a staged batch: the entries (in order) whose alpha
-// box can touch a pixel of this warp's 8x4 footprint (x in [fx0, fx0+7],
-// y in [fy0, fy0+3]).  The test is conservative (0.01 px slack over the
+// box can touch a pixel of this warp's 8 x fh footprint (x in [fx0, fx0+7],
+// y in [fy0, fy0+fh-1]).  The test is conservative (0.01 px slack over the
 // per-pixel box test), so skipping the other entries changes no decision.
 // Returns the number of entries written to wl.
 __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float fx0, float fy0,
-                                            unsigned char* wl) {
+                                            unsigned char* wl, int fh = WARP_H) {
     const int lane = threadIdx.x & 31;
     int n = 0;
     for (int r = 0; r < cnt; r += 32) {
@@ -83,7 +83,7 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
             const float4 a = sb.A[e];
             const float2 h = sb.H[e];
             hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx0 + (float)(WARP_W - 1)) &&
-                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy0 + (float)(WARP_H - 1));
+                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy0 + (float)(fh - 1));
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) wl[n + __popc(m & ((1u << lane) - 1u))] = (unsigned char)e;
@@ -551,152 +551,187 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(int n_views, const int* __restrict__ tile_base,
-                                                           const ViewDev* __restrict__ views, RenderParams rp,
-                                                           SplatArrays sp, int n, const uint32_t* __restrict__ starts,
-                                                           const uint32_t* __restrict__ sorted_idx, uint32_t cap,
-                                                           const float* __restrict__ image,
-                                                           const float* __restrict__ T_final,
-                                                           const uint32_t* __restrict__ n_contrib, int loss_kind,
-                                                           float w_l1, float l1_mask_t,
-                                                           const float* __restrict__ target,
-                                                           const float* __restrict__ dldc, Grad2DArrays g2d,
-                                                           float* __restrict__ tile_loss,
-                                                           unsigned long long* __restrict__ counters) {
+// Per-pixel state of the backward blend.
+struct BwdPixel {
+    float T, g0, g1, g2, sg;
+    uint32_t last;
+    bool inside;
+};
+
+// PX pixels per thread (1 or 2): each warp covers an 8 x (4 PX) pixel block,
+// 8 / PX warps a tile.  With two pixels a lane sums both pixels' contributions
+// before the warp reduction, so one reduction serves 64 pixels.
+template <int PX>
+__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 8) k_blend_bwd(
+    int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
+    int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
+    const float* __restrict__ image, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+    int loss_kind, float w_l1, float l1_mask_t, const float* __restrict__ target, const float* __restrict__ dldc,
+    Grad2DArrays g2d, float* __restrict__ tile_loss, unsigned long long* __restrict__ counters) {
+    constexpr int NT = GS_TILE_PIX / PX;   // threads
+    constexpr int NW = NT / 32;            // warps
     __shared__ SplatBatch sb;
     __shared__ uint32_t s_idx[BATCH];
-    __shared__ uint32_t s_max[GS_TILE_PIX / 32];
+    __shared__ uint32_t s_max[NW];
     __shared__ float s_acc[BATCH * 9];
-    __shared__ unsigned char s_wl[GS_TILE_PIX / 32][BATCH];
+    __shared__ unsigned char s_wl[NW][BATCH];
     const int t = blockIdx.x;
     const int v = view_of_tile(tile_base, n_views, t);
     const ViewDev& vd = views[v];
     const int W = vd.W, H = vd.H, gw = vd.gw;
     const int lt = t - vd.tile_base;
-    const int px = (lt % gw) * GS_TILE + tile_px(threadIdx.x);
-    const int py = (lt / gw) * GS_TILE + tile_py(threadIdx.x);
-    const bool inside = px < W && py < H;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // warp footprint origin and this lane's first pixel (tile-relative)
+    const int wx0 = (wid & 1) * WARP_W, wy0 = (wid >> 1) * (WARP_H * PX);
+    const int lx = wx0 + (lane & (WARP_W - 1)), ly = wy0 + (lane >> 3);
+    const int tx0 = (lt % gw) * GS_TILE, ty0 = (lt / gw) * GS_TILE;
     // tile-relative pixel coordinates (the staged means are moved to the same origin)
-    const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
-    const float fpx = (float)tile_px(threadIdx.x), fpy = (float)tile_py(threadIdx.x);
+    const float ox = (float)tx0, oy = (float)ty0;
+    const float fpx = (float)lx;
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
     const size_t vbase = (size_t)v * n;
-    // per-pixel state
-    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, l1 = 0.0f;
-    uint32_t last = 0;
-    if (inside) {
-        const size_t p = (size_t)py * W + px;
-        const size_t np = (size_t)W * H;
-        T = T_final[vd.pix_off + p];
-        last = n_contrib[vd.pix_off + p];
-        const float* img = image + vd.img_off;
-        if (loss_kind == GS_LOSS_DLDC || loss_kind == GS_LOSS_L1_DSSIM) {
-            const float* d = dldc + vd.img_off;
-            g0 = d[p]; g1 = d[np + p]; g2 = d[2 * np + p];
+    BwdPixel pix[PX];
+    float l1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        BwdPixel& P = pix[q];
+        const int px = tx0 + lx, py = ty0 + ly + WARP_H * q;
+        P.inside = px < W && py < H;
+        P.T = 1.0f; P.g0 = P.g1 = P.g2 = 0.0f; P.last = 0;
+        if (P.inside) {
+            const size_t p = (size_t)py * W + px;
+            const size_t np = (size_t)W * H;
+            P.T = T_final[vd.pix_off + p];
+            P.last = n_contrib[vd.pix_off + p];
+            const float* img = image + vd.img_off;
+            if (loss_kind == GS_LOSS_DLDC || loss_kind == GS_LOSS_L1_DSSIM) {
+                const float* d = dldc + vd.img_off;
+                P.g0 = d[p]; P.g1 = d[np + p]; P.g2 = d[2 * np + p];
+            }
+            // L1 term (Eq. 16), or its confidence-masked form (Eq. 20-21): pixels
+            // whose accumulated alpha 1 - T is not above the mask threshold
+            // contribute nothing
+            if ((loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM || loss_kind == GS_LOSS_L1_MASKED) &&
+                P.T < l1_mask_t) {
+                const float* tg = target + vd.img_off;
+                const float sc = w_l1 * vd.inv_npix3;
+                const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
+                P.g0 += d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+                P.g1 += d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+                P.g2 += d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+                l1 += fabsf(d0) + fabsf(d1) + fabsf(d2);
+            }
         }
-        // L1 term (Eq. 16), or its confidence-masked form (Eq. 20-21): pixels whose
-        // accumulated alpha 1 - T is not above the mask threshold contribute nothing
-        if ((loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM || loss_kind == GS_LOSS_L1_MASKED) &&
-            T < l1_mask_t) {
-            const float* tg = target + vd.img_off;
-            const float sc = w_l1 * vd.inv_npix3;
-            const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
-            g0 += d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
-            g1 += d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
-            g2 += d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
-            l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
-        }
+        // dL/dC . (colour accumulated behind the current splat), starting with
+        // the background: sg = sum_{behind} w_j (c_j . g) + T_final (bg . g)
+        P.sg = P.T * (rp.bg[0] * P.g0 + rp.bg[1] * P.g1 + rp.bg[2] * P.g2);
+        if (!(P.inside && ((P.g0 != 0.f) | (P.g1 != 0.f) | (P.g2 != 0.f)))) P.last = 0;  // takes no part
     }
     if (tile_loss) {
         float r = l1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = __float_as_uint(r);
+        if (lane == 0) s_max[wid] = __float_as_uint(r);
         __syncthreads();
         if (threadIdx.x == 0) {
             float acc = 0.0f;
-            for (int w = 0; w < GS_TILE_PIX / 32; w++) acc += __uint_as_float(s_max[w]);
+            for (int w = 0; w < NW; w++) acc += __uint_as_float(s_max[w]);
             tile_loss[t] = acc;
         }
         __syncthreads();
     }
-    // dL/dC . (colour accumulated behind the current splat), starting with the
-    // background: sg = sum_{behind} w_j (c_j . g) + T_final (bg . g)
-    float sg = T * (rp.bg[0] * g0 + rp.bg[1] * g1 + rp.bg[2] * g2);
-    // longest list prefix used by any pixel of the tile
-    uint32_t mx = last;
+    // longest list prefix used by any pixel of the tile (n_contrib of the
+    // pixels that take part)
+    uint32_t mx = 0;
+#pragma unroll
+    for (int q = 0; q < PX; q++) mx = max(mx, pix[q].last);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    if (lane == 0) s_max[wid] = mx;
     __syncthreads();
     uint32_t tile_last = 0;
-    for (int w = 0; w < GS_TILE_PIX / 32; w++) tile_last = max(tile_last, s_max[w]);
+    for (int w = 0; w < NW; w++) tile_last = max(tile_last, s_max[w]);
     if (tile_last > e - s) tile_last = e - s;
     if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
-    const bool any_grad = (g0 != 0.f) | (g1 != 0.f) | (g2 != 0.f);
     uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
-    const int lane = threadIdx.x & 31;
     // component held by this lane after the transposed reduction
     const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t id = sorted_idx[s + bstart + threadIdx.x];
+        for (int j = threadIdx.x; j < cnt; j += NT) {
+            const uint32_t id = sorted_idx[s + bstart + j];
             const size_t k = vbase + id;
             const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
-            s_idx[threadIdx.x] = id;
-            sb.A[threadIdx.x] = a;
-            sb.B[threadIdx.x] = b;
-            sb.Cb[threadIdx.x] = sp.Cb[k];
-            sb.H[threadIdx.x] = alpha_box(a, b, rp.alpha_min);
+            s_idx[j] = id;
+            sb.A[j] = a;
+            sb.B[j] = b;
+            sb.Cb[j] = sp.Cb[k];
+            sb.H[j] = alpha_box(a, b, rp.alpha_min);
         }
-        for (int q = threadIdx.x; q < BATCH * 9; q += GS_TILE_PIX) s_acc[q] = 0.0f;
+        for (int q = threadIdx.x; q < BATCH * 9; q += NT) s_acc[q] = 0.0f;
         __syncthreads();
-        unsigned char* wl = s_wl[threadIdx.x >> 5];
-        const int nw = warp_compact(sb, cnt, warp_x0(threadIdx.x), warp_y0(threadIdx.x), wl);
-        for (int q = nw - 1; q >= 0; q--) {
-            const int jj = wl[q];
+        unsigned char* wl = s_wl[wid];
+        const int nw = warp_compact(sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
+        for (int qq = nw - 1; qq >= 0; qq--) {
+            const int jj = wl[qq];
             const uint32_t pos = (uint32_t)(bstart + jj);
             const float4 a = sb.A[jj];
             const float2 h = sb.H[jj];
-            bool use = inside && any_grad && pos < last;
-            const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
-            use = use && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
-            n_eval += use;
-            if (!__any_sync(0xffffffffu, use)) continue;
+            const float dx = __fsub_rn(fpx, a.x);
+            bool use[PX];
+            float dy[PX];
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < PX; q++) {
+                dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
+                use[q] = pos < pix[q].last && fabsf(dx) <= h.x && fabsf(dy[q]) <= h.y;
+                n_eval += use[q];
+                any |= use[q];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
             n_w1++;
             const float4 b = sb.B[jj];
-            float G = 0.f, alpha = 0.f;
-            bool cl = false;
-            if (use) use = pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl);
-            if (!__any_sync(0xffffffffu, use)) continue;
+            float G[PX], alpha[PX];
+            bool cl[PX];
+            any = false;
+#pragma unroll
+            for (int q = 0; q < PX; q++) {
+                G[q] = 0.f; alpha[q] = 0.f; cl[q] = false;
+                if (use[q]) use[q] = pair_alpha(a, b, dx, dy[q], rp.alpha_min, rp.alpha_max, G[q], alpha[q], cl[q]);
+                any |= use[q];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
             n_w2++;
-            n_used += use;
             float r[8], r8 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; c++) r[c] = 0.0f;
-            if (use) {
-                const float cb = sb.Cb[jj];
-                const float inv_om = __fdividef(1.0f, 1.0f - alpha);
-                const float Ti = T * inv_om;
-                const float wgt = alpha * Ti;
-                r[6] = wgt * g0; r[7] = wgt * g1; r8 = wgt * g2;
-                const float cg = b.z * g0 + b.w * g1 + cb * g2;
-                const float dLda = Ti * cg - sg * inv_om;
-                sg = fmaf(wgt, cg, sg);
-                T = Ti;
-                if (!cl) {
-                    r[5] = G * dLda;
-                    const float dp = alpha * dLda;
-                    r[0] = dp * (a.z * dx + a.w * dy);
-                    r[1] = dp * (a.w * dx + b.x * dy);
-                    r[2] = -0.5f * dp * dx * dx;
-                    r[3] = -dp * dx * dy;
-                    r[4] = -0.5f * dp * dy * dy;
+            const float cb = sb.Cb[jj];
+#pragma unroll
+            for (int q = 0; q < PX; q++) {
+                if (!use[q]) continue;
+                n_used++;
+                BwdPixel& P = pix[q];
+                const float inv_om = __fdividef(1.0f, 1.0f - alpha[q]);
+                const float Ti = P.T * inv_om;
+                const float wgt = alpha[q] * Ti;
+                r[6] += wgt * P.g0; r[7] += wgt * P.g1; r8 += wgt * P.g2;
+                const float cg = b.z * P.g0 + b.w * P.g1 + cb * P.g2;
+                const float dLda = Ti * cg - P.sg * inv_om;
+                P.sg = fmaf(wgt, cg, P.sg);
+                P.T = Ti;
+                if (!cl[q]) {
+                    r[5] += G[q] * dLda;
+                    const float dp = alpha[q] * dLda;
+                    const float y = dy[q];
+                    r[0] += dp * (a.z * dx + a.w * y);
+                    r[1] += dp * (a.w * dx + b.x * y);
+                    r[2] += -0.5f * dp * dx * dx;
+                    r[3] += -dp * dx * y;
+                    r[4] += -0.5f * dp * y * y;
                 }
             }
             // transposed reduce-scatter of r[0..7]: afterwards lane L (L % 4 == 0)
@@ -729,14 +764,14 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(int n_views, const
         }
         __syncthreads();
         // one set of vector atomics per (tile, splat) of the batch
-        if ((int)threadIdx.x < cnt) {
-            const float* acc = s_acc + threadIdx.x * 9;
+        for (int j = threadIdx.x; j < cnt; j += NT) {
+            const float* acc = s_acc + j * 9;
             const float4 ga = make_float4(acc[0], acc[1], acc[2], acc[3]);
             const float4 gb = make_float4(acc[4], acc[5], acc[6], acc[7]);
             const bool nz = (ga.x != 0.f) | (ga.y != 0.f) | (ga.z != 0.f) | (ga.w != 0.f) | (gb.x != 0.f) |
                             (gb.y != 0.f) | (gb.z != 0.f) | (gb.w != 0.f) | (acc[8] != 0.f);
             if (nz) {
-                const size_t k = vbase + s_idx[threadIdx.x];
+                const size_t k = vbase + s_idx[j];
                 atomicAdd(g2d.gA + k, ga);
                 atomicAdd(g2d.gB + k, gb);
                 atomicAdd(g2d.gC + k, acc[8]);
@@ -750,7 +785,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(int n_views, const
             ce += __shfl_xor_sync(0xffffffffu, ce, o);
             cu += __shfl_xor_sync(0xffffffffu, cu, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(counters, ce);
             atomicAdd(counters + 1, cu);
             atomicAdd(counters + 7, (unsigned long long)n_w1);   // warp-entries with a pixel in the box
@@ -763,12 +798,16 @@ void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const View
                       SplatArrays sp, int n, const uint32_t* starts, const uint32_t* sorted_idx, uint32_t cap,
                       const float* image, const float* T_final, const uint32_t* n_contrib, int loss_kind, float w_l1,
                       float l1_mask_t, const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
-                      unsigned long long* counters, cudaStream_t s) {
+                      unsigned long long* counters, int px_per_thread, cudaStream_t s) {
     if (n_tiles <= 0) return;
-    k_blend_bwd<<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap, image,
-                                                 T_final, n_contrib, loss_kind, w_l1, l1_mask_t, target, dldc, g2d,
-                                                 tile_loss,
-                                                 counters);
+    if (px_per_thread == 2)
+        k_blend_bwd<2><<<n_tiles, GS_TILE_PIX / 2, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx,
+                                                           cap, image, T_final, n_contrib, loss_kind, w_l1, l1_mask_t,
+                                                           target, dldc, g2d, tile_loss, counters);
+    else
+        k_blend_bwd<1><<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap,
+                                                       image, T_final, n_contrib, loss_kind, w_l1, l1_mask_t, target,
+                                                       dldc, g2d, tile_loss, counters);
 }
 
 }  // namespace gs

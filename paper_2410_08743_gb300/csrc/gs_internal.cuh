@@ -144,7 +144,7 @@ void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const View
                       const uint32_t* sorted_idx, uint32_t cap, const float* image, const float* T_final,
                       const uint32_t* n_contrib, int loss_kind, float w_l1, float l1_mask_t, const float* target,
                       const float* dldc, Grad2DArrays g2d, float* tile_loss, unsigned long long* counters,
-                      cudaStream_t s);
+                      int px_per_thread, cudaStream_t s);
 
 void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials,

@@ -182,8 +182,17 @@ def test_forward_image_and_splats(R, case):
     np.testing.assert_allclose(got[ok, 6:9], vals[ok, 6:9], rtol=0, atol=2e-6)
 
 
+@pytest.mark.parametrize("bwd_px", [1, 2], ids=["1px", "2px"])
 @pytest.mark.parametrize("case", GRAD_CASES)
-def test_backward_gradients_and_pose(R, case):
+def test_backward_gradients_and_pose(R, case, bwd_px):
+    L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, bwd_px)
+    try:
+        _backward_case(R, case)
+    finally:
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, 1)
+
+
+def _backward_case(R, case):
     sc, views, poses = CASES[case]()
     p, P, img, _, _ = gpu_forward(R, sc, views, poses)
     ref = oracle.render(sc, views, poses)
