@@ -293,12 +293,13 @@ int gs_gather_rows(gs_ctx* ctx, int64_t n, const uint32_t* perm, int n_arrays, c
  * Gaussians per CTA of the tile counting / key scatter (1024..8192), the run
  * length of the forward blend's lazy tile sort (1024 or 2048 keys), the
  * block size of the forward preprocess (128 or 256 threads) and the pixels
- * each thread of the backward blend handles (1 or 2). */
+ * each thread of the backward and of the forward blend handles (1 or 2). */
 typedef struct {
     int32_t scatter_chunk;
     int32_t sort_chunk;
     int32_t preprocess_threads;
     int32_t bwd_pixels_per_thread;  /* backward blend: 1 (256-thread tiles) or 2 (128) */
+    int32_t fwd_pixels_per_thread;  /* forward blend: 1 or 2, likewise */
 } gs_tuning;
 
 int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t);

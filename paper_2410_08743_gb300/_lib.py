@@ -68,7 +68,7 @@ class gs_grads(C.Structure):
 
 class gs_tuning(C.Structure):
     _fields_ = [("scatter_chunk", C.c_int32), ("sort_chunk", C.c_int32), ("preprocess_threads", C.c_int32),
-                ("bwd_pixels_per_thread", C.c_int32)]
+                ("bwd_pixels_per_thread", C.c_int32), ("fwd_pixels_per_thread", C.c_int32)]
 
 
 class gs_raw_params(C.Structure):
@@ -482,8 +482,9 @@ def gs_server_destroy(srv: int) -> None:
 
 
 def gs_ctx_set_tuning(ctx: int, scatter_chunk: int, sort_chunk: int, preprocess_threads: int,
-                      bwd_pixels_per_thread: int = 1) -> None:
-    t = gs_tuning(int(scatter_chunk), int(sort_chunk), int(preprocess_threads), int(bwd_pixels_per_thread))
+                      bwd_pixels_per_thread: int = 1, fwd_pixels_per_thread: int = 1) -> None:
+    t = gs_tuning(int(scatter_chunk), int(sort_chunk), int(preprocess_threads), int(bwd_pixels_per_thread),
+                  int(fwd_pixels_per_thread))
     _ck(load().gs_ctx_set_tuning(C.c_void_p(ctx), C.byref(t)))
 
 

@@ -79,7 +79,7 @@ struct gs_ctx {
     double prof_ms[PK_COUNT] = {};
     long long prof_n[PK_COUNT] = {};
     long long launches = 0;         // kernels launched by this context
-    gs_tuning tune{4096, 2048, 256, 1};  // result-neutral launch parameters
+    gs_tuning tune{4096, 2048, 256, 1, 1};  // result-neutral launch parameters
     // scratch of the regularisers and the pruning select/compaction
     void* reg_scratch = nullptr;
     size_t reg_cap = 0;
@@ -663,7 +663,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         CK_LAUNCH();
     } else {
         PROF(PK_BLEND_FWD, 1);
-        gs::launch_blend_fwd_lazy(T, ctx->tune.sort_chunk, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
+        gs::launch_blend_fwd_lazy(T, ctx->tune.sort_chunk, ctx->tune.fwd_pixels_per_thread, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
                                   fr->tmp_keys.p, fr->sorted_idx.p, fr->sorted_count.p, cap, image, fr->T_final.p,
                                   fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
         CK_LAUNCH();
@@ -1208,6 +1208,8 @@ int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
         return fail(GS_EINVAL, "preprocess_threads must be 128 or 256");
     if (t->bwd_pixels_per_thread != 1 && t->bwd_pixels_per_thread != 2)
         return fail(GS_EINVAL, "bwd_pixels_per_thread must be 1 or 2");
+    if (t->fwd_pixels_per_thread != 1 && t->fwd_pixels_per_thread != 2)
+        return fail(GS_EINVAL, "fwd_pixels_per_thread must be 1 or 2");
     ctx->tune = *t;
     return GS_OK;
 }
@@ -1241,8 +1243,9 @@ int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, 
     for (int a : chunks)
         for (int b : sorts)
             for (int c : threads)
-              for (int d : bwd_px) {
-                ctx->tune = gs_tuning{a, b, c, d};
+              for (int d : bwd_px)
+                for (int f : bwd_px) {
+                ctx->tune = gs_tuning{a, b, c, d, f};
                 for (int r = 0; r <= repeats && rc == GS_OK; r++) {
                     if (r == 1) cudaEventRecord(e0, s);
                     rc = gs_render_forward(ctx, scene, n_views, views, poses, opts, fr, image, nullptr, nullptr, stream);
@@ -1256,7 +1259,7 @@ int gs_autotune(gs_ctx* ctx, gs_frames* fr, const gs_scene* scene, int n_views, 
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms / repeats < bms) { bms = ms / repeats; bt = ctx->tune; }
-              }
+                }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->prof = prof;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
 #define LZ_NB 1024
 #define LZ_T GS_TILE_PIX
 
-template <int LZ_CAP>
+template <int LZ_CAP, int NT>
 struct LazySmem {
     union {
         struct {
@@ -239,106 +239,131 @@ struct LazySmem {
         } srt;
         SplatBatch sb;  // blending reuses the sort buffers
     } u;
-    uint32_t hist[(LZ_T / 32) * 256];  // radix histograms, then bucket cursors
+    uint32_t hist[(NT / 32) * 256];  // radix histograms, then bucket cursors
     uint32_t bstart[LZ_NB + 1];
-    unsigned char wl[LZ_T / 32][BATCH];  // per-warp compacted batch entries
+    unsigned char wl[NT / 32][BATCH];  // per-warp compacted batch entries
 };
 
-template <int LZ_CAP>
-__global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const int* __restrict__ tile_base,
-                                                         const ViewDev* __restrict__ views, RenderParams rp,
-                                                         SplatArrays sp, int n, const uint32_t* __restrict__ starts,
-                                                         unsigned long long* __restrict__ keys,
-                                                         unsigned long long* __restrict__ tmp,
-                                                         uint32_t* __restrict__ sorted_idx,
-                                                         uint32_t* __restrict__ sorted_count, uint32_t cap,
-                                                         float* __restrict__ image, float* __restrict__ T_final,
-                                                         uint32_t* __restrict__ n_contrib,
-                                                         const float* __restrict__ target,
-                                                         float* __restrict__ tile_loss,
-                                                         unsigned long long* __restrict__ counters) {
+// PX pixels per thread (1 or 2): each warp covers an 8 x (4 PX) pixel block.
+// Two pixels per thread share every shared-memory read of a splat and give
+// each thread two independent compositing chains.
+template <int LZ_CAP, int PX>
+__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 6) k_blend_fwd_lazy(
+    int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
+    int n, const uint32_t* __restrict__ starts, unsigned long long* __restrict__ keys,
+    unsigned long long* __restrict__ tmp, uint32_t* __restrict__ sorted_idx, uint32_t* __restrict__ sorted_count,
+    uint32_t cap, float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib,
+    const float* __restrict__ target, float* __restrict__ tile_loss, unsigned long long* __restrict__ counters) {
+    constexpr int NT = GS_TILE_PIX / PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LazySmem<LZ_CAP>& sm = *reinterpret_cast<LazySmem<LZ_CAP>*>(smem_raw);
-    __shared__ float s_red[LZ_T / 32];
-    __shared__ uint32_t s_warp[LZ_T / 32];
+    LazySmem<LZ_CAP, NT>& sm = *reinterpret_cast<LazySmem<LZ_CAP, NT>*>(smem_raw);
+    __shared__ float s_red[NT / 32];
+    __shared__ uint32_t s_warp[NT / 32];
     __shared__ uint32_t s_mm[2];
     const int t = blockIdx.x;
     const int v = view_of_tile(tile_base, n_views, t);
     const ViewDev& vd = views[v];
     const int W = vd.W, H = vd.H, gw = vd.gw;
     const int lt = t - vd.tile_base;
-    const int px = (lt % gw) * GS_TILE + tile_px(threadIdx.x);
-    const int py = (lt / gw) * GS_TILE + tile_py(threadIdx.x);
-    const bool inside = px < W && py < H;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wx0 = (wid & 1) * WARP_W, wy0 = (wid >> 1) * (WARP_H * PX);
+    const int lx = wx0 + (lane & (WARP_W - 1)), ly = wy0 + (lane >> 3);
+    const int tx0 = (lt % gw) * GS_TILE, ty0 = (lt / gw) * GS_TILE;
     // tile-relative pixel coordinates (the staged means are moved to the same origin)
-    const float ox = (float)((lt % gw) * GS_TILE), oy = (float)((lt / gw) * GS_TILE);
-    const float fpx = (float)tile_px(threadIdx.x), fpy = (float)tile_py(threadIdx.x);
+    const float ox = (float)tx0, oy = (float)ty0;
+    const float fpx = (float)lx;
     uint32_t s = starts[t], e = starts[t + 1];
     if (s > cap) s = cap;
     if (e > cap) e = cap;
     const uint32_t n_list = e - s;
     const size_t vbase = (size_t)v * n;
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0, n_eval = 0, n_blend = 0, n_read = 0, n_went = 0;
-    bool done = !inside;
+    float T[PX], C0[PX], C1[PX], C2[PX];
+    uint32_t last[PX];
+    bool done[PX];
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        T[q] = 1.0f; C0[q] = C1[q] = C2[q] = 0.0f; last[q] = 0;
+        done[q] = !(tx0 + lx < W && ty0 + ly + WARP_H * q < H);
+    }
+    auto all_done = [&]() -> bool {
+        bool d = true;
+#pragma unroll
+        for (int q = 0; q < PX; q++) d = d && done[q];
+        return d;
+    };
+    uint32_t n_eval = 0, n_blend = 0, n_read = 0, n_went = 0;
     uint32_t n_sorted = 0;
 
     // Blends list positions [p0, p1) read from sorted_idx; returns true when
     // every pixel of the tile has stopped.
     auto blend_range = [&](uint32_t p0, uint32_t p1) -> bool {
         for (uint32_t base = p0; base < p1; base += BATCH) {
-            if (__syncthreads_count(done) == LZ_T) return true;
-            const uint32_t j = base + threadIdx.x;
+            if (__syncthreads_count(all_done()) == NT) return true;
             n_read += (threadIdx.x == 0) ? min((uint32_t)BATCH, p1 - base) : 0u;
-            if (j < p1) {
-                const size_t k = vbase + sorted_idx[s + j];
+            const int cnt = (int)min((uint32_t)BATCH, p1 - base);
+            for (int j = threadIdx.x; j < cnt; j += NT) {
+                const size_t k = vbase + sorted_idx[s + base + j];
                 const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
-                sm.u.sb.A[threadIdx.x] = a;
-                sm.u.sb.B[threadIdx.x] = b;
-                sm.u.sb.Cb[threadIdx.x] = sp.Cb[k];
-                sm.u.sb.H[threadIdx.x] = alpha_box(a, b, rp.alpha_min);
+                sm.u.sb.A[j] = a;
+                sm.u.sb.B[j] = b;
+                sm.u.sb.Cb[j] = sp.Cb[k];
+                sm.u.sb.H[j] = alpha_box(a, b, rp.alpha_min);
             }
             __syncthreads();
-            const int cnt = (int)min((uint32_t)BATCH, p1 - base);
-            unsigned char* wl = sm.wl[threadIdx.x >> 5];
-            const int nw = warp_compact(sm.u.sb, cnt, warp_x0(threadIdx.x), warp_y0(threadIdx.x), wl);
-            if (__any_sync(0xffffffffu, !done)) n_went += (uint32_t)nw;
-            if (!done) {
-                for (int q = 0; q < nw; q++) {
-                    const int jj = wl[q];
+            unsigned char* wl = sm.wl[wid];
+            const int nw = warp_compact(sm.u.sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
+            const bool live = !all_done();
+            if (__any_sync(0xffffffffu, live)) n_went += (uint32_t)nw;
+            if (live) {
+                for (int qq = 0; qq < nw; qq++) {
+                    const int jj = wl[qq];
                     const float4 a = sm.u.sb.A[jj];
                     const float2 h = sm.u.sb.H[jj];
-                    const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
-                    if (fabsf(dx) > h.x || fabsf(dy) > h.y) continue;
-                    n_eval++;
+                    const float dx = __fsub_rn(fpx, a.x);
+                    if (fabsf(dx) > h.x) continue;
+                    float dy[PX];
+                    bool inbox[PX], any = false;
+#pragma unroll
+                    for (int q = 0; q < PX; q++) {
+                        dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
+                        inbox[q] = !done[q] && fabsf(dy[q]) <= h.y;
+                        any |= inbox[q];
+                    }
+                    if (!any) continue;
                     const float4 b = sm.u.sb.B[jj];
-                    float G, alpha;
-                    bool cl;
-                    if (!pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
-                    const float Tn = T * (1.0f - alpha);
-                    if (Tn < rp.t_min) { done = true; break; }
-                    n_blend++;
-                    const float w = alpha * T;
-                    C0 = fmaf(b.z, w, C0);
-                    C1 = fmaf(b.w, w, C1);
-                    C2 = fmaf(sm.u.sb.Cb[jj], w, C2);
-                    T = Tn;
-                    last = base + jj + 1;
+#pragma unroll
+                    for (int q = 0; q < PX; q++) {
+                        if (!inbox[q]) continue;
+                        n_eval++;
+                        float G, alpha;
+                        bool cl;
+                        if (!pair_alpha(a, b, dx, dy[q], rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
+                        const float Tn = T[q] * (1.0f - alpha);
+                        if (Tn < rp.t_min) { done[q] = true; continue; }
+                        n_blend++;
+                        const float w = alpha * T[q];
+                        C0[q] = fmaf(b.z, w, C0[q]);
+                        C1[q] = fmaf(b.w, w, C1[q]);
+                        C2[q] = fmaf(sm.u.sb.Cb[jj], w, C2[q]);
+                        T[q] = Tn;
+                        last[q] = base + jj + 1;
+                    }
+                    if (all_done()) break;
                 }
             }
         }
-        return __syncthreads_count(done) == LZ_T;
+        return __syncthreads_count(all_done()) == NT;
     };
     // Sorts list positions [c0, c0 + m) found in src (shared b0 or global) and
     // writes their indices to sorted_idx.
     auto sort_write = [&](unsigned long long* src, unsigned long long* scratch, uint32_t c0, int m) {
-        unsigned long long* r = sort_tile_keys<LZ_T>(src, scratch, m, sm.hist);
-        for (int j = threadIdx.x; j < m; j += LZ_T) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
+        unsigned long long* r = sort_tile_keys<NT>(src, scratch, m, sm.hist);
+        for (int j = threadIdx.x; j < m; j += NT) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
         __syncthreads();
     };
 
     if (n_list <= LZ_CAP) {
-        for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) sm.u.srt.b0[j] = keys[s + j];
+        for (uint32_t j = threadIdx.x; j < n_list; j += NT) sm.u.srt.b0[j] = keys[s + j];
         __syncthreads();
         if (n_list > 0) sort_write(sm.u.srt.b0, sm.u.srt.b1, 0, (int)n_list);
         n_sorted = n_list;
@@ -346,7 +371,7 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
     } else {
         // depth range of the tile
         uint32_t lo = 0xffffffffu, hi = 0u;
-        for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+        for (uint32_t j = threadIdx.x; j < n_list; j += NT) {
             const uint32_t d = (uint32_t)(keys[s + j] >> 32);
             lo = min(lo, d);
             hi = max(hi, d);
@@ -370,19 +395,19 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
         } else {
             const int bits = 32 - __clz(hi - lo);
             const int shift = bits > 10 ? bits - 10 : 0;
-            for (int b = threadIdx.x; b <= LZ_NB; b += LZ_T) sm.bstart[b] = 0u;
+            for (int b = threadIdx.x; b <= LZ_NB; b += NT) sm.bstart[b] = 0u;
             __syncthreads();
-            for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T)
+            for (uint32_t j = threadIdx.x; j < n_list; j += NT)
                 atomicAdd(&sm.bstart[((uint32_t)(keys[s + j] >> 32) - lo) >> shift], 1u);
             __syncthreads();
             {
-                uint32_t c[LZ_NB / LZ_T], sum = 0;
+                uint32_t c[LZ_NB / NT], sum = 0;
 #pragma unroll
-                for (int k = 0; k < LZ_NB / LZ_T; k++) { c[k] = sm.bstart[threadIdx.x * (LZ_NB / LZ_T) + k]; sum += c[k]; }
-                uint32_t off = block_scan_excl<LZ_T>(sum, s_warp);
+                for (int k = 0; k < LZ_NB / NT; k++) { c[k] = sm.bstart[threadIdx.x * (LZ_NB / NT) + k]; sum += c[k]; }
+                uint32_t off = block_scan_excl<NT>(sum, s_warp);
 #pragma unroll
-                for (int k = 0; k < LZ_NB / LZ_T; k++) {
-                    const int b = threadIdx.x * (LZ_NB / LZ_T) + k;
+                for (int k = 0; k < LZ_NB / NT; k++) {
+                    const int b = threadIdx.x * (LZ_NB / NT) + k;
                     sm.bstart[b] = off;
                     off += c[k];
                 }
@@ -403,9 +428,9 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
                 while (cb1 < LZ_NB && sm.bstart[cb1 + 1] - c0 <= (uint32_t)LZ_CAP) cb1++;
                 const int m = (int)(sm.bstart[cb1] - c0);
                 if (!scattered && (m > LZ_CAP || run >= 2)) {
-                    for (int b = threadIdx.x; b < LZ_NB; b += LZ_T) sm.hist[b] = sm.bstart[b];
+                    for (int b = threadIdx.x; b < LZ_NB; b += NT) sm.hist[b] = sm.bstart[b];
                     __syncthreads();
-                    for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+                    for (uint32_t j = threadIdx.x; j < n_list; j += NT) {
                         const unsigned long long x = keys[s + j];
                         const uint32_t pos = atomicAdd(&sm.hist[((uint32_t)(x >> 32) - lo) >> shift], 1u);
                         tmp[s + pos] = x;
@@ -416,13 +441,13 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
                 if (m > LZ_CAP) {
                     sort_write(tmp + s + c0, keys + s + c0, c0, m);  // one oversized bucket
                 } else if (scattered) {
-                    for (int j = threadIdx.x; j < m; j += LZ_T) sm.u.srt.b0[j] = tmp[s + c0 + j];
+                    for (int j = threadIdx.x; j < m; j += NT) sm.u.srt.b0[j] = tmp[s + c0 + j];
                     __syncthreads();
                     sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
                 } else {
                     if (threadIdx.x == 0) s_mm[0] = 0u;
                     __syncthreads();
-                    for (uint32_t j = threadIdx.x; j < n_list; j += LZ_T) {
+                    for (uint32_t j = threadIdx.x; j < n_list; j += NT) {
                         const unsigned long long x = keys[s + j];
                         const int b = (int)(((uint32_t)(x >> 32) - lo) >> shift);
                         if (b >= cb && b < cb1) sm.u.srt.b0[atomicAdd(&s_mm[0], 1u)] = x;
@@ -439,31 +464,35 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
     }
     if (threadIdx.x == 0) sorted_count[t] = n_sorted;
     float l1 = 0.0f;
-    if (inside) {
-        const size_t p = (size_t)py * W + px;
-        const size_t np = (size_t)W * H;
-        float* img = image + vd.img_off;
-        C0 = fmaf(T, rp.bg[0], C0);
-        C1 = fmaf(T, rp.bg[1], C1);
-        C2 = fmaf(T, rp.bg[2], C2);
-        img[p] = C0;
-        img[np + p] = C1;
-        img[2 * np + p] = C2;
-        T_final[vd.pix_off + p] = T;
-        n_contrib[vd.pix_off + p] = last;
-        if (target) {
-            const float* tg = target + vd.img_off;
-            l1 = fabsf(C0 - tg[p]) + fabsf(C1 - tg[np + p]) + fabsf(C2 - tg[2 * np + p]);
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        const int px = tx0 + lx, py = ty0 + ly + WARP_H * q;
+        if (px < W && py < H) {
+            const size_t p = (size_t)py * W + px;
+            const size_t np = (size_t)W * H;
+            float* img = image + vd.img_off;
+            const float c0 = fmaf(T[q], rp.bg[0], C0[q]);
+            const float c1 = fmaf(T[q], rp.bg[1], C1[q]);
+            const float c2 = fmaf(T[q], rp.bg[2], C2[q]);
+            img[p] = c0;
+            img[np + p] = c1;
+            img[2 * np + p] = c2;
+            T_final[vd.pix_off + p] = T[q];
+            n_contrib[vd.pix_off + p] = last[q];
+            if (target) {
+                const float* tg = target + vd.img_off;
+                l1 += fabsf(c0 - tg[p]) + fabsf(c1 - tg[np + p]) + fabsf(c2 - tg[2 * np + p]);
+            }
         }
     }
     if (target) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = l1;
+        if (lane == 0) s_red[wid] = l1;
         __syncthreads();
         if (threadIdx.x == 0) {
             float acc = 0.0f;
-            for (int w = 0; w < LZ_T / 32; w++) acc += s_red[w];
+            for (int w = 0; w < NT / 32; w++) acc += s_red[w];
             tile_loss[t] = acc;
         }
     }
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
             ce += __shfl_xor_sync(0xffffffffu, ce, o);
             cbl += __shfl_xor_sync(0xffffffffu, cbl, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(counters, ce);
             atomicAdd(counters + 1, cbl);
             atomicAdd(counters + 8, (unsigned long long)n_went);   // warp-entries walked
@@ -486,28 +515,40 @@ __global__ void __launch_bounds__(LZ_T, 4) k_blend_fwd_lazy(int n_views, const i
     }
 }
 
-void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int n_views, const int* tile_base, const ViewDev* views,
-                           const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+template <int CAP, int PX>
+static void launch_lazy(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
+                        SplatArrays sp, int n, const uint32_t* starts, unsigned long long* keys,
+                        unsigned long long* tmp, uint32_t* sorted_idx, uint32_t* sorted_count, uint32_t cap,
+                        float* image, float* T_final, uint32_t* n_contrib, const float* target, float* tile_loss,
+                        unsigned long long* counters, cudaStream_t s) {
+    constexpr int NT = GS_TILE_PIX / PX;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_blend_fwd_lazy<CAP, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LazySmem<CAP, NT>));
+        attr = true;
+    }
+    k_blend_fwd_lazy<CAP, PX><<<n_tiles, NT, sizeof(LazySmem<CAP, NT>), s>>>(
+        n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
+        n_contrib, target, tile_loss, counters);
+}
+
+void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int px_per_thread, int n_views, const int* tile_base,
+                           const ViewDev* views, const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
                            unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
                            uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
                            const float* target, float* tile_loss, unsigned long long* counters, cudaStream_t s) {
     if (n_tiles <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_blend_fwd_lazy<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(LazySmem<1024>));
-        cudaFuncSetAttribute(k_blend_fwd_lazy<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(LazySmem<2048>));
-        attr = true;
+#define GS_LAZY_ARGS n_tiles, n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, \
+                     image, T_final, n_contrib, target, tile_loss, counters, s
+    if (sort_chunk <= 1024) {
+        if (px_per_thread == 2) launch_lazy<1024, 2>(GS_LAZY_ARGS);
+        else launch_lazy<1024, 1>(GS_LAZY_ARGS);
+    } else {
+        if (px_per_thread == 2) launch_lazy<2048, 2>(GS_LAZY_ARGS);
+        else launch_lazy<2048, 1>(GS_LAZY_ARGS);
     }
-    if (sort_chunk <= 1024)
-        k_blend_fwd_lazy<1024><<<n_tiles, LZ_T, sizeof(LazySmem<1024>), s>>>(
-            n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
-            n_contrib, target, tile_loss, counters);
-    else
-        k_blend_fwd_lazy<2048><<<n_tiles, LZ_T, sizeof(LazySmem<2048>), s>>>(
-            n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
-            n_contrib, target, tile_loss, counters);
+#undef GS_LAZY_ARGS
 }
 
 void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,

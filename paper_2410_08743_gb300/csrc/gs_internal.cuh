@@ -130,8 +130,8 @@ void launch_blend_fwd(int n_tiles, int n_views, const int* tile_base, const View
                       uint32_t* n_contrib, const float* target, float* tile_loss, unsigned long long* counters,
                       cudaStream_t s);
 
-void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int n_views, const int* tile_base, const ViewDev* views,
-                           const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int px_per_thread, int n_views, const int* tile_base,
+                           const ViewDev* views, const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
                            unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
                            uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
                            const float* target, float* tile_loss, unsigned long long* counters, cudaStream_t s);

@@ -23,7 +23,7 @@ def workload_key(gpu_name: str, views, n_gaussians: int) -> str:
     px = sum(int(v["width"]) * int(v["height"]) for v in views)
     res_class = f"views{len(views)}-px2^{int(round(math.log2(max(px, 1))))}"
     n_class = f"n2^{int(round(math.log2(max(n_gaussians, 1))))}"
-    return f"t2|{gpu_name}|{res_class}|{n_class}"   # t2: the knob set with the backward pixel count
+    return f"t3|{gpu_name}|{res_class}|{n_class}"   # t3: the knob set with the blends' pixel counts
 
 
 def autotune(renderer, params: dict, views, poses, image, loss, grads=None, pose_grad=None, repeats: int = 2,
@@ -42,7 +42,7 @@ def autotune(renderer, params: dict, views, poses, image, loss, grads=None, pose
     if key in cache and not force:
         t = cache[key]["tuning"]
         L.gs_ctx_set_tuning(renderer.ctx, t["scatter_chunk"], t["sort_chunk"], t["preprocess_threads"],
-                            t.get("bwd_pixels_per_thread", 1))
+                            t.get("bwd_pixels_per_thread", 1), t.get("fwd_pixels_per_thread", 1))
         return dict(tuning=t, ms=cache[key]["ms"], cached=True, key=key)
     sc = L.gs_scene_borrow(params["means"], params["scales"], params["quats"], params["opac"], params["sh"],
                            params["sh_degree"])
