@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
 // of a fully sorted list.  The sorted prefix and its length go to sorted_idx /
 // sorted_count for the backward pass, which never reads past it.
 #define LZ_NB 1024
+// the first run of buckets is cut at LZ_FIRST keys: most tiles stop within
+// a few hundred entries, so a short first run sorts little that is not used
+#define LZ_FIRST 512
 #define LZ_T GS_TILE_PIX
 
 template <int LZ_CAP, int NT>
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 6) k_blend_fwd
                 const uint32_t c0 = sm.bstart[cb];
                 if (c0 >= n_list) break;
                 int cb1 = cb + 1;
-                while (cb1 < LZ_NB && sm.bstart[cb1 + 1] - c0 <= (uint32_t)LZ_CAP) cb1++;
+                while (cb1 < LZ_NB && sm.bstart[cb1 + 1] - c0 <= (run == 0 ? (uint32_t)LZ_FIRST : (uint32_t)LZ_CAP)) cb1++;
                 const int m = (int)(sm.bstart[cb1] - c0);
                 if (!scattered && (m > LZ_CAP || run >= 2)) {
                     for (int b = threadIdx.x; b < LZ_NB; b += NT) sm.hist[b] = sm.bstart[b];
