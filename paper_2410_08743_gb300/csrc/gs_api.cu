@@ -919,7 +919,7 @@ int gs_gaussian_adam(gs_ctx* ctx, int64_t n, int sh_degree, gs_raw_params* raw, 
     G[4] = {raw->sh, grads->sh, m + 11 * N, v + 11 * N, nullptr, 48, 3 * (sh_degree + 1) * (sh_degree + 1), 0,
             lrs->sh_dc, lrs->sh_rest, 3};
     {
-        PROF(PK_GAUSS_ADAM, 5);
+        PROF(PK_GAUSS_ADAM, 1);
         gs::launch_gaussian_adam(N, G, 5, b1, b2, eps, step, s);
     }
     CK_LAUNCH();

@@ -167,9 +167,19 @@ void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m,
 // do/dlogit = o (1 - o); it then writes the activated values the next render
 // reads.  One thread per parameter element; element k of Gaussian i in a
 // group of width w lives at i * w + k in both the parameter and moment arrays.
-__global__ void k_gaussian_adam(int64_t n, AdamGroup G, float b1, float b2, float eps, float c1, float c2) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * G.width) return;
+struct AdamGroups {
+    AdamGroup g[5];
+    long long end[5];   // exclusive end of each group's element range (n * width, cumulative)
+    int count;
+};
+
+__global__ void k_gaussian_adam(int64_t n, AdamGroups A, float b1, float b2, float eps, float c1, float c2) {
+    const long long gidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gidx >= A.end[A.count - 1]) return;
+    int gi = 0;
+    while (gi + 1 < A.count && gidx >= A.end[gi]) gi++;
+    const AdamGroup& G = A.g[gi];
+    const int64_t idx = gidx - (gi ? A.end[gi - 1] : 0);
     const int k = (int)(idx % G.width);
     if (k >= G.used) return;
     float p = G.p[idx];
@@ -186,14 +196,20 @@ __global__ void k_gaussian_adam(int64_t n, AdamGroup G, float b1, float b2, floa
     if (G.act) G.act[idx] = G.act_kind == 1 ? expf(p) : 1.0f / (1.0f + expf(-p));
 }
 
+// All groups in one launch: element e of the concatenated group ranges.
 void launch_gaussian_adam(int64_t n, const AdamGroup* groups, int n_groups, float b1, float b2, float eps, int step,
                           cudaStream_t s) {
-    if (n <= 0) return;
+    if (n <= 0 || n_groups <= 0) return;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-    for (int k = 0; k < n_groups; k++) {
-        const int64_t total = n * groups[k].width;
-        k_gaussian_adam<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, groups[k], b1, b2, eps, c1, c2);
+    AdamGroups A{};
+    A.count = n_groups > 5 ? 5 : n_groups;
+    long long acc = 0;
+    for (int k = 0; k < A.count; k++) {
+        A.g[k] = groups[k];
+        acc += n * groups[k].width;
+        A.end[k] = acc;
     }
+    k_gaussian_adam<<<(unsigned)((acc + 255) / 256), 256, 0, s>>>(n, A, b1, b2, eps, c1, c2);
 }
 
 }  // namespace gs

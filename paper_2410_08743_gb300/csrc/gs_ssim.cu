@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -27,131 +28,214 @@ static void upload_window() {
     done = true;
 }
 
-// Horizontal pass over NM planes: in[m] -> out[m]; the inputs are built from
-// x (rendered) and y (target): {x, y, x*x, y*y, x*y} when NM == 5, or taken
-// from `src` planes when products == false.
-template <int NM, bool PRODUCTS>
-__global__ void k_hpass(int W, int H, const float* __restrict__ x, const float* __restrict__ y,
-                        const float* __restrict__ src, float* __restrict__ out) {
-    const int px = blockIdx.x * blockDim.x + threadIdx.x;
-    const int py = blockIdx.y;
-    if (px >= W) return;
-    const size_t np = (size_t)W * H;
-    float acc[NM];
-#pragma unroll
-    for (int m = 0; m < NM; m++) acc[m] = 0.0f;
-#pragma unroll
-    for (int a = -5; a <= 5; a++) {
-        const int xx = px + a;
-        if (xx < 0 || xx >= W) continue;
-        const size_t q = (size_t)py * W + xx;
-        const float w = c_win[a + 5];
-        if (PRODUCTS) {
-            const float xv = x[q], yv = y[q];
-            acc[0] += w * xv; acc[1] += w * yv; acc[2] += w * xv * xv; acc[3] += w * yv * yv; acc[4] += w * xv * yv;
-        } else {
-#pragma unroll
-            for (int m = 0; m < NM; m++) acc[m] += w * src[m * np + q];
+// Tiled, fused D-SSIM.  One block computes 32x32 outputs of one channel of
+// one view: it stages the tile of rendered (x) and target (y) values with a
+// 5-pixel halo in shared memory (zero outside the image), filters the five
+// moments x, y, x^2, y^2, xy horizontally then vertically, and writes the
+// SSIM value's partials
+//   dA = df/dmu_x - 2 mu_x df/dsxx - mu_y df/dsxy, dB = df/dsxx, dC = df/dsxy
+// (f = SSIM at the pixel) plus a per-block sum of f.  A second pass filters
+// the three partial planes the same way (the zero-padded symmetric window is
+// its own adjoint) and forms dL/dx = -w/(3HW) (F dA + 2 x F dB + y F dC).
+#define SS_T 32                 // outputs per block side
+#define SS_R 5                  // window radius
+#define SS_S (SS_T + 2 * SS_R)  // staged side
+#define SS_THREADS 256
+#define SS_MAXV 32              // views per launch
+
+struct DssimBatch {
+    int n;                       // views in this launch
+    int max_tiles;               // tiles of the largest view
+    int W[SS_MAXV], H[SS_MAXV], tx[SS_MAXV];
+    long long off[SS_MAXV];      // float offset of the view's planar image
+};
+
+__device__ __forceinline__ bool ss_block(const DssimBatch& b, int& j, int& ch, int& W, int& H, int& x0, int& y0,
+                                         long long& off) {
+    j = blockIdx.y / 3;
+    ch = blockIdx.y % 3;
+    W = b.W[j];
+    H = b.H[j];
+    const int tile = blockIdx.x;
+    const int ty = (H + SS_T - 1) / SS_T;
+    if (tile >= b.tx[j] * ty) return false;
+    x0 = (tile % b.tx[j]) * SS_T;
+    y0 = (tile / b.tx[j]) * SS_T;
+    off = b.off[j] + (long long)ch * W * H;
+    return true;
+}
+
+__global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(DssimBatch b, const float* __restrict__ image,
+                                                        const float* __restrict__ target, float* __restrict__ parts,
+                                                        long long part_stride, float* __restrict__ block_sum) {
+    __shared__ float sx[SS_S][SS_S + 1], sy[SS_S][SS_S + 1];
+    __shared__ float hm[5][SS_S][SS_T + 1];
+    __shared__ float red[SS_THREADS / 32];
+    int j, ch, W, H, x0, y0;
+    long long off;
+    const bool live = ss_block(b, j, ch, W, H, x0, y0, off);
+    float fsum = 0.0f;
+    if (live) {
+        for (int k = threadIdx.x; k < SS_S * SS_S; k += SS_THREADS) {
+            const int r = k / SS_S, c = k % SS_S;
+            const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const size_t q = (size_t)gy * W + gx;
+            sx[r][c] = in ? image[off + q] : 0.0f;
+            sy[r][c] = in ? target[off + q] : 0.0f;
         }
     }
-    const size_t p = (size_t)py * W + px;
+    __syncthreads();
+    if (live) {
+        for (int k = threadIdx.x; k < SS_S * SS_T; k += SS_THREADS) {
+            const int r = k / SS_T, c = k % SS_T;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll
-    for (int m = 0; m < NM; m++) out[m * np + p] = acc[m];
-}
-
-// Vertical pass of the five moments, the SSIM map and the partials
-// dA = df/dmu_x - 2 mu_x df/dsxx - mu_y df/dsxy, dB = df/dsxx, dC = df/dsxy.
-__global__ void k_vpass_ssim(int W, int H, const float* __restrict__ h5, float* __restrict__ parts,
-                             float* __restrict__ smap) {
-    const int px = blockIdx.x * blockDim.x + threadIdx.x;
-    const int py = blockIdx.y;
-    if (px >= W) return;
-    const size_t np = (size_t)W * H;
-    float m[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-    for (int b = -5; b <= 5; b++) {
-        const int yy = py + b;
-        if (yy < 0 || yy >= H) continue;
-        const size_t q = (size_t)yy * W + px;
-        const float w = c_win[b + 5];
-#pragma unroll
-        for (int k = 0; k < 5; k++) m[k] += w * h5[k * np + q];
+            for (int t = 0; t < 2 * SS_R + 1; t++) {
+                const float w = c_win[t], xv = sx[r][c + t], yv = sy[r][c + t];
+                a0 += w * xv; a1 += w * yv; a2 += w * xv * xv; a3 += w * yv * yv; a4 += w * xv * yv;
+            }
+            hm[0][r][c] = a0; hm[1][r][c] = a1; hm[2][r][c] = a2; hm[3][r][c] = a3; hm[4][r][c] = a4;
+        }
     }
-    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    const float ux = m[0], uy = m[1];
-    const float vx = m[2] - ux * ux, vy = m[3] - uy * uy, cxy = m[4] - ux * uy;
-    const float N1 = 2.f * ux * uy + C1, N2 = 2.f * cxy + C2;
-    const float D1 = ux * ux + uy * uy + C1, D2 = vx + vy + C2;
-    const float iD = 1.0f / (D1 * D2);
-    const float f = N1 * N2 * iD;
-    const float dmu = 2.f * uy * N2 * iD - f * 2.f * ux / D1;
-    const float dvx = -f / D2;
-    const float dcxy = 2.f * N1 * iD;
-    const size_t p = (size_t)py * W + px;
-    parts[p] = dmu - 2.f * ux * dvx - uy * dcxy;
-    parts[np + p] = dvx;
-    parts[2 * np + p] = dcxy;
-    smap[p] = f;
-}
-
-// Vertical pass of the three filtered partials and the image gradient
-// dL/dx = -w/(3HW) (F dA + 2 x F dB + y F dC).
-__global__ void k_vpass_grad(int W, int H, const float* __restrict__ h3, const float* __restrict__ x,
-                             const float* __restrict__ y, float scale, float* __restrict__ out) {
-    const int px = blockIdx.x * blockDim.x + threadIdx.x;
-    const int py = blockIdx.y;
-    if (px >= W) return;
-    const size_t np = (size_t)W * H;
-    float m[3] = {0, 0, 0};
+    __syncthreads();
+    if (live) {
+        const long long np = (long long)W * H;
+        for (int k = threadIdx.x; k < SS_T * SS_T; k += SS_THREADS) {
+            const int r = k / SS_T, c = k % SS_T;
+            const int gy = y0 + r, gx = x0 + c;
+            if (gx >= W || gy >= H) continue;
+            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int b = -5; b <= 5; b++) {
-        const int yy = py + b;
-        if (yy < 0 || yy >= H) continue;
-        const size_t q = (size_t)yy * W + px;
-        const float w = c_win[b + 5];
+            for (int t = 0; t < 2 * SS_R + 1; t++) {
+                const float w = c_win[t];
 #pragma unroll
-        for (int k = 0; k < 3; k++) m[k] += w * h3[k * np + q];
+                for (int u = 0; u < 5; u++) m[u] += w * hm[u][r + t][c];
+            }
+            const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+            const float ux = m[0], uy = m[1];
+            const float vx = m[2] - ux * ux, vy = m[3] - uy * uy, cxy = m[4] - ux * uy;
+            const float N1 = 2.f * ux * uy + C1, N2 = 2.f * cxy + C2;
+            const float D1 = ux * ux + uy * uy + C1, D2 = vx + vy + C2;
+            const float iD = 1.0f / (D1 * D2);
+            const float f = N1 * N2 * iD;
+            const float dmu = 2.f * uy * N2 * iD - f * 2.f * ux / D1;
+            const float dvx = -f / D2;
+            const float dcxy = 2.f * N1 * iD;
+            const size_t q = (size_t)off + (size_t)gy * W + gx;
+            parts[q] = dmu - 2.f * ux * dvx - uy * dcxy;
+            parts[part_stride + q] = dvx;
+            parts[2 * part_stride + q] = dcxy;
+            fsum += f;
+            (void)np;
+        }
     }
-    const size_t p = (size_t)py * W + px;
-    out[p] = scale * (m[0] + 2.f * x[p] * m[1] + y[p] * m[2]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fsum;
+    __syncthreads();
+    if (threadIdx.x == 0 && block_sum) {
+        float acc = 0.0f;
+        for (int w = 0; w < SS_THREADS / 32; w++) acc += red[w];
+        block_sum[(size_t)blockIdx.y * b.max_tiles + blockIdx.x] = live ? acc : 0.0f;
+    }
 }
 
-// Per-view loss value w_dssim * (1 - mean SSIM), summed in a fixed order.
-__global__ void k_ssim_value(const float* __restrict__ smap, long long n, float w, double* __restrict__ out) {
+__global__ void __launch_bounds__(SS_THREADS) k_ssim_bwd(DssimBatch b, const float* __restrict__ image,
+                                                        const float* __restrict__ target,
+                                                        const float* __restrict__ parts, long long part_stride,
+                                                        float w_dssim, float* __restrict__ dldc) {
+    __shared__ float sp[3][SS_S][SS_S + 1];
+    __shared__ float hm[3][SS_S][SS_T + 1];
+    int j, ch, W, H, x0, y0;
+    long long off;
+    if (!ss_block(b, j, ch, W, H, x0, y0, off)) return;
+    for (int k = threadIdx.x; k < SS_S * SS_S; k += SS_THREADS) {
+        const int r = k / SS_S, c = k % SS_S;
+        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const size_t q = (size_t)off + (size_t)gy * W + gx;
+#pragma unroll
+        for (int u = 0; u < 3; u++) sp[u][r][c] = in ? parts[u * part_stride + q] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SS_S * SS_T; k += SS_THREADS) {
+        const int r = k / SS_T, c = k % SS_T;
+        float a[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 2 * SS_R + 1; t++) {
+            const float w = c_win[t];
+#pragma unroll
+            for (int u = 0; u < 3; u++) a[u] += w * sp[u][r][c + t];
+        }
+#pragma unroll
+        for (int u = 0; u < 3; u++) hm[u][r][c] = a[u];
+    }
+    __syncthreads();
+    const float scale = -w_dssim / (3.0f * (float)W * (float)H);
+    for (int k = threadIdx.x; k < SS_T * SS_T; k += SS_THREADS) {
+        const int r = k / SS_T, c = k % SS_T;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gx >= W || gy >= H) continue;
+        float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 2 * SS_R + 1; t++) {
+            const float w = c_win[t];
+#pragma unroll
+            for (int u = 0; u < 3; u++) m[u] += w * hm[u][r + t][c];
+        }
+        const size_t q = (size_t)off + (size_t)gy * W + gx;
+        dldc[q] = scale * (m[0] + 2.f * image[q] * m[1] + target[q] * m[2]);
+    }
+}
+
+// Per-view loss w_dssim (1 - mean SSIM): the view's block sums added in block
+// order (deterministic).
+__global__ void k_ssim_loss(DssimBatch b, const float* __restrict__ block_sum, float w, double* __restrict__ out) {
+    const int j = blockIdx.x;
     __shared__ double sm[256];
     double acc = 0.0;
-    for (long long k = threadIdx.x; k < n; k += blockDim.x) acc += (double)smap[k];
+    const int nb = 3 * b.max_tiles;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += (double)block_sum[(size_t)j * nb + k];
     sm[threadIdx.x] = acc;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
         if ((int)threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = (double)w * (1.0 - sm[0] / (double)n);
+    if (threadIdx.x == 0) out[j] = (double)w * (1.0 - sm[0] / (3.0 * (double)b.W[j] * (double)b.H[j]));
 }
 
-// tmp must hold 11 planes of the largest view: 5 moments, 3 partials and the
-// 3-channel SSIM map.  loss_out (nullable, device [V]) receives w_dssim (1 - SSIM).
+// tmp: 3 planes of the packed image (the SSIM partials) plus 3 floats per
+// 32x32 tile of the largest view per view of a launch (at most 32 views) for
+// the per-block SSIM sums.  loss_out (nullable, device [V]) receives
+// w_dssim (1 - SSIM) per view.
 void launch_dssim(int n_views, const gs_view* views, const long long* img_off, const float* image,
                   const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
                   cudaStream_t s) {
     upload_window();
-    for (int v = 0; v < n_views; v++) {
-        const int W = views[v].width, H = views[v].height;
-        const size_t np = (size_t)W * H;
-        const dim3 blk(128), grd((W + 127) / 128, H);
-        float* smap = tmp + 8 * np;  // [3][H][W]
-        for (int ch = 0; ch < 3; ch++) {
-            const float* x = image + img_off[v] + ch * np;
-            const float* y = target + img_off[v] + ch * np;
-            float* h5 = tmp;           // 5 planes
-            float* parts = tmp + 5 * np;  // 3 planes
-            k_hpass<5, true><<<grd, blk, 0, s>>>(W, H, x, y, nullptr, h5);
-            k_vpass_ssim<<<grd, blk, 0, s>>>(W, H, h5, parts, smap + ch * np);
-            k_hpass<3, false><<<grd, blk, 0, s>>>(W, H, nullptr, nullptr, parts, h5);
-            k_vpass_grad<<<grd, blk, 0, s>>>(W, H, h5, x, y, -w_dssim / (3.0f * (float)np), dldc_out + img_off[v] + ch * np);
+    long long total = 0;
+    for (int v = 0; v < n_views; v++)
+        total = std::max(total, img_off[v] + 3LL * views[v].width * views[v].height);
+    float* parts = tmp;                       // [3][total]
+    float* bsum = tmp + 3 * (size_t)total;    // per-block SSIM sums of one launch
+    for (int v0 = 0; v0 < n_views; v0 += SS_MAXV) {
+        DssimBatch b{};
+        b.n = std::min(SS_MAXV, n_views - v0);
+        int mt = 1;
+        for (int j = 0; j < b.n; j++) {
+            const gs_view& vw = views[v0 + j];
+            b.W[j] = vw.width;
+            b.H[j] = vw.height;
+            b.tx[j] = (vw.width + SS_T - 1) / SS_T;
+            b.off[j] = img_off[v0 + j];
+            mt = std::max(mt, b.tx[j] * ((vw.height + SS_T - 1) / SS_T));
         }
-        if (loss_out) k_ssim_value<<<1, 256, 0, s>>>(smap, (long long)(3 * np), w_dssim, loss_out + v);
+        b.max_tiles = mt;
+        const dim3 grid(mt, 3 * b.n);
+        k_ssim_fwd<<<grid, SS_THREADS, 0, s>>>(b, image, target, parts, total, loss_out ? bsum : nullptr);
+        k_ssim_bwd<<<grid, SS_THREADS, 0, s>>>(b, image, target, parts, total, w_dssim, dldc_out);
+        if (loss_out) k_ssim_loss<<<b.n, 256, 0, s>>>(b, bsum, w_dssim, loss_out + v0);
     }
 }
 
