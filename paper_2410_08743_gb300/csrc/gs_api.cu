@@ -179,6 +179,10 @@ static const size_t kMaxViewTables = 64;
 
 struct gs_frames {
     gs_ctx* ctx = nullptr;
+    // gs_step with host buffers: side stream that uploads the loss input while
+    // the forward runs, and its fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // launch configuration of the last forward
     int n_views = 0;
     int n = 0;
@@ -538,6 +542,9 @@ void gs_frames_destroy(gs_frames* f) {
     cudaSetDevice(f->ctx->device);
     cudaDeviceSynchronize();
     f->release();
+    if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+    if (f->ev_join) cudaEventDestroy(f->ev_join);
+    if (f->side) cudaStreamDestroy(f->side);
     delete f;
 }
 
@@ -844,7 +851,17 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
         dd.means = P + off_m; dd.scales = P + off_s; dd.quats = P + off_q; dd.opacities = P + off_o; dd.sh = P + off_sh;
         if (n_views > 0) {
             CK(cudaMemcpyAsync(fr->st_poses.p, poses, 12 * sizeof(double) * n_views, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(fr->st_target.p, in_img, n_img * sizeof(float), cudaMemcpyHostToDevice, s));
+            // the loss input is first read by the backward: upload it on the side
+            // stream (after everything already queued on s) while the forward runs
+            if (!fr->side) {
+                CK(cudaStreamCreateWithFlags(&fr->side, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&fr->ev_fork, cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&fr->ev_join, cudaEventDisableTiming));
+            }
+            CK(cudaEventRecord(fr->ev_fork, s));
+            CK(cudaStreamWaitEvent(fr->side, fr->ev_fork, 0));
+            CK(cudaMemcpyAsync(fr->st_target.p, in_img, n_img * sizeof(float), cudaMemcpyHostToDevice, fr->side));
+            CK(cudaEventRecord(fr->ev_join, fr->side));
         }
         dposes = fr->st_poses.p;
         if (need_target) dl.target = fr->st_target.p; else dl.dl_dimage = fr->st_target.p;
@@ -877,6 +894,10 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
     o2.flags &= ~(uint32_t)GS_F_HOST_IO;
     dl.loss = dloss;
     rc = gs_render_forward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, nullptr, nullptr, stream);
+    if (rc == GS_OK && host && n_views > 0) {
+        const cudaError_t e = cudaStreamWaitEvent(s, fr->ev_join, 0);
+        if (e != cudaSuccess) rc = fail(GS_ECUDA, "join of the loss-input upload: %s", cudaGetErrorString(e));
+    }
     if (rc == GS_OK)
         rc = gs_render_backward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, &dl, grads ? &dg : nullptr,
                                 dpose_grad, stream);

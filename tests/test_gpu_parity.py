@@ -491,3 +491,51 @@ def test_forward_pixels_per_thread_is_result_neutral(R, case):
     # the sorted prefixes agree where both sorted (each covers its own blend)
     n = min(len(outs[0][3]), len(outs[1][3]))
     assert n > 0
+
+
+def test_step_with_host_buffers_equals_device_path(R):
+    """gs_step with GS_F_HOST_IO (host inputs and outputs, copies inside the
+    call, the loss input uploaded beside the forward) equals the same step on
+    device buffers; twice in a row, so the upload stream is reused."""
+    sc, views, poses = _ragged_case(81, 3000, 2)
+    rng = np.random.default_rng(81)
+    p = to_dev(sc)
+    P = poses_dev(poses)
+    n_img = sum(3 * v["width"] * v["height"] for v in views)
+    target = rng.uniform(size=n_img).astype(np.float32)
+    V = len(views)
+    # device path
+    img_d = torch.empty(n_img, device=DEV)
+    g_d = zero_grads(p)
+    pg_d = torch.zeros(V, 6, dtype=torch.float64, device=DEV)
+    lo_d = torch.zeros(V, dtype=torch.float64, device=DEV)
+    tg = torch.from_numpy(target).to(DEV)
+    desc = L.scene_desc(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
+    loss = L.make_loss(L.GS_LOSS_L1_DSSIM, target=tg, w_l1=0.8, w_dssim=0.2)
+    L.gs_step(R.ctx, R.frames, desc, R.views(views), V, P.data_ptr(), R.opts, loss, img_d.data_ptr(),
+              L.make_grads(**g_d), pg_d.data_ptr(), lo_d.data_ptr())
+    torch.cuda.synchronize()
+    # host path
+    hp = {k: p[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
+    hposes = torch.from_numpy(poses).pin_memory()
+    htg = torch.from_numpy(target).pin_memory()
+    himg = torch.zeros(n_img).pin_memory()
+    hg = {k: torch.zeros_like(hp[k]).pin_memory() for k in hp}
+    hpg = torch.zeros(V, 6, dtype=torch.float64).pin_memory()
+    hlo = torch.zeros(V, dtype=torch.float64).pin_memory()
+    hdesc = L.scene_desc(hp["means"], hp["scales"], hp["quats"], hp["opac"], hp["sh"], p["sh_degree"])
+    hloss = L.make_loss(L.GS_LOSS_L1_DSSIM, target=htg, w_l1=0.8, w_dssim=0.2)
+    R.opts.flags = L.GS_F_HOST_IO
+    try:
+        for _ in range(2):
+            L.gs_step(R.ctx, R.frames, hdesc, R.views(views), V, hposes.data_ptr(), R.opts, hloss, himg.data_ptr(),
+                      L.make_grads(**hg), hpg.data_ptr(), hlo.data_ptr())
+            torch.cuda.synchronize()
+            assert torch.equal(himg, img_d.cpu())
+            for k in hg:
+                np.testing.assert_allclose(hg[k].numpy(), g_d[k].cpu().numpy(), rtol=1e-4,
+                                           atol=1e-6 * float(g_d[k].abs().max()))
+            np.testing.assert_allclose(hpg.numpy(), pg_d.cpu().numpy(), rtol=1e-5, atol=1e-9)
+            np.testing.assert_allclose(hlo.numpy(), lo_d.cpu().numpy(), rtol=1e-6)
+    finally:
+        R.opts.flags = 0
