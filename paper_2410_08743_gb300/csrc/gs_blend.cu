@@ -251,7 +251,7 @@ struct LazySmem {
 // Two pixels per thread share every shared-memory read of a splat and give
 // each thread two independent compositing chains.
 template <int LZ_CAP, int PX>
-__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 6) k_blend_fwd_lazy(
+__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd_lazy(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, unsigned long long* __restrict__ keys,
     unsigned long long* __restrict__ tmp, uint32_t* __restrict__ sorted_idx, uint32_t* __restrict__ sorted_count,
@@ -606,7 +606,7 @@ struct BwdPixel {
 // 8 / PX warps a tile.  With two pixels a lane sums both pixels' contributions
 // before the warp reduction, so one reduction serves 64 pixels.
 template <int PX>
-__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 8) k_blend_bwd(
+__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
     const float* __restrict__ image, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
