@@ -664,7 +664,7 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # DRAM bytes (read + write) per unit from one ncu capture of the current
 # kernel on the 4-view small case, scaled to a launch by the run's units
 # (profiles/top_kernels_batched_1M_4views.md).  Re-measure when the kernel changes.
-TRAFFIC_PER_UNIT = {"blend_bwd": (41.9, 5)}   # bytes per list entry read by the backward blend
+TRAFFIC_PER_UNIT = {}   # kernel -> (bytes per unit, counter index); empty until re-measured
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
