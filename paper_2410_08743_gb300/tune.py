@@ -1,7 +1,8 @@
 """Autotuning of the renderer's result-neutral launch parameters.
 
 `autotune` picks the tuning (Gaussians per count/scatter CTA, lazy-sort run
-length, forward-preprocess block size) with the library's gs_autotune for a
+length, forward-preprocess block size, pixels per thread of the two blends)
+with the library's gs_autotune for a
 workload class and caches the choice in a JSON file keyed by GPU name,
 resolution class and Gaussian-count class, so later runs of the same class
 reuse it without timing again."""
