@@ -383,10 +383,11 @@ def run_gpu(args):
         # the paper's offered load (200/s of 100-step solves at ~0.4 Mpix) exceeds
         # one GPU (about 15 solves/s), so its latencies include the backlog; a
         # second replay at a load both forms sustain shows latency without it
-        serving = run_serving(p, dev, args, 64)
-        serving["plain"] = run_serving(p, dev, args, 1)
-        serving["sustainable"] = {"batched": run_serving(p, dev, args, 64, rate_hz=6.0, n_requests=30),
-                                  "plain": run_serving(p, dev, args, 1, rate_hz=6.0, n_requests=30)}
+        tt = tuned["tuning"]
+        serving = run_serving(p, dev, args, 64, tuning=tt)
+        serving["plain"] = run_serving(p, dev, args, 1, tuning=tt)
+        serving["sustainable"] = {"batched": run_serving(p, dev, args, 64, rate_hz=6.0, n_requests=30, tuning=tt),
+                                  "plain": run_serving(p, dev, args, 1, rate_hz=6.0, n_requests=30, tuning=tt)}
 
     extras = None
     if not args.no_extras:
@@ -534,6 +535,7 @@ def run_joint(dev, args, iterations: int = 1000):
         raw = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in synth.perturb_scene_raw(12, sc).items()}
         P = torch.from_numpy(w["init_poses"]).to(dev)
         J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=iterations + V, spatial_order=True)
+        tuned = J.autotune(0)
         for k in range(V):
             J.step(k)
         torch.cuda.synchronize()
@@ -546,7 +548,7 @@ def run_joint(dev, args, iterations: int = 1000):
                 "iterations": iterations, "ms_per_iter": ms / iterations,
                 "mpix_s_incl_optimizer": iterations * npix / (ms * 1e-3) / 1e6,
                 "loss_first_pass": first, "loss_last_pass": float(J.loss.mean().item()),
-                "rot_err_deg": [rot0, rot1], "centre_err": [cen0, cen1]}
+                "rot_err_deg": [rot0, rot1], "centre_err": [cen0, cen1], "tuning": tuned["tuning"]}
     finally:
         r.close()
 
@@ -584,6 +586,7 @@ def run_trajectory(dev, args, batch: int = 8, epochs: int = 1):
                for k, a in synth.perturb_scene_raw(13, sc, means_std=0.005).items()}
         P = torch.from_numpy(w["init_poses"]).to(dev)
         J = JointRefiner(r, raw, sc["sh_degree"], views, P, tg, iterations=(epochs + 1) * nb, spatial_order=True)
+        tuned = J.autotune(0, batch)
         for b in range(nb):
             J.step(b * batch, min(V, (b + 1) * batch))
         torch.cuda.synchronize()
@@ -596,12 +599,14 @@ def run_trajectory(dev, args, batch: int = 8, epochs: int = 1):
                 "ms_per_step": ms / (epochs * nb), "frames_per_step": batch,
                 "mpix_s_incl_optimizer": npix / (ms * 1e-3) / 1e6,
                 "device_gb_held": (free0 - free1) / 1e9,
-                "loss_first_pass": first, "loss_second_pass": float(J.loss.mean().item())}
+                "loss_first_pass": first, "loss_second_pass": float(J.loss.mean().item()),
+                "tuning": tuned["tuning"]}
     finally:
         r.close()
 
 
-def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_requests: int | None = None):
+def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_requests: int | None = None,
+                tuning: dict | None = None):
     """Replays Poisson arrivals of pose-estimation requests (mixed sizes
     256..1280 wide) in real time against a server with `slots` slots and
     returns latency percentiles and throughput."""
@@ -619,7 +624,8 @@ def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_reques
     imgs = [r.forward(p, [q["view"]], torch.from_numpy(q["gt_pose"][None]).to(dev)).cpu().numpy() for q in reqs]
     r.close()
     sh = L.gs_scene_borrow(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
-    srv = L.gs_server_create(dev.index or 0, sh, L.gs_default_opts(), slots, 1280, 720, 200 * (1 << 30), 1 << 20)
+    srv = L.gs_server_create(dev.index or 0, sh, L.gs_default_opts(), slots, 1280, 720, 200 * (1 << 30), 1 << 20,
+                             tuning=tuning)
     # warm the worker (workspaces) with one small solve
     q0 = reqs[0]
     L.gs_solve_wait(srv, L.gs_solve_submit(srv, q0["view"], imgs[0], q0["init_pose"], 2, 1e-2, 1e-4), 600000)

@@ -396,6 +396,7 @@ typedef struct {
     float mask_alpha;         /* 0: plain L1; > 0: confidence-masked L1 (GS_LOSS_L1_MASKED)
                                  with this accumulated-alpha threshold (the paper uses 0.99) */
     int32_t pose_param;       /* GS_POSE_SE3 or GS_POSE_TXSO3 */
+    gs_tuning tuning;         /* launch parameters of the server's renderer (all zero: defaults) */
 } gs_server_config;
 
 typedef struct {

@@ -84,7 +84,7 @@ class gs_gaussian_lrs(C.Structure):
 class gs_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_width", C.c_int32), ("max_height", C.c_int32),
                 ("mem_budget", C.c_int64), ("queue_capacity", C.c_int32), ("mask_alpha", C.c_float),
-                ("pose_param", C.c_int32)]
+                ("pose_param", C.c_int32), ("tuning", gs_tuning)]
 
 
 class gs_solve_request(C.Structure):
@@ -430,9 +430,10 @@ def gs_gaussian_adam(ctx: int, raw: dict, act_scales, act_opac, grads: dict, m, 
 
 def gs_server_create(device: int, scene: int, opts: gs_render_opts, max_slots: int, max_width: int, max_height: int,
                      mem_budget: int = 0, queue_capacity: int = 65536, mask_alpha: float = 0.0,
-                     pose_param: int = GS_POSE_SE3) -> int:
+                     pose_param: int = GS_POSE_SE3, tuning: dict | None = None) -> int:
+    t = gs_tuning(*[int(tuning[k]) for k, _ in gs_tuning._fields_]) if tuning else gs_tuning()
     cfg = gs_server_config(int(max_slots), int(max_width), int(max_height), int(mem_budget), int(queue_capacity),
-                           float(mask_alpha), int(pose_param))
+                           float(mask_alpha), int(pose_param), t)
     h = C.c_void_p()
     _ck(load().gs_server_create(int(device), C.c_void_p(scene), C.byref(opts), C.byref(cfg), C.byref(h)))
     return h.value

@@ -280,6 +280,7 @@ int gs_server_create(int device, const gs_scene* scene, const gs_render_opts* op
     s->opts.flags = 0;
     s->cfg = *cfg;
     int rc = gs_ctx_create(device, &s->ctx);
+    if (rc == GS_OK && cfg->tuning.scatter_chunk != 0) rc = gs_ctx_set_tuning(s->ctx, &cfg->tuning);
     if (rc == GS_OK) rc = gs_frames_create(s->ctx, &s->fr);
     if (rc != GS_OK) { gs_server_destroy(s); return rc; }
     const int S = cfg->max_slots;

@@ -151,6 +151,27 @@ class JointRefiner:
             L.gs_pose_step(self.r.ctx, pose, self.pm[v0:v1], self.pv[v0:v1], pg, lr, self.pose_steps[v0])
         self.it += 1
 
+    def autotune(self, v0: int = 0, v1: int | None = None, repeats: int = 1) -> dict:
+        """Picks the renderer's result-neutral launch parameters for iterations
+        over views [v0, v1) (tune.autotune, cached per workload class)."""
+        from . import tune
+        v1 = v0 + 1 if v1 is None else v1
+        views = self.views[v0:v1]
+        params = dict(means=self.raw["means"], scales=self.scales, quats=self.raw["quats"], opac=self.opac,
+                      sh=self.raw["sh"], sh_degree=self.deg)
+        n_img = self.img_off[v1] - self.img_off[v0]
+        img = self.image.get(n_img)
+        if img is None:
+            img = self.image[n_img] = torch.empty(n_img, device=self.raw["means"].device)
+        kind = L.GS_LOSS_L1_DSSIM if self.w_dssim != 0.0 else L.GS_LOSS_L1
+        loss = L.make_loss(kind, target=self.targets[self.img_off[v0]:self.img_off[v1]], w_l1=self.w_l1,
+                           w_dssim=self.w_dssim)
+        # the tuner's trial steps accumulate into scratch gradients, not the refiner's
+        scratch = D.FlatGrads(self.n, self.raw["means"].device)
+        self.r.forward(params, views, self.poses[v0:v1], image=img)
+        return tune.autotune(self.r, params, views, self.poses[v0:v1], img, loss, scratch.as_dict(),
+                             self.pose_grad[v0:v1], repeats=repeats)
+
     def prune(self, n_target: int, min_opacity: float = 0.005) -> int:
         """Adaptive opacity pruning (Sec. 3.3): removes the Gaussians whose
         opacity is at or below the threshold that leaves at most n_target of
