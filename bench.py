@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--no-joint", action="store_true", help="skip the 300k joint-refinement leg")
     ap.add_argument("--no-traj", action="store_true", help="skip the 3M trajectory leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the masked-L1 / regulariser / pruning timings")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch tuning 'scatter_chunk,sort_chunk,preprocess_threads,bwd_px,fwd_px' "
+                         "instead of the autotuner's choice (e.g. to profile one kernel variant)")
     return ap.parse_args()
 
 
@@ -231,7 +234,15 @@ def run_gpu(args):
     step()
     torch.cuda.synchronize()
     from paper_2410_08743_gb300 import tune
-    tuned = tune.autotune(r, p, views, P, image, l1, grads, pose_grad, repeats=1)
+    if args.tuning:
+        kv = dict(zip(("scatter_chunk", "sort_chunk", "preprocess_threads", "bwd_pixels_per_thread",
+                       "fwd_pixels_per_thread"), (int(x) for x in args.tuning.split(","))))
+        if len(kv) != 5:
+            raise SystemExit("--tuning wants five comma-separated integers")
+        L.gs_ctx_set_tuning(r.ctx, **kv)
+        tuned = dict(tuning=kv, ms=None, cached=False, fixed=True)
+    else:
+        tuned = tune.autotune(r, p, views, P, image, l1, grads, pose_grad, repeats=1)
     for g in grads.values():
         g.zero_()
     r.set_flags(L.GS_F_NO_SYNC)

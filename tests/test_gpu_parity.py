@@ -64,6 +64,24 @@ def _same_depth_case(n=30000, seed=32):
     return sc, views, synth.pose_from_center(np.eye(3), np.zeros(3))[None]
 
 
+def _needle_case(n=6000, seed=33):
+    """Thin rotated Gaussians (axis ratios up to ~40) and opacities just above
+    alpha_min: alpha boxes far larger than the ellipses, so the per-warp
+    culling of the blends decides many entries near the ellipse boundary."""
+    rng = np.random.default_rng(seed)
+    sc = synth.make_scene_box(seed, n, sh_degree=1, lo=(-1.0, -0.8, 3.0), hi=(1.0, 0.8, 5.0))
+    ratio = np.exp(rng.uniform(0.0, np.log(40.0), n))
+    sc["scales"][:, 0] *= np.sqrt(ratio).astype(np.float32)
+    sc["scales"][:, 1] /= np.sqrt(ratio).astype(np.float32)
+    low = rng.random(n) < 0.5
+    sc["opac"][low] = rng.uniform(1.05 / 255.0, 6.0 / 255.0, int(low.sum())).astype(np.float32)
+    views = [dict(fx=70.0, fy=70.0, cx=40.0, cy=30.0, width=80, height=60),
+             dict(fx=50.0, fy=52.0, cx=19.5, cy=22.0, width=41, height=45)]
+    base = synth.pose_from_center(np.eye(3), np.zeros(3))
+    poses = np.stack([synth.perturb_normal(rng, base, 3.0, 0.05) for _ in views])
+    return sc, views, poses
+
+
 CASES = {
     "tiny": lambda: (lambda w: (w["scene"], w["views"], w["poses"]))(synth.tiny_workload(0)),
     "ragged_sh3": lambda: _ragged_case(),
@@ -71,6 +89,7 @@ CASES = {
     "dense_medium": lambda: _dense_case(20000),
     "dense_large": lambda: _dense_case(120000),
     "same_depth": lambda: _same_depth_case(),
+    "needles": lambda: _needle_case(),
 }
 GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium"]
 
@@ -126,9 +145,11 @@ def test_keys_bit_exact(R, case, full):
         assert lens.max() > 12288         # MSD-split path exercised
 
 
-@pytest.mark.parametrize("case", ["ragged_sh3", "dense_large", "same_depth"])
+@pytest.mark.parametrize("case", ["ragged_sh3", "dense_large", "same_depth", "needles"])
 def test_lazy_sort_equals_full_sort(R, case):
-    """Sorting tiles only as far as they are consumed changes nothing."""
+    """Sorting tiles only as far as they are consumed changes nothing; nor does
+    the per-warp box and ellipse culling of the lazy blend (the full-sort blend
+    tests every staged entry at every pixel)."""
     sc, views, poses = CASES[case]()
     outs = []
     for flags in (L.GS_F_FULL_SORT, 0):
