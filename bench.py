@@ -681,7 +681,9 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # DRAM bytes (read + write) per unit from one ncu capture of the current
 # kernel on the 4-view small case, scaled to a launch by the run's units
 # (profiles/top_kernels_batched_1M_4views.md).  Re-measure when the kernel changes.
-TRAFFIC_PER_UNIT = {}   # kernel -> (bytes per unit, counter index); empty until re-measured
+# kernel -> (DRAM bytes per unit, counter index) from an ncu capture of the same kernel
+# (k_blend_bwd<2>: 35,705,856 B for 852,644 list entries read, 4 views at 1M Gaussians)
+TRAFFIC_PER_UNIT = {"blend_bwd": (41.88, 5)}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
