@@ -205,8 +205,14 @@ int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs
  * pointer.  With GS_F_HOST_IO every array (the scene's parameters, poses,
  * loss->target / loss->dl_dimage, image_out, grads, pose_grad, loss_out) is
  * HOST memory, preferably pinned: the call copies the inputs to library-owned
- * device staging, runs the step and copies the outputs back, all on `stream`;
- * the outputs are valid after the stream synchronises. */
+ * device staging, runs the step and copies the outputs back, ordered after
+ * the work already queued on `stream`; the outputs are valid after `stream`
+ * synchronises.  The copies overlap the computation on an internal stream:
+ * the parameters go up in slices of Gaussians (four from 2^18 Gaussians on),
+ * each slice's forward preprocess starting once its slice has landed; the
+ * loss input goes up and the image comes down while the other kernels run;
+ * each slice's gradients come down as soon as the backward has finished
+ * them.  The results equal those of the device-buffer call. */
 int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* scene, int n_views, const gs_view* views,
             const double* poses, const gs_render_opts* opts, const gs_loss* loss, float* image_out,
             gs_grads* grads, double* pose_grad, double* loss_out, void* stream);

@@ -183,6 +183,10 @@ struct gs_frames {
     // the forward runs, and its fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // ... and the events of its Gaussian slices (parameters uploaded, gradients
+    // final) and of the end of the gradient download
+    gs::SlicePipe pipe;
+    cudaEvent_t ev_down = nullptr, ev_img = nullptr;
     // launch configuration of the last forward
     int n_views = 0;
     int n = 0;
@@ -254,6 +258,7 @@ struct gs_frames {
 };
 
 static const int kViewChunk = 64;  // views per preprocess launch (bounds shared memory)
+static const size_t kHostSlices = 4;  // Gaussian slices of a gs_step with host buffers (at most GS_MAX_SLICES)
 
 // ------------------------------------------------------------ helpers
 static int check_scene(const gs_scene* sc) {
@@ -544,6 +549,12 @@ void gs_frames_destroy(gs_frames* f) {
     f->release();
     if (f->ev_fork) cudaEventDestroy(f->ev_fork);
     if (f->ev_join) cudaEventDestroy(f->ev_join);
+    if (f->ev_down) cudaEventDestroy(f->ev_down);
+    if (f->ev_img) cudaEventDestroy(f->ev_img);
+    for (int c = 0; c < GS_MAX_SLICES; c++) {
+        if (f->pipe.ready[c]) cudaEventDestroy(f->pipe.ready[c]);
+        if (f->pipe.done[c]) cudaEventDestroy(f->pipe.done[c]);
+    }
     if (f->side) cudaStreamDestroy(f->side);
     delete f;
 }
@@ -582,7 +593,8 @@ int gs_render_backward(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs
 
 int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
                             const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
-                            float* image, const float* target, double* loss_out, cudaStream_t s) {
+                            float* image, const float* target, double* loss_out, cudaStream_t s,
+                            const SlicePipe* pipe) {
     if (!ctx || !fr || !opts) return fail(GS_EINVAL, "NULL ctx/frames/opts");
     if (fr->ctx != ctx) return fail(GS_EINVAL, "frames belong to another context");
     int rc;
@@ -623,7 +635,15 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         SplatArrays spc = sp;
         const size_t off = (size_t)v0 * n;
         spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
-        {
+        if (pipe && pipe->n_slices > 0) {
+            // slice by slice, each as soon as its parameters are on the device
+            PROF(PK_PRE_FWD, pipe->n_slices);
+            for (int c = 0; c < pipe->n_slices; c++) {
+                if (v0 == 0) CK(cudaStreamWaitEvent(s, pipe->ready[c], 0));
+                gs::launch_preprocess_fwd(scene->d, ctx->tune.preprocess_threads, nv, fr->vdev.p + v0, rp, spc,
+                                          nullptr, s, pipe->bounds[c], pipe->bounds[c + 1]);
+            }
+        } else {
             PROF(PK_PRE_FWD, 1);
             gs::launch_preprocess_fwd(scene->d, ctx->tune.preprocess_threads, nv, fr->vdev.p + v0, rp, spc, nullptr, s);
         }
@@ -687,7 +707,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
 int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
                              const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
                              const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad,
-                             cudaStream_t s) {
+                             cudaStream_t s, const SlicePipe* pipe) {
     if (!ctx || !fr || !opts || !loss) return fail(GS_EINVAL, "NULL ctx/frames/opts/loss");
     int rc;
     if ((rc = check_scene(scene)) || (rc = check_views(n_views, views))) return rc;
@@ -787,7 +807,15 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         spc.A += off; spc.B += off; spc.Cb += off; spc.rect += off; spc.depth += off; spc.radius += off;
         g2c.gA += off; g2c.gB += off; g2c.gC += off;
         double* part = fr->pose_partials.p;
-        {
+        if (pipe && pipe->n_slices > 0) {
+            // slice by slice; after the last view chunk a slice's gradients are final
+            PROF(PK_PRE_BWD, pipe->n_slices);
+            for (int k = 0; k < pipe->n_slices; k++) {
+                gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, s,
+                                          pipe->bounds[k], pipe->bounds[k + 1]);
+                if (c == nchunks - 1) CK(cudaEventRecord(pipe->done[k], s));
+            }
+        } else {
             PROF(PK_PRE_BWD, 1);
             gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, s);
         }
@@ -841,25 +869,49 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
             (rc = fr->st_loss.ensure(std::max(n_views, 1), grow, "staging loss")))
             return rc;
         float* P = fr->st_params.p;
-        if (n > 0) {
-            CK(cudaMemcpyAsync(P + off_m, sd->means, 3 * n * 4, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(P + off_s, sd->scales, 3 * n * 4, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(P + off_q, sd->quats, 4 * n * 4, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(P + off_o, sd->opacities, n * 4, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(P + off_sh, sd->sh, 48 * n * 4, cudaMemcpyHostToDevice, s));
+        if (n_views > 0 && !fr->side) {
+            CK(cudaStreamCreateWithFlags(&fr->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&fr->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&fr->ev_join, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&fr->ev_down, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&fr->ev_img, cudaEventDisableTiming));
+            for (int c = 0; c < GS_MAX_SLICES; c++) {
+                CK(cudaEventCreateWithFlags(&fr->pipe.ready[c], cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&fr->pipe.done[c], cudaEventDisableTiming));
+            }
+        }
+        // The parameters go up in slices of Gaussians on the side stream (after
+        // everything already queued on s, which may still read the staging
+        // block), and the forward preprocess of a slice starts once its copy
+        // has landed; the loss input, first read by the backward, follows.
+        fr->pipe.n_slices = 0;
+        if (n_views > 0) {
+            CK(cudaEventRecord(fr->ev_fork, s));
+            CK(cudaStreamWaitEvent(fr->side, fr->ev_fork, 0));
+            if (n > 0) {
+                const size_t k = n >= ((size_t)1 << 18) ? kHostSlices : 1;
+                const size_t step = ((n + k - 1) / k + 255) / 256 * 256;
+                int c = 0;
+                for (size_t b = 0; b < n && c < GS_MAX_SLICES; b += step, c++) fr->pipe.bounds[c] = (int)b;
+                fr->pipe.n_slices = c;
+                fr->pipe.bounds[c] = (int)n;
+            }
+        }
+        const int n_up = n_views > 0 ? fr->pipe.n_slices : (n > 0 ? 1 : 0);
+        for (int c = 0; c < n_up; c++) {
+            const size_t b0 = n_views > 0 ? (size_t)fr->pipe.bounds[c] : 0;
+            const size_t m = (n_views > 0 ? (size_t)fr->pipe.bounds[c + 1] : n) - b0;
+            cudaStream_t cs = n_views > 0 ? fr->side : s;
+            CK(cudaMemcpyAsync(P + off_m + 3 * b0, sd->means + 3 * b0, 3 * m * 4, cudaMemcpyHostToDevice, cs));
+            CK(cudaMemcpyAsync(P + off_s + 3 * b0, sd->scales + 3 * b0, 3 * m * 4, cudaMemcpyHostToDevice, cs));
+            CK(cudaMemcpyAsync(P + off_q + 4 * b0, sd->quats + 4 * b0, 4 * m * 4, cudaMemcpyHostToDevice, cs));
+            CK(cudaMemcpyAsync(P + off_o + b0, sd->opacities + b0, m * 4, cudaMemcpyHostToDevice, cs));
+            CK(cudaMemcpyAsync(P + off_sh + 48 * b0, sd->sh + 48 * b0, 48 * m * 4, cudaMemcpyHostToDevice, cs));
+            if (n_views > 0) CK(cudaEventRecord(fr->pipe.ready[c], cs));
         }
         dd.means = P + off_m; dd.scales = P + off_s; dd.quats = P + off_q; dd.opacities = P + off_o; dd.sh = P + off_sh;
         if (n_views > 0) {
             CK(cudaMemcpyAsync(fr->st_poses.p, poses, 12 * sizeof(double) * n_views, cudaMemcpyHostToDevice, s));
-            // the loss input is first read by the backward: upload it on the side
-            // stream (after everything already queued on s) while the forward runs
-            if (!fr->side) {
-                CK(cudaStreamCreateWithFlags(&fr->side, cudaStreamNonBlocking));
-                CK(cudaEventCreateWithFlags(&fr->ev_fork, cudaEventDisableTiming));
-                CK(cudaEventCreateWithFlags(&fr->ev_join, cudaEventDisableTiming));
-            }
-            CK(cudaEventRecord(fr->ev_fork, s));
-            CK(cudaStreamWaitEvent(fr->side, fr->ev_fork, 0));
             CK(cudaMemcpyAsync(fr->st_target.p, in_img, n_img * sizeof(float), cudaMemcpyHostToDevice, fr->side));
             CK(cudaEventRecord(fr->ev_join, fr->side));
         }
@@ -893,25 +945,55 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
     gs_render_opts o2 = *opts;
     o2.flags &= ~(uint32_t)GS_F_HOST_IO;
     dl.loss = dloss;
-    rc = gs_render_forward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, nullptr, nullptr, stream);
+    const gs::SlicePipe* pipe = (host && fr->pipe.n_slices > 0) ? &fr->pipe : nullptr;
+    rc = gs::render_forward_impl(ctx, sc, n_views, views, nullptr, dposes, &o2, fr, dimage, nullptr, nullptr, s, pipe);
     if (rc == GS_OK && host && n_views > 0) {
+        if (image_out && n_img) {
+            // the rendered image goes down on the side stream while the backward runs
+            cudaError_t e = cudaEventRecord(fr->ev_img, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(fr->side, fr->ev_img, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, fr->side);
+            if (e != cudaSuccess) rc = fail(GS_ECUDA, "image download: %s", cudaGetErrorString(e));
+        }
         const cudaError_t e = cudaStreamWaitEvent(s, fr->ev_join, 0);
-        if (e != cudaSuccess) rc = fail(GS_ECUDA, "join of the loss-input upload: %s", cudaGetErrorString(e));
+        if (rc == GS_OK && e != cudaSuccess) rc = fail(GS_ECUDA, "join of the loss-input upload: %s", cudaGetErrorString(e));
     }
     if (rc == GS_OK)
-        rc = gs_render_backward(ctx, sc, n_views, views, dposes, &o2, fr, dimage, &dl, grads ? &dg : nullptr,
-                                dpose_grad, stream);
+        rc = gs::render_backward_impl(ctx, sc, n_views, views, nullptr, dposes, &o2, fr, dimage, &dl,
+                                      grads ? &dg : nullptr, dpose_grad, s, grads ? pipe : nullptr);
     gs_scene_free(sc);
     if (rc != GS_OK) return rc;
     if (host) {
-        if (image_out && n_img) CK(cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (image_out && n_img && n_views == 0)
+            CK(cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (grads && n > 0) {
+            // slice by slice on the side stream as each slice's gradients become
+            // final (one slice on s without the pipeline); s then waits for them
             const float* G = fr->st_grads.p;
-            if (grads->means) CK(cudaMemcpyAsync(grads->means, G + off_m, 3 * n * 4, cudaMemcpyDeviceToHost, s));
-            if (grads->scales) CK(cudaMemcpyAsync(grads->scales, G + off_s, 3 * n * 4, cudaMemcpyDeviceToHost, s));
-            if (grads->quats) CK(cudaMemcpyAsync(grads->quats, G + off_q, 4 * n * 4, cudaMemcpyDeviceToHost, s));
-            if (grads->opacities) CK(cudaMemcpyAsync(grads->opacities, G + off_o, n * 4, cudaMemcpyDeviceToHost, s));
-            if (grads->sh) CK(cudaMemcpyAsync(grads->sh, G + off_sh, 48 * n * 4, cudaMemcpyDeviceToHost, s));
+            const int ns = pipe ? pipe->n_slices : 1;
+            cudaStream_t ds = pipe ? fr->side : s;
+            for (int c = 0; c < ns; c++) {
+                const size_t b0 = pipe ? (size_t)pipe->bounds[c] : 0;
+                const size_t m = (pipe ? (size_t)pipe->bounds[c + 1] : n) - b0;
+                if (pipe) CK(cudaStreamWaitEvent(ds, pipe->done[c], 0));
+                if (grads->means)
+                    CK(cudaMemcpyAsync(grads->means + 3 * b0, G + off_m + 3 * b0, 3 * m * 4, cudaMemcpyDeviceToHost, ds));
+                if (grads->scales)
+                    CK(cudaMemcpyAsync(grads->scales + 3 * b0, G + off_s + 3 * b0, 3 * m * 4, cudaMemcpyDeviceToHost, ds));
+                if (grads->quats)
+                    CK(cudaMemcpyAsync(grads->quats + 4 * b0, G + off_q + 4 * b0, 4 * m * 4, cudaMemcpyDeviceToHost, ds));
+                if (grads->opacities)
+                    CK(cudaMemcpyAsync(grads->opacities + b0, G + off_o + b0, m * 4, cudaMemcpyDeviceToHost, ds));
+                if (grads->sh)
+                    CK(cudaMemcpyAsync(grads->sh + 48 * b0, G + off_sh + 48 * b0, 48 * m * 4, cudaMemcpyDeviceToHost, ds));
+            }
+        }
+        if (n_views > 0) {
+            // everything queued on the side stream (uploads, image and gradient
+            // downloads) is done when s passes this point
+            CK(cudaEventRecord(fr->ev_down, fr->side));
+            CK(cudaStreamWaitEvent(s, fr->ev_down, 0));
         }
         if (pose_grad && n_views)
             CK(cudaMemcpyAsync(pose_grad, dpose_grad, 6 * sizeof(double) * n_views, cudaMemcpyDeviceToHost, s));

@@ -107,8 +107,9 @@ namespace gs {
 void launch_setup_views(const gs_view* dummy, int n_views, const double* poses, ViewDev* views_dev,
                         const RenderParams& rp, cudaStream_t s);
 
+// [i_begin, i_end): the Gaussians this launch covers (i_end < 0: to the end)
 void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const ViewDev* views, const RenderParams& rp,
-                           SplatArrays sp, uint32_t* tile_counts, cudaStream_t s);
+                           SplatArrays sp, uint32_t* tile_counts, cudaStream_t s, int i_begin = 0, int i_end = -1);
 
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t scan_tmp_bytes(int n);
@@ -146,9 +147,11 @@ void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const View
                       const float* dldc, Grad2DArrays g2d, float* tile_loss, unsigned long long* counters,
                       int px_per_thread, cudaStream_t s);
 
+// [i_begin, i_end): the Gaussians this launch covers (i_begin a multiple of 256;
+// i_end < 0: to the end); n_blocks bounds the launch's blocks
 void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials,
-                           int n_blocks, cudaStream_t s);
+                           int n_blocks, cudaStream_t s, int i_begin = 0, int i_end = -1);
 int preprocess_bwd_blocks(int n);
 
 void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* pose_grad, cudaStream_t s);
@@ -219,14 +222,30 @@ int set_error(int code, const char* msg);
 int scene_count(const gs_scene* scene);
 uint32_t frames_num_keys(const gs_frames* fr);
 
+// Slices of the Gaussians for a step whose parameters arrive from and whose
+// gradients return to host memory: the forward preprocess of slice c waits
+// for ready[c] (its parameters are on the device), and the backward records
+// done[c] on the stream once slice c's gradients are final, so that copies of
+// one slice overlap the preprocess of the others.  bounds[c] are multiples of
+// 256 (the backward preprocess's block), bounds[n_slices] = N.
+#define GS_MAX_SLICES 8
+struct SlicePipe {
+    int n_slices = 0;
+    int bounds[GS_MAX_SLICES + 1] = {};
+    cudaEvent_t ready[GS_MAX_SLICES] = {};
+    cudaEvent_t done[GS_MAX_SLICES] = {};
+};
+
 // Forward / backward with optional per-view float offsets of the planar
 // images (img_offs == nullptr: packed layout).  Used by the serving loop,
 // whose views keep their images in fixed per-slot storage.
 int render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
                         const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
-                        float* image, const float* target, double* loss_out, cudaStream_t s);
+                        float* image, const float* target, double* loss_out, cudaStream_t s,
+                        const SlicePipe* pipe = nullptr);
 int render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, const gs_view* views,
                          const long long* img_offs, const double* poses, const gs_render_opts* opts, gs_frames* fr,
-                         const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad, cudaStream_t s);
+                         const float* image, const gs_loss* loss, gs_grads* grads, double* pose_grad, cudaStream_t s,
+                         const SlicePipe* pipe = nullptr);
 
 }  // namespace gs

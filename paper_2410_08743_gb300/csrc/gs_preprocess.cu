@@ -12,6 +12,8 @@
 // function of the inputs and reproducible bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -307,10 +309,12 @@ __device__ __forceinline__ void project_ff(float xh, float xl, float zh, float z
 }
 
 // ------------------------------------------------------------ forward
+// Gaussians [i_begin, i_end) of the scene (a launch may cover a slice, so that
+// the slices can start while later ones are still being uploaded).
 template <int D>
-__global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
-                                                        RenderParams rp, SplatArrays sp,
-                                                        uint32_t* __restrict__ tile_counts) {
+__global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int i_begin, int i_end, int n_views,
+                                                        const ViewDev* __restrict__ views, RenderParams rp,
+                                                        SplatArrays sp, uint32_t* __restrict__ tile_counts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ViewDev* sv = reinterpret_cast<ViewDev*>(smem_raw);
     {
@@ -320,8 +324,8 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views
         for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n) return;
+    const int i = i_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i_end) return;
     constexpr int NC = (D + 1) * (D + 1);
     float mu[3], s[3], q[4];
 #pragma unroll
@@ -387,17 +391,21 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int n_views
 }
 
 void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const ViewDev* views, const RenderParams& rp,
-                           SplatArrays sp, uint32_t* tile_counts, cudaStream_t s) {
-    if (sc.n <= 0 || n_views <= 0) return;
+                           SplatArrays sp, uint32_t* tile_counts, cudaStream_t s, int i_begin, int i_end) {
+    if (i_end < 0 || i_end > sc.n) i_end = sc.n;
+    if (i_begin < 0) i_begin = 0;
+    if (i_end <= i_begin || n_views <= 0) return;
     const int T = threads == 128 ? 128 : 256;
-    const int grid = (sc.n + T - 1) / T;
+    const int grid = (i_end - i_begin + T - 1) / T;
     const size_t sm = sizeof(ViewDev) * (size_t)n_views;
+#define GS_PRE_FWD(D) k_preprocess_fwd<D><<<grid, T, sm, s>>>(sc, i_begin, i_end, n_views, views, rp, sp, tile_counts)
     switch (sc.sh_degree) {
-        case 0: k_preprocess_fwd<0><<<grid, T, sm, s>>>(sc, n_views, views, rp, sp, tile_counts); break;
-        case 1: k_preprocess_fwd<1><<<grid, T, sm, s>>>(sc, n_views, views, rp, sp, tile_counts); break;
-        case 2: k_preprocess_fwd<2><<<grid, T, sm, s>>>(sc, n_views, views, rp, sp, tile_counts); break;
-        default: k_preprocess_fwd<3><<<grid, T, sm, s>>>(sc, n_views, views, rp, sp, tile_counts); break;
+        case 0: GS_PRE_FWD(0); break;
+        case 1: GS_PRE_FWD(1); break;
+        case 2: GS_PRE_FWD(2); break;
+        default: GS_PRE_FWD(3); break;
     }
+#undef GS_PRE_FWD
 }
 
 // ------------------------------------------------------------ backward
@@ -405,10 +413,14 @@ void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const V
 //   conic -> Sigma_hat -> (J, Sigma_c) -> mu_c, Sigma -> M -> (s, R -> q)
 //   colour -> SH coefficients and viewing direction -> mu
 //   pose: rho += g_mu_c + R_c g_mu(SH);  phi += mu_c x g_mu_c + 2 w(Sigma_c G_Sigma_c)
+// Gaussians [i_begin, i_end) of the scene; i_begin is a multiple of the block
+// size, and block b of the launch writes pose partial row i_begin / 256 + b, so
+// a sliced pass gives the same partials as one launch over all Gaussians.
 template <int D, bool POSE_ONLY>
-__global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_views, const ViewDev* __restrict__ views,
-                                                        RenderParams rp, SplatArrays sp, Grad2DArrays g2d,
-                                                        gs_grads grads, double* __restrict__ pose_partials) {
+__global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_begin, int i_end, int n_views,
+                                                        const ViewDev* __restrict__ views, RenderParams rp,
+                                                        SplatArrays sp, Grad2DArrays g2d, gs_grads grads,
+                                                        double* __restrict__ pose_partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ViewDev* sv = reinterpret_cast<ViewDev*>(smem_raw);
     const int nwarps = blockDim.x >> 5;
@@ -424,8 +436,8 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < sc.n;
+    const int i = i_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < i_end;
     constexpr int NC = (D + 1) * (D + 1);
     float mu[3] = {0, 0, 0}, s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.0f;
     float f[NC * 3];
@@ -668,7 +680,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int n_vi
     for (int t = threadIdx.x; t < n_views * 6; t += blockDim.x) {
         double acc = 0.0;
         for (int wi = 0; wi < nwarps; wi++) acc += spose[(size_t)wi * n_views * 6 + t];
-        pose_partials[(size_t)blockIdx.x * n_views * 6 + t] = acc;
+        pose_partials[((size_t)(i_begin / blockDim.x) + blockIdx.x) * n_views * 6 + t] = acc;
     }
 }
 
@@ -676,9 +688,13 @@ int preprocess_bwd_blocks(int n) { return (n + 255) / 256; }
 
 void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials, int n_blocks,
-                           cudaStream_t s) {
-    if (sc.n <= 0 || n_views <= 0) return;
+                           cudaStream_t s, int i_begin, int i_end) {
     const int T = 256;
+    if (i_end < 0 || i_end > sc.n) i_end = sc.n;
+    if (i_begin < 0) i_begin = 0;
+    i_begin -= i_begin % T;  // block-aligned
+    if (i_end <= i_begin || n_views <= 0) return;
+    n_blocks = std::min(n_blocks, (i_end - i_begin + T - 1) / T);
     const int nc3 = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
     const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6 +
                       sizeof(float) * nc3 * T;
@@ -697,8 +713,12 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
     }
     const bool po = !grads.means && !grads.scales && !grads.quats && !grads.opacities && !grads.sh;
 #define GS_PRE_BWD(D)                                                                                          \
-    if (po) k_preprocess_bwd<D, true><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials); \
-    else k_preprocess_bwd<D, false><<<n_blocks, T, sm, s>>>(sc, n_views, views, rp, sp, g2d, grads, pose_partials)
+    if (po)                                                                                                    \
+        k_preprocess_bwd<D, true><<<n_blocks, T, sm, s>>>(sc, i_begin, i_end, n_views, views, rp, sp, g2d, grads, \
+                                                          pose_partials);                                      \
+    else                                                                                                       \
+        k_preprocess_bwd<D, false><<<n_blocks, T, sm, s>>>(sc, i_begin, i_end, n_views, views, rp, sp, g2d, grads, \
+                                                           pose_partials)
     switch (sc.sh_degree) {
         case 0: GS_PRE_BWD(0); break;
         case 1: GS_PRE_BWD(1); break;
