@@ -555,6 +555,9 @@ void gs_frames_destroy(gs_frames* f) {
         if (f->pipe.ready[c]) cudaEventDestroy(f->pipe.ready[c]);
         if (f->pipe.done[c]) cudaEventDestroy(f->pipe.done[c]);
     }
+    if (f->pipe.fork) cudaEventDestroy(f->pipe.fork);
+    if (f->pipe.join) cudaEventDestroy(f->pipe.join);
+    if (f->pipe.aux) cudaStreamDestroy(f->pipe.aux);
     if (f->side) cudaStreamDestroy(f->side);
     delete f;
 }
@@ -638,11 +641,16 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         if (pipe && pipe->n_slices > 0) {
             // slice by slice, each as soon as its parameters are on the device
             PROF(PK_PRE_FWD, pipe->n_slices);
+            CK(cudaEventRecord(pipe->fork, s));
+            CK(cudaStreamWaitEvent(pipe->aux, pipe->fork, 0));
             for (int c = 0; c < pipe->n_slices; c++) {
-                if (v0 == 0) CK(cudaStreamWaitEvent(s, pipe->ready[c], 0));
+                cudaStream_t cs = (c & 1) ? pipe->aux : s;
+                if (v0 == 0) CK(cudaStreamWaitEvent(cs, pipe->ready[c], 0));
                 gs::launch_preprocess_fwd(scene->d, ctx->tune.preprocess_threads, nv, fr->vdev.p + v0, rp, spc,
-                                          nullptr, s, pipe->bounds[c], pipe->bounds[c + 1]);
+                                          nullptr, cs, pipe->bounds[c], pipe->bounds[c + 1]);
             }
+            CK(cudaEventRecord(pipe->join, pipe->aux));
+            CK(cudaStreamWaitEvent(s, pipe->join, 0));
         } else {
             PROF(PK_PRE_FWD, 1);
             gs::launch_preprocess_fwd(scene->d, ctx->tune.preprocess_threads, nv, fr->vdev.p + v0, rp, spc, nullptr, s);
@@ -810,11 +818,16 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         if (pipe && pipe->n_slices > 0) {
             // slice by slice; after the last view chunk a slice's gradients are final
             PROF(PK_PRE_BWD, pipe->n_slices);
+            CK(cudaEventRecord(pipe->fork, s));
+            CK(cudaStreamWaitEvent(pipe->aux, pipe->fork, 0));
             for (int k = 0; k < pipe->n_slices; k++) {
-                gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, s,
+                cudaStream_t cs = (k & 1) ? pipe->aux : s;
+                gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, cs,
                                           pipe->bounds[k], pipe->bounds[k + 1]);
-                if (c == nchunks - 1) CK(cudaEventRecord(pipe->done[k], s));
+                if (c == nchunks - 1) CK(cudaEventRecord(pipe->done[k], cs));
             }
+            CK(cudaEventRecord(pipe->join, pipe->aux));
+            CK(cudaStreamWaitEvent(s, pipe->join, 0));
         } else {
             PROF(PK_PRE_BWD, 1);
             gs::launch_preprocess_bwd(scene->d, nv, fr->vdev.p + v0, rp, spc, g2c, gg, part, nblk, s);
@@ -879,6 +892,9 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
                 CK(cudaEventCreateWithFlags(&fr->pipe.ready[c], cudaEventDisableTiming));
                 CK(cudaEventCreateWithFlags(&fr->pipe.done[c], cudaEventDisableTiming));
             }
+            CK(cudaStreamCreateWithFlags(&fr->pipe.aux, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&fr->pipe.fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&fr->pipe.join, cudaEventDisableTiming));
         }
         // The parameters go up in slices of Gaussians on the side stream (after
         // everything already queued on s, which may still read the staging

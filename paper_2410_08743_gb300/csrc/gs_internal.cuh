@@ -228,12 +228,17 @@ uint32_t frames_num_keys(const gs_frames* fr);
 // done[c] on the stream once slice c's gradients are final, so that copies of
 // one slice overlap the preprocess of the others.  bounds[c] are multiples of
 // 256 (the backward preprocess's block), bounds[n_slices] = N.
+// Odd slices run on `aux` (forked from and joined back into the caller's
+// stream around each sliced pass), so that one slice's last wave overlaps the
+// next slice's first.
 #define GS_MAX_SLICES 8
 struct SlicePipe {
     int n_slices = 0;
     int bounds[GS_MAX_SLICES + 1] = {};
     cudaEvent_t ready[GS_MAX_SLICES] = {};
     cudaEvent_t done[GS_MAX_SLICES] = {};
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Forward / backward with optional per-view float offsets of the planar
