@@ -284,6 +284,12 @@ def run_gpu(args):
     prof = L.gs_ctx_profile(r.ctx)
     L.gs_ctx_set_profiling(r.ctx, False)
     st = L.gs_status(r.ctx)
+    # the work counters come from one more (untimed) step with counting on; the
+    # timed steps run the blends without the counting bookkeeping
+    r.set_flags(L.GS_F_NO_SYNC | L.GS_F_COUNT)
+    step()
+    torch.cuda.synchronize()
+    r.set_flags(L.GS_F_NO_SYNC)
     counters = L.gs_frames_counters(r.frames)
     n_keys = int(r.query(L.GS_Q_NUM_KEYS)[0])
     value = world * npix / (ms * 1e-3) / 1e6

@@ -69,11 +69,15 @@ enum {
                                  view batches in turn and memory stays bounded by
                                  one batch's tile lists (the forward is deterministic,
                                  so the result is the same) */
-    GS_F_FULL_SORT = 1u << 2  /* sort every tile's whole list before blending.  By
+    GS_F_FULL_SORT = 1u << 2, /* sort every tile's whole list before blending.  By
                                  default a tile is sorted only as far as the forward
                                  blend consumes it (identical image and gradients);
                                  GS_Q_SORTED_IDX then holds each tile's sorted prefix
                                  of GS_Q_SORTED_COUNT entries. */
+    GS_F_COUNT = 1u << 4      /* the blends accumulate the work counters that
+                                 gs_frames_counters reads (off by default: counting
+                                 costs a few percent of the blends' instructions;
+                                 results are the same either way) */
 };
 
 typedef struct gs_ctx gs_ctx;
@@ -483,7 +487,8 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int64_t gs_ctx_launch_count(gs_ctx* ctx);
 
-/* Work counters of the last forward/backward of `fr` (synchronous):
+/* Work counters of the last forward/backward of `fr` (synchronous), counted
+ * only by passes run with GS_F_COUNT (zero otherwise):
  * out[0] (pixel, splat) pairs whose alpha the forward blend evaluated (pairs
  * inside the splat's alpha box), out[1] pairs blended, out[2] pairs whose
  * alpha the backward blend evaluated, out[3] pairs that

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgsplat.so")
 
 GS_OK, GS_PENDING = 0, 1
 GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3, -4, -5, -6
-GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT, GS_F_RECOMPUTE = 1, 2, 4, 8
+GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT, GS_F_RECOMPUTE, GS_F_COUNT = 1, 2, 4, 8, 16
 GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM, GS_LOSS_L1_MASKED = 0, 1, 2, 3
 (GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
  GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT) = range(11)

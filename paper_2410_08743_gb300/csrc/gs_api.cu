@@ -682,6 +682,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     }
     CK_LAUNCH();
     fr->full_sort = (opts->flags & GS_F_FULL_SORT) != 0;
+    unsigned long long* counters = (opts->flags & GS_F_COUNT) ? fr->counters.p : nullptr;
     if (fr->full_sort) {
         {
             PROF(PK_SORT, 4);
@@ -693,14 +694,14 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
             PROF(PK_BLEND_FWD, 1);
             gs::launch_blend_fwd(T, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->sorted_idx.p,
                                  cap, image, fr->T_final.p, fr->n_contrib.p, target,
-                                 target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
+                                 target ? fr->tile_loss.p : nullptr, counters, s);
         }
         CK_LAUNCH();
     } else {
         PROF(PK_BLEND_FWD, 1);
         gs::launch_blend_fwd_lazy(T, ctx->tune.sort_chunk, ctx->tune.fwd_pixels_per_thread, n_views, fr->tile_base.p, fr->vdev.p, rp, sp, n, fr->starts.p, fr->keys.p,
                                   fr->tmp_keys.p, fr->sorted_idx.p, fr->sorted_count.p, cap, image, fr->T_final.p,
-                                  fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr, fr->counters.p, s);
+                                  fr->n_contrib.p, target, target ? fr->tile_loss.p : nullptr, counters, s);
         CK_LAUNCH();
     }
     if (target && loss_out) {
@@ -790,7 +791,8 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         PROF(PK_BLEND_BWD, 1);
         gs::launch_blend_bwd(fr->total_tiles, n_views, fr->tile_base.p, fr->vdev.p, rp, fr->splats(), n, fr->starts.p,
                              fr->sorted_idx.p, cap, image, fr->T_final.p, fr->n_contrib.p, loss->kind, loss->w_l1,
-                             l1_mask_t, loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr, fr->counters.p + 2,
+                             l1_mask_t, loss->target, dldc, fr->g2d(), l1_loss ? fr->tile_loss.p : nullptr,
+                             (opts->flags & GS_F_COUNT) ? fr->counters.p + 2 : nullptr,
                              ctx->tune.bwd_pixels_per_thread, s);
     }
     CK_LAUNCH();

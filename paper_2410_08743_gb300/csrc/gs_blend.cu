@@ -299,7 +299,9 @@ struct LazySmem {
 // PX pixels per thread (1 or 2): each warp covers an 8 x (4 PX) pixel block.
 // Two pixels per thread share every shared-memory read of a splat and give
 // each thread two independent compositing chains.
-template <int LZ_CAP, int PX>
+// CNT: accumulate the work counters (pairs evaluated and blended, entries read
+// and sorted, warp entries); the timed variant carries none of that bookkeeping.
+template <int LZ_CAP, int PX, bool CNT>
 __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd_lazy(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, unsigned long long* __restrict__ keys,
@@ -548,7 +550,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
             tile_loss[t] = acc;
         }
     }
-    if (counters) {
+    if (CNT) {
         unsigned long long ce = n_eval, cbl = n_blend;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -567,22 +569,36 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
     }
 }
 
+template <int CAP, int PX, bool CNT>
+static void launch_lazy_cnt(int n_tiles, int n_views, const int* tile_base, const ViewDev* views,
+                            const RenderParams& rp, SplatArrays sp, int n, const uint32_t* starts,
+                            unsigned long long* keys, unsigned long long* tmp, uint32_t* sorted_idx,
+                            uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
+                            const float* target, float* tile_loss, unsigned long long* counters, cudaStream_t s) {
+    constexpr int NT = GS_TILE_PIX / PX;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_blend_fwd_lazy<CAP, PX, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LazySmem<CAP, NT>));
+        attr = true;
+    }
+    k_blend_fwd_lazy<CAP, PX, CNT><<<n_tiles, NT, sizeof(LazySmem<CAP, NT>), s>>>(
+        n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
+        n_contrib, target, tile_loss, counters);
+}
+
 template <int CAP, int PX>
 static void launch_lazy(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
                         SplatArrays sp, int n, const uint32_t* starts, unsigned long long* keys,
                         unsigned long long* tmp, uint32_t* sorted_idx, uint32_t* sorted_count, uint32_t cap,
                         float* image, float* T_final, uint32_t* n_contrib, const float* target, float* tile_loss,
                         unsigned long long* counters, cudaStream_t s) {
-    constexpr int NT = GS_TILE_PIX / PX;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_blend_fwd_lazy<CAP, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(LazySmem<CAP, NT>));
-        attr = true;
-    }
-    k_blend_fwd_lazy<CAP, PX><<<n_tiles, NT, sizeof(LazySmem<CAP, NT>), s>>>(
-        n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
-        n_contrib, target, tile_loss, counters);
+    if (counters)
+        launch_lazy_cnt<CAP, PX, true>(n_tiles, n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx,
+                                       sorted_count, cap, image, T_final, n_contrib, target, tile_loss, counters, s);
+    else
+        launch_lazy_cnt<CAP, PX, false>(n_tiles, n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx,
+                                        sorted_count, cap, image, T_final, n_contrib, target, tile_loss, counters, s);
 }
 
 void launch_blend_fwd_lazy(int n_tiles, int sort_chunk, int px_per_thread, int n_views, const int* tile_base,
@@ -654,7 +670,7 @@ struct BwdPixel {
 // PX pixels per thread (1 or 2): each warp covers an 8 x (4 PX) pixel block,
 // 8 / PX warps a tile.  With two pixels a lane sums both pixels' contributions
 // before the warp reduction, so one reduction serves 64 pixels.
-template <int PX>
+template <int PX, bool CNT>
 __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
@@ -747,7 +763,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
     uint32_t tile_last = 0;
     for (int w = 0; w < NW; w++) tile_last = max(tile_last, s_max[w]);
     if (tile_last > e - s) tile_last = e - s;
-    if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
+    if (CNT && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)tile_last);
     uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
     // component held by this lane after the transposed reduction
     const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
@@ -871,7 +887,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
             }
         }
     }
-    if (counters) {
+    if (CNT) {
         unsigned long long ce = n_eval, cu = n_used;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -893,14 +909,18 @@ void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const View
                       float l1_mask_t, const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
                       unsigned long long* counters, int px_per_thread, cudaStream_t s) {
     if (n_tiles <= 0) return;
-    if (px_per_thread == 2)
-        k_blend_bwd<2><<<n_tiles, GS_TILE_PIX / 2, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx,
-                                                           cap, image, T_final, n_contrib, loss_kind, w_l1, l1_mask_t,
-                                                           target, dldc, g2d, tile_loss, counters);
-    else
-        k_blend_bwd<1><<<n_tiles, GS_TILE_PIX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap,
-                                                       image, T_final, n_contrib, loss_kind, w_l1, l1_mask_t, target,
-                                                       dldc, g2d, tile_loss, counters);
+#define GS_BWD_LAUNCH(PX, CNT)                                                                                     \
+    k_blend_bwd<PX, CNT><<<n_tiles, GS_TILE_PIX / PX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts,         \
+                                                              sorted_idx, cap, image, T_final, n_contrib, loss_kind, \
+                                                              w_l1, l1_mask_t, target, dldc, g2d, tile_loss, counters)
+    if (px_per_thread == 2) {
+        if (counters) GS_BWD_LAUNCH(2, true);
+        else GS_BWD_LAUNCH(2, false);
+    } else {
+        if (counters) GS_BWD_LAUNCH(1, true);
+        else GS_BWD_LAUNCH(1, false);
+    }
+#undef GS_BWD_LAUNCH
 }
 
 }  // namespace gs

@@ -514,6 +514,38 @@ def test_forward_pixels_per_thread_is_result_neutral(R, case):
     assert n > 0
 
 
+@pytest.mark.parametrize("bwd_px", [1, 2])
+def test_work_counters_only_with_count_flag(R, bwd_px):
+    """The blends count their work only under GS_F_COUNT; image, per-pixel
+    state and gradients are the same with and without the counting."""
+    sc, views, poses = CASES["ragged_sh3"]()
+    rng = np.random.default_rng(7)
+    n_img = sum(3 * v["width"] * v["height"] for v in views)
+    dldc = rng.normal(size=n_img).astype(np.float32)
+    outs = []
+    try:
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, bwd_px, 2)
+        for flags in (0, L.GS_F_COUNT):
+            R.opts.flags = flags
+            p, P, img, _, _ = gpu_forward(R, sc, views, poses)
+            g, pg = gpu_backward_dldc(R, p, views, P, img, dldc)
+            outs.append((img.cpu().numpy(), R.query(L.GS_Q_T_FINAL), R.query(L.GS_Q_N_CONTRIB), g, pg,
+                         np.asarray(L.gs_frames_counters(R.frames))))
+    finally:
+        R.opts.flags = 0
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, 1, 1)
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert np.array_equal(a, b)
+    for k in outs[0][3]:
+        np.testing.assert_allclose(outs[1][3][k], outs[0][3][k], rtol=1e-4,
+                                   atol=1e-6 * float(np.abs(outs[0][3][k]).max() + 1e-30))
+    np.testing.assert_allclose(outs[1][4], outs[0][4], rtol=1e-5, atol=1e-9)
+    assert not outs[0][5].any()
+    c = outs[1][5]
+    assert c[0] >= c[1] > 0 and c[2] >= c[3] > 0 and c[1] == c[3]   # blended = contributing pairs
+    assert c[4] > 0 and c[5] > 0 and c[7] > 0 and c[8] >= c[9] > 0
+
+
 @pytest.mark.parametrize("n,with_image", [(3000, True), (300_000, True), (300_000, False)])
 def test_step_with_host_buffers_equals_device_path(R, n, with_image):
     """gs_step with GS_F_HOST_IO (host inputs and outputs, copies inside the
