@@ -147,8 +147,8 @@ void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const View
                       const float* dldc, Grad2DArrays g2d, float* tile_loss, unsigned long long* counters,
                       int px_per_thread, cudaStream_t s);
 
-// [i_begin, i_end): the Gaussians this launch covers (i_begin a multiple of 256;
-// i_end < 0: to the end); n_blocks bounds the launch's blocks
+// [i_begin, i_end): the Gaussians this launch covers (i_begin a multiple of the
+// block, 128; i_end < 0: to the end); n_blocks bounds the launch's blocks
 void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials,
                            int n_blocks, cudaStream_t s, int i_begin = 0, int i_end = -1);
@@ -227,7 +227,7 @@ uint32_t frames_num_keys(const gs_frames* fr);
 // for ready[c] (its parameters are on the device), and the backward records
 // done[c] on the stream once slice c's gradients are final, so that copies of
 // one slice overlap the preprocess of the others.  bounds[c] are multiples of
-// 256 (the backward preprocess's block), bounds[n_slices] = N.
+// 256 (a multiple of the backward preprocess's block), bounds[n_slices] = N.
 // Odd slices run on `aux` (forked from and joined back into the caller's
 // stream around each sliced pass), so that one slice's last wave overlaps the
 // next slice's first.

@@ -413,11 +413,32 @@ void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const V
 //   conic -> Sigma_hat -> (J, Sigma_c) -> mu_c, Sigma -> M -> (s, R -> q)
 //   colour -> SH coefficients and viewing direction -> mu
 //   pose: rho += g_mu_c + R_c g_mu(SH);  phi += mu_c x g_mu_c + 2 w(Sigma_c G_Sigma_c)
+// Asynchronous global -> shared copies (cp.async): a thread copies its own
+// 2D gradients of the next views into shared memory and reads them back after
+// waiting for their group, so several views' loads are in flight without
+// holding registers.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// views of 2D gradients staged ahead of their use
+#define PB_STAGES 4
+#define PB_T 128
+
 // Gaussians [i_begin, i_end) of the scene; i_begin is a multiple of the block
-// size, and block b of the launch writes pose partial row i_begin / 256 + b, so
+// size, and block b of the launch writes pose partial row i_begin / PB_T + b, so
 // a sliced pass gives the same partials as one launch over all Gaussians.
 template <int D, bool POSE_ONLY>
-__global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_begin, int i_end, int n_views,
+__global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_begin, int i_end, int n_views,
                                                         const ViewDev* __restrict__ views, RenderParams rp,
                                                         SplatArrays sp, Grad2DArrays g2d, gs_grads grads,
                                                         double* __restrict__ pose_partials) {
@@ -427,6 +448,12 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_be
     double* spose = reinterpret_cast<double*>(smem_raw + ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15));
     // SH-coefficient gradient accumulators of every thread, [coefficient][thread]
     float* sgf = reinterpret_cast<float*>(spose + (size_t)nwarps * n_views * 6);
+    // staged 2D gradients, [stage][thread]
+    constexpr int NC3 = 3 * (D + 1) * (D + 1);
+    float4* stA = reinterpret_cast<float4*>(
+        (reinterpret_cast<uintptr_t>(sgf + (size_t)NC3 * PB_T) + 15) & ~(uintptr_t)15);
+    float4* stB = stA + PB_STAGES * PB_T;
+    float* stC = reinterpret_cast<float*>(stB + PB_STAGES * PB_T);
     {
         const int words = n_views * (int)(sizeof(ViewDev) / 4);
         const int* src = reinterpret_cast<const int*>(views);
@@ -479,19 +506,32 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_be
 
     // The 2D gradients are zero for every culled (view, Gaussian) pair (the
     // buffers are cleared before the backward blend), so they are read without
-    // consulting the tile rectangle, one view ahead of their use.
-    float4 na4 = make_float4(0, 0, 0, 0), nb4 = make_float4(0, 0, 0, 0);
-    float nc1 = 0.0f;
-    if (live && n_views > 0) { na4 = g2d.gA[i]; nb4 = g2d.gB[i]; nc1 = g2d.gC[i]; }
+    // consulting the tile rectangle, PB_STAGES - 1 views ahead of their use.
+    const int tid = threadIdx.x;
+    auto stage_view = [&](int vv) {
+        if (live && vv < n_views) {
+            const size_t k = (size_t)vv * sc.n + i;
+            const int st = (vv % PB_STAGES) * PB_T + tid;
+            cp_async16(stA + st, g2d.gA + k);
+            cp_async16(stB + st, g2d.gB + k);
+            cp_async4(stC + st, g2d.gC + k);
+        }
+        cp_async_commit();   // one group per view, empty past the last view
+    };
+#pragma unroll
+    for (int vv = 0; vv < PB_STAGES - 1; vv++) stage_view(vv);
     for (int v = 0; v < n_views; v++) {
         const ViewDev& vd = sv[v];
         float pr[6] = {0, 0, 0, 0, 0, 0};
-        const float4 a4 = na4, b4 = nb4;
-        const float c1 = nc1;
-        if (live && v + 1 < n_views) {
-            const size_t kn = (size_t)(v + 1) * sc.n + i;
-            na4 = g2d.gA[kn]; nb4 = g2d.gB[kn]; nc1 = g2d.gC[kn];
+        cp_async_wait<PB_STAGES - 2>();   // view v's group has landed
+        float4 a4 = make_float4(0, 0, 0, 0), b4 = make_float4(0, 0, 0, 0);
+        float c1 = 0.0f;
+        if (live) {
+            const int st = (v % PB_STAGES) * PB_T + tid;
+            a4 = stA[st]; b4 = stB[st]; c1 = stC[st];
         }
+        // refill the stage consumed in the previous view
+        stage_view(v + PB_STAGES - 1);
         const bool act = (a4.x != 0.f) | (a4.y != 0.f) | (a4.z != 0.f) | (a4.w != 0.f) | (b4.x != 0.f) |
                          (b4.y != 0.f) | (b4.z != 0.f) | (b4.w != 0.f) | (c1 != 0.f);
         if (act) {
@@ -632,6 +672,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_be
             }
         }
     }
+    cp_async_wait_all();
     if (live && !POSE_ONLY) {
         // Sigma = M M^T -> dL/dM = 2 gSig M  (gSig symmetric)
         float GM[9];
@@ -684,12 +725,12 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(SceneDev sc, int i_be
     }
 }
 
-int preprocess_bwd_blocks(int n) { return (n + 255) / 256; }
+int preprocess_bwd_blocks(int n) { return (n + PB_T - 1) / PB_T; }
 
 void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views, const RenderParams& rp,
                            SplatArrays sp, Grad2DArrays g2d, gs_grads grads, double* pose_partials, int n_blocks,
                            cudaStream_t s, int i_begin, int i_end) {
-    const int T = 256;
+    const int T = PB_T;
     if (i_end < 0 || i_end > sc.n) i_end = sc.n;
     if (i_begin < 0) i_begin = 0;
     i_begin -= i_begin % T;  // block-aligned
@@ -697,7 +738,7 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
     n_blocks = std::min(n_blocks, (i_end - i_begin + T - 1) / T);
     const int nc3 = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
     const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6 +
-                      sizeof(float) * nc3 * T;
+                      sizeof(float) * nc3 * T + 16 + (size_t)PB_STAGES * T * (16 + 16 + 4);
     static bool attr = false;
     if (!attr) {
         const int mx = 200 * 1024;
