@@ -431,7 +431,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // views of 2D gradients staged ahead of their use
-#define PB_STAGES 4
+#define PB_STAGES 5
 #define PB_T 128
 
 // Gaussians [i_begin, i_end) of the scene; i_begin is a multiple of the block
