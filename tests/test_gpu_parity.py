@@ -546,14 +546,27 @@ def test_work_counters_only_with_count_flag(R, bwd_px):
     assert c[4] > 0 and c[5] > 0 and c[7] > 0 and c[8] >= c[9] > 0
 
 
-@pytest.mark.parametrize("n,with_image", [(3000, True), (300_000, True), (300_000, False)])
-def test_step_with_host_buffers_equals_device_path(R, n, with_image):
+def _many_views_case(n, n_views=70, seed=82):
+    """More views than one preprocess launch takes (64), so the sliced passes
+    run once per view chunk."""
+    rng = np.random.default_rng(seed)
+    sc = synth.make_scene_box(seed, n, sh_degree=1, lo=(-1, -1, 2.5), hi=(1, 1, 5))
+    views = [dict(fx=20.0, fy=21.0, cx=12.0, cy=10.0, width=24, height=20) for _ in range(n_views)]
+    base = synth.pose_from_center(np.eye(3), np.zeros(3))
+    poses = np.stack([synth.perturb_normal(rng, base, 3.0, 0.05) for _ in views])
+    return sc, views, poses
+
+
+@pytest.mark.parametrize("n,with_image,many_views", [(3000, True, False), (300_000, True, False),
+                                                     (300_000, False, False), (300_000, True, True)])
+def test_step_with_host_buffers_equals_device_path(R, n, with_image, many_views):
     """gs_step with GS_F_HOST_IO (host inputs and outputs, copies inside the
     call, the loss input uploaded beside the forward) equals the same step on
     device buffers; twice in a row, so the upload stream is reused.  At 300k
     Gaussians the parameters go up and the gradients come down in four slices
-    that overlap the preprocess kernels; with or without the image download."""
-    sc, views, poses = _ragged_case(81, n, 2)
+    that overlap the preprocess kernels; with or without the image download;
+    and with 70 views, two view chunks per preprocess pass."""
+    sc, views, poses = _many_views_case(n) if many_views else _ragged_case(81, n, 2)
     rng = np.random.default_rng(81)
     p = to_dev(sc)
     P = poses_dev(poses)
