@@ -165,51 +165,83 @@ void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m,
 // differentiates the activated scales s = exp(log s) and opacities
 // o = sigmoid(logit o), so the update first chains ds/dlog s = s and
 // do/dlogit = o (1 - o); it then writes the activated values the next render
-// reads.  One thread per parameter element; element k of Gaussian i in a
-// group of width w lives at i * w + k in both the parameter and moment arrays.
+// reads.  Element k of Gaussian i in a group of width w lives at i * w + k in
+// both the parameter and moment arrays.  Blocks are assigned to groups in
+// order (each group's elements padded to whole blocks), and a thread updates
+// ADAM_UNR elements of its group a block-width apart, so its loads of all of
+// them are in flight together.
+#define ADAM_T 256
+#define ADAM_UNR 4
 struct AdamGroups {
     AdamGroup g[5];
-    long long end[5];   // exclusive end of each group's element range (n * width, cumulative)
+    long long count_of[5];   // elements of each group (n * width)
+    int blk_end[5];          // exclusive end of each group's block range (cumulative)
     int count;
 };
 
-__global__ void k_gaussian_adam(int64_t n, AdamGroups A, float b1, float b2, float eps, float c1, float c2) {
-    const long long gidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gidx >= A.end[A.count - 1]) return;
+__global__ void __launch_bounds__(ADAM_T) k_gaussian_adam(AdamGroups A, float b1, float b2, float eps, float ic1,
+                                                          float ic2) {
     int gi = 0;
-    while (gi + 1 < A.count && gidx >= A.end[gi]) gi++;
+    while (gi + 1 < A.count && (int)blockIdx.x >= A.blk_end[gi]) gi++;
     const AdamGroup& G = A.g[gi];
-    const int64_t idx = gidx - (gi ? A.end[gi - 1] : 0);
-    const int k = (int)(idx % G.width);
-    if (k >= G.used) return;
-    float p = G.p[idx];
-    float g = G.g ? G.g[idx] : 0.0f;
-    if (G.act_kind == 1) g *= expf(p);
-    else if (G.act_kind == 2) { const float o = 1.0f / (1.0f + expf(-p)); g *= o * (1.0f - o); }
-    const float mk = b1 * G.m[idx] + (1.0f - b1) * g;
-    const float vk = b2 * G.v[idx] + (1.0f - b2) * g * g;
-    G.m[idx] = mk;
-    G.v[idx] = vk;
-    const float lr = k >= G.tail_from ? G.lr_tail : G.lr;
-    p -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
-    G.p[idx] = p;
-    if (G.act) G.act[idx] = G.act_kind == 1 ? expf(p) : 1.0f / (1.0f + expf(-p));
+    const long long cnt = A.count_of[gi];
+    const long long base = (long long)(blockIdx.x - (gi ? A.blk_end[gi - 1] : 0)) * (ADAM_T * ADAM_UNR) + threadIdx.x;
+    // the element's place in its Gaussian matters only for groups with unused
+    // or separately scheduled trailing elements (the SH coefficients)
+    const bool need_k = G.used < G.width || G.tail_from < G.width;
+    float p[ADAM_UNR], g[ADAM_UNR], m[ADAM_UNR], v[ADAM_UNR];
+#pragma unroll
+    for (int u = 0; u < ADAM_UNR; u++) {
+        const long long idx = base + u * ADAM_T;
+        p[u] = g[u] = m[u] = v[u] = 0.0f;
+        if (idx < cnt) {
+            p[u] = G.p[idx];
+            g[u] = G.g ? G.g[idx] : 0.0f;
+            m[u] = G.m[idx];
+            v[u] = G.v[idx];
+        }
+    }
+    // k of the first element, then stepped by ADAM_T mod width
+    int k = 0, dk = 0;
+    if (need_k) {
+        k = base < 0x7fffffffLL ? (int)((unsigned)base % (unsigned)G.width) : (int)(base % G.width);
+        dk = ADAM_T % G.width;
+    }
+#pragma unroll
+    for (int u = 0; u < ADAM_UNR; u++, k = (k + dk >= G.width) ? k + dk - G.width : k + dk) {
+        const long long idx = base + u * ADAM_T;
+        if (idx >= cnt) continue;
+        if (k >= G.used) continue;
+        float pu = p[u], gu = g[u];
+        if (G.act_kind == 1) gu *= expf(pu);
+        else if (G.act_kind == 2) { const float o = 1.0f / (1.0f + expf(-pu)); gu *= o * (1.0f - o); }
+        const float mk = b1 * m[u] + (1.0f - b1) * gu;
+        const float vk = b2 * v[u] + (1.0f - b2) * gu * gu;
+        G.m[idx] = mk;
+        G.v[idx] = vk;
+        const float lr = k >= G.tail_from ? G.lr_tail : G.lr;
+        pu -= lr * (mk * ic1) / (sqrtf(vk * ic2) + eps);
+        G.p[idx] = pu;
+        if (G.act) G.act[idx] = G.act_kind == 1 ? expf(pu) : 1.0f / (1.0f + expf(-pu));
+    }
 }
 
-// All groups in one launch: element e of the concatenated group ranges.
+// All groups in one launch.
 void launch_gaussian_adam(int64_t n, const AdamGroup* groups, int n_groups, float b1, float b2, float eps, int step,
                           cudaStream_t s) {
     if (n <= 0 || n_groups <= 0) return;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     AdamGroups A{};
     A.count = n_groups > 5 ? 5 : n_groups;
-    long long acc = 0;
+    long long blocks = 0;
     for (int k = 0; k < A.count; k++) {
         A.g[k] = groups[k];
-        acc += n * groups[k].width;
-        A.end[k] = acc;
+        A.count_of[k] = n * groups[k].width;
+        blocks += (A.count_of[k] + ADAM_T * ADAM_UNR - 1) / (ADAM_T * ADAM_UNR);
+        A.blk_end[k] = (int)blocks;
     }
-    k_gaussian_adam<<<(unsigned)((acc + 255) / 256), 256, 0, s>>>(n, A, b1, b2, eps, c1, c2);
+    if (blocks <= 0) return;
+    k_gaussian_adam<<<(unsigned)blocks, ADAM_T, 0, s>>>(A, b1, b2, eps, 1.0f / c1, 1.0f / c2);
 }
 
 }  // namespace gs
