@@ -447,11 +447,16 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     const int nwarps = blockDim.x >> 5;
     double* spose = reinterpret_cast<double*>(smem_raw + ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15));
     // SH-coefficient gradient accumulators of every thread, [coefficient][thread]
+    // with rows padded to PB_T + 1 floats, so that both a thread's walk over its
+    // coefficients and the block's row-major copies to and from global memory
+    // are free of bank conflicts.  Before the view loop it holds the block's SH
+    // coefficients on their way into registers.
+    constexpr int SGS = PB_T + 1;
     float* sgf = reinterpret_cast<float*>(spose + (size_t)nwarps * n_views * 6);
     // staged 2D gradients, [stage][thread]
     constexpr int NC3 = 3 * (D + 1) * (D + 1);
     float4* stA = reinterpret_cast<float4*>(
-        (reinterpret_cast<uintptr_t>(sgf + (size_t)NC3 * PB_T) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(sgf + (size_t)NC3 * SGS) + 15) & ~(uintptr_t)15);
     float4* stB = stA + PB_STAGES * PB_T;
     float* stC = reinterpret_cast<float*>(stB + PB_STAGES * PB_T);
     {
@@ -463,13 +468,23 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = i_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = i_begin + blockIdx.x * PB_T;            // the block's first Gaussian
+    const int m_blk = min(PB_T, i_end - i0);               // its Gaussians
+    const int i = i0 + threadIdx.x;
     const bool live = i < i_end;
     constexpr int NC = (D + 1) * (D + 1);
     float mu[3] = {0, 0, 0}, s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.0f;
+    // SH coefficients: the block's rows (48 floats per Gaussian) read row-major
+    // (coalesced) into shared memory, then each thread takes its own
+    for (int e = threadIdx.x; e < m_blk * 48; e += PB_T) {
+        const int r = e / 48, c = e - r * 48;
+        if (c < NC3) sgf[c * SGS + r] = sc.sh[(size_t)i0 * 48 + e];
+    }
+    __syncthreads();
     float f[NC * 3];
 #pragma unroll
-    for (int k = 0; k < NC * 3; k++) f[k] = 0.0f;
+    for (int k = 0; k < NC * 3; k++) f[k] = live ? sgf[k * SGS + threadIdx.x] : 0.0f;
+    __syncthreads();
     if (live) {
 #pragma unroll
         for (int k = 0; k < 3; k++) { mu[k] = sc.means[3 * i + k]; s[k] = sc.scales[3 * i + k]; }
@@ -477,9 +492,6 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
         qlen = sqrtf(qq.x * qq.x + qq.y * qq.y + qq.z * qq.z + qq.w * qq.w);
         float il = 1.0f / qlen;
         qn[0] = qq.x * il; qn[1] = qq.y * il; qn[2] = qq.z * il; qn[3] = qq.w * il;
-        const float* fs = sc.sh + (size_t)i * 48;
-#pragma unroll
-        for (int k = 0; k < NC * 3; k++) f[k] = fs[k];
     }
     // rotation, M = R diag(s), Sigma = M M^T (value path)
     const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
@@ -502,7 +514,7 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     for (int k = 0; k < 9; k++) gSig[k] = 0.0f;
     float gop = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NC * 3; k++) sgf[k * blockDim.x + threadIdx.x] = 0.0f;
+    for (int k = 0; k < NC * 3; k++) sgf[k * SGS + threadIdx.x] = 0.0f;
 
     // The 2D gradients are zero for every culled (view, Gaussian) pair (the
     // buffers are cleared before the backward blend), so they are read without
@@ -631,7 +643,7 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
                 const float gch = raw < 0.0f ? 0.0f : gcol[ch];
 #pragma unroll
                 for (int b = 0; b < NC; b++) {
-                    if constexpr (!POSE_ONLY) sgf[(b * 3 + ch) * blockDim.x + threadIdx.x] += Y[b] * gch;
+                    if constexpr (!POSE_ONLY) sgf[(b * 3 + ch) * SGS + threadIdx.x] += Y[b] * gch;
                     wsum[b] += f[b * 3 + ch] * gch;
                 }
             }
@@ -710,13 +722,15 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
             *gqp = o4;
         }
         if (grads.opacities) grads.opacities[i] += gop;
-        if (grads.sh) {
-            float* gsp = grads.sh + (size_t)i * 48;
-#pragma unroll
-            for (int kk = 0; kk < NC * 3; kk++) gsp[kk] += sgf[kk * blockDim.x + threadIdx.x];
-        }
     }
     __syncthreads();
+    if (!POSE_ONLY && grads.sh) {
+        // SH gradients added row-major (coalesced) from the accumulators
+        for (int e = threadIdx.x; e < m_blk * 48; e += PB_T) {
+            const int r = e / 48, c = e - r * 48;
+            if (c < NC3) grads.sh[(size_t)i0 * 48 + e] += sgf[c * SGS + r];
+        }
+    }
     // block partial of every view's pose gradient, warps summed in order
     for (int t = threadIdx.x; t < n_views * 6; t += blockDim.x) {
         double acc = 0.0;
@@ -738,7 +752,7 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
     n_blocks = std::min(n_blocks, (i_end - i_begin + T - 1) / T);
     const int nc3 = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
     const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6 +
-                      sizeof(float) * nc3 * T + 16 + (size_t)PB_STAGES * T * (16 + 16 + 4);
+                      sizeof(float) * nc3 * (T + 1) + 16 + (size_t)PB_STAGES * T * (16 + 16 + 4);
     static bool attr = false;
     if (!attr) {
         const int mx = 200 * 1024;
