@@ -205,6 +205,10 @@ struct gs_frames {
     // per (view, Gaussian)
     DevBuf<float4> A, B, gA, gB;
     DevBuf<float> Cb, depth, gC;
+    // leading (view, Gaussian) records of gA/gB/gC known to be zero: the
+    // backward preprocess clears every record it consumes, so after a complete
+    // backward the next one needs no clearing pass over the records it uses
+    size_t g2d_zero = 0;
     DevBuf<uint2> rect;
     DevBuf<float2> Mlo;
     DevBuf<int> radius;
@@ -750,10 +754,16 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
     CK(cudaSetDevice(ctx->device));
     const int n = scene->d.n;
     const size_t vn = (size_t)n * n_views;
-    if ((rc = fr->gA.ensure(std::max<size_t>(vn, 1), grow, "g2d A")) ||
-        (rc = fr->gB.ensure(std::max<size_t>(vn, 1), grow, "g2d B")) ||
-        (rc = fr->gC.ensure(std::max<size_t>(vn, 1), grow, "g2d C")))
-        return rc;
+    {
+        const void* before[3] = {fr->gA.p, fr->gB.p, fr->gC.p};
+        if ((rc = fr->gA.ensure(std::max<size_t>(vn, 1), grow, "g2d A")) ||
+            (rc = fr->gB.ensure(std::max<size_t>(vn, 1), grow, "g2d B")) ||
+            (rc = fr->gC.ensure(std::max<size_t>(vn, 1), grow, "g2d C"))) {
+            fr->g2d_zero = 0;
+            return rc;
+        }
+        if (before[0] != fr->gA.p || before[1] != fr->gB.p || before[2] != fr->gC.p) fr->g2d_zero = 0;  // new storage
+    }
     const int nblk = gs::preprocess_bwd_blocks(n);
     const int nchunks = (n_views + kViewChunk - 1) / kViewChunk;
     if ((rc = fr->pose_partials.ensure((size_t)std::max(nblk, 1) * n_views * 6 + 6, grow, "pose partials"))) return rc;
@@ -780,12 +790,15 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         CK_LAUNCH();
         dldc = fr->dldc_ssim.p;
     }
-    {
+    // the backward blend accumulates into records [0, vn), which must start at zero
+    const size_t g2d_zero_after = std::max(fr->g2d_zero, vn);
+    if (fr->g2d_zero < vn) {
         PROF(PK_MEMSET, 0);
         CK(cudaMemsetAsync(fr->gA.p, 0, sizeof(float4) * vn, s));
         CK(cudaMemsetAsync(fr->gB.p, 0, sizeof(float4) * vn, s));
         CK(cudaMemsetAsync(fr->gC.p, 0, sizeof(float) * vn, s));
     }
+    fr->g2d_zero = 0;   // until the backward preprocess has cleared them again
     const uint32_t cap = (uint32_t)std::min<size_t>(fr->keys.cap, 0xffffffffu);
     {
         PROF(PK_BLEND_BWD, 1);
@@ -841,6 +854,7 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
             CK_LAUNCH();
         }
     }
+    fr->g2d_zero = g2d_zero_after;   // every record of [0, vn) was consumed and cleared
     return GS_OK;
 }
 

@@ -517,8 +517,9 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     for (int k = 0; k < NC * 3; k++) sgf[k * SGS + threadIdx.x] = 0.0f;
 
     // The 2D gradients are zero for every culled (view, Gaussian) pair (the
-    // buffers are cleared before the backward blend), so they are read without
-    // consulting the tile rectangle, PB_STAGES - 1 views ahead of their use.
+    // records are zero before the backward blend), so they are read without
+    // consulting the tile rectangle, PB_STAGES - 1 views ahead of their use;
+    // each record is cleared once read, which restores that state.
     const int tid = threadIdx.x;
     auto stage_view = [&](int vv) {
         if (live && vv < n_views) {
@@ -547,6 +548,11 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
         const bool act = (a4.x != 0.f) | (a4.y != 0.f) | (a4.z != 0.f) | (a4.w != 0.f) | (b4.x != 0.f) |
                          (b4.y != 0.f) | (b4.z != 0.f) | (b4.w != 0.f) | (c1 != 0.f);
         if (act) {
+            // consumed: cleared for the next backward blend, which accumulates into it
+            const size_t k = (size_t)v * sc.n + i;
+            g2d.gA[k] = make_float4(0, 0, 0, 0);
+            g2d.gB[k] = make_float4(0, 0, 0, 0);
+            g2d.gC[k] = 0.0f;
             const float* Rc = vd.Rf;
             const float fx = vd.fx, fy = vd.fy;
             float mc[3];

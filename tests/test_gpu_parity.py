@@ -514,6 +514,33 @@ def test_forward_pixels_per_thread_is_result_neutral(R, case):
     assert n > 0
 
 
+def test_backward_state_carries_over_between_batches(R):
+    """The backward preprocess leaves the 2D-gradient records cleared for the
+    next backward (which then skips its clearing pass): a backward of three
+    views, one of a single view, and the three views again give the first
+    result again, as does a backward after a larger batch grew the buffers."""
+    sc, views, poses = CASES["ragged_sh3"]()
+    rng = np.random.default_rng(9)
+    n_img = sum(3 * v["width"] * v["height"] for v in views)
+    dldc = rng.normal(size=n_img).astype(np.float32)
+    n0 = 3 * views[0]["width"] * views[0]["height"]
+    res = []
+    for sel in ([0, 1, 2], [0], [0, 1, 2], [2, 1, 0, 2, 1], [0, 1, 2]):
+        vs = [views[k] for k in sel]
+        ps = poses[sel]
+        offs = np.cumsum([0] + [3 * views[k]["width"] * views[k]["height"] for k in range(3)])
+        d = np.concatenate([dldc[offs[k]:offs[k + 1]] for k in sel])
+        p, P, img, _, _ = gpu_forward(R, sc, vs, ps)
+        g, pg = gpu_backward_dldc(R, p, vs, P, img, d)
+        res.append((sel, g, pg))
+    ref = res[0]
+    for sel, g, pg in (res[2], res[4]):
+        for k in g:
+            np.testing.assert_allclose(g[k], ref[1][k], rtol=1e-4, atol=1e-6 * float(np.abs(ref[1][k]).max() + 1e-30))
+        np.testing.assert_allclose(pg, ref[2], rtol=1e-5, atol=1e-9)
+    assert n0 > 0
+
+
 @pytest.mark.parametrize("bwd_px", [1, 2])
 def test_work_counters_only_with_count_flag(R, bwd_px):
     """The blends count their work only under GS_F_COUNT; image, per-pixel
