@@ -181,7 +181,7 @@ struct gs_frames {
     gs_ctx* ctx = nullptr;
     // gs_step with host buffers: side stream that uploads the loss input while
     // the forward runs, and its fork/join events
-    cudaStream_t side = nullptr;
+    cudaStream_t side = nullptr, down = nullptr;   // uploads / downloads
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // ... and the events of its Gaussian slices (parameters uploaded, gradients
     // final) and of the end of the gradient download
@@ -563,6 +563,7 @@ void gs_frames_destroy(gs_frames* f) {
     if (f->pipe.join) cudaEventDestroy(f->pipe.join);
     if (f->pipe.aux) cudaStreamDestroy(f->pipe.aux);
     if (f->side) cudaStreamDestroy(f->side);
+    if (f->down) cudaStreamDestroy(f->down);
     delete f;
 }
 
@@ -900,6 +901,7 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
         float* P = fr->st_params.p;
         if (n_views > 0 && !fr->side) {
             CK(cudaStreamCreateWithFlags(&fr->side, cudaStreamNonBlocking));
+            CK(cudaStreamCreateWithFlags(&fr->down, cudaStreamNonBlocking));
             CK(cudaEventCreateWithFlags(&fr->ev_fork, cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&fr->ev_join, cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&fr->ev_down, cudaEventDisableTiming));
@@ -983,9 +985,9 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
         if (image_out && n_img) {
             // the rendered image goes down on the side stream while the backward runs
             cudaError_t e = cudaEventRecord(fr->ev_img, s);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(fr->side, fr->ev_img, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(fr->down, fr->ev_img, 0);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, fr->side);
+                e = cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, fr->down);
             if (e != cudaSuccess) rc = fail(GS_ECUDA, "image download: %s", cudaGetErrorString(e));
         }
         const cudaError_t e = cudaStreamWaitEvent(s, fr->ev_join, 0);
@@ -1004,7 +1006,7 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
             // final (one slice on s without the pipeline); s then waits for them
             const float* G = fr->st_grads.p;
             const int ns = pipe ? pipe->n_slices : 1;
-            cudaStream_t ds = pipe ? fr->side : s;
+            cudaStream_t ds = pipe ? fr->down : s;
             for (int c = 0; c < ns; c++) {
                 const size_t b0 = pipe ? (size_t)pipe->bounds[c] : 0;
                 const size_t m = (pipe ? (size_t)pipe->bounds[c + 1] : n) - b0;
@@ -1022,9 +1024,9 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
             }
         }
         if (n_views > 0) {
-            // everything queued on the side stream (uploads, image and gradient
-            // downloads) is done when s passes this point
-            CK(cudaEventRecord(fr->ev_down, fr->side));
+            // the downloads (image and gradients) are done when s passes this
+            // point; the uploads were joined before the backward
+            CK(cudaEventRecord(fr->ev_down, fr->down));
             CK(cudaStreamWaitEvent(s, fr->ev_down, 0));
         }
         if (pose_grad && n_views)
