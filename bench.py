@@ -684,12 +684,11 @@ def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_reques
 OPS_FWD_EVAL, OPS_FWD_BLEND = 16, 7
 OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 
-# DRAM bytes (read + write) per unit from one ncu capture of the current
-# kernel on the 4-view small case, scaled to a launch by the run's units
-# (profiles/top_kernels_batched_1M_4views.md).  Re-measure when the kernel changes.
-# kernel -> (DRAM bytes per unit, counter index) from an ncu capture of the same kernel
-# (k_blend_bwd<2>: 35,705,856 B for 852,644 list entries read, 4 views at 1M Gaussians)
-TRAFFIC_PER_UNIT = {"blend_bwd": (41.88, 5)}
+# kernel -> (DRAM bytes, read + write, per unit; counter index of the unit) from one
+# ncu capture of the current kernel on the 4-view small case, scaled to a launch by
+# the run's units; re-measure when the kernel changes.
+# k_blend_bwd<2, 0>: 35,698,176 B for 852,644 list entries read, 4 views at 1M Gaussians.
+TRAFFIC_PER_UNIT = {"blend_bwd": (41.87, 5)}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
