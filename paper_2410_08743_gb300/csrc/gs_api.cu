@@ -179,12 +179,14 @@ static const size_t kMaxViewTables = 64;
 
 struct gs_frames {
     gs_ctx* ctx = nullptr;
-    // gs_step with host buffers: side stream that uploads the loss input while
-    // the forward runs, and its fork/join events
-    cudaStream_t side = nullptr, down = nullptr;   // uploads / downloads
+    // gs_step with host buffers: the stream that uploads the parameters and the
+    // loss input while the forward runs (fork: after the caller's queued work;
+    // join: before the backward) and the stream that downloads the image and
+    // the gradients while the backward runs
+    cudaStream_t side = nullptr, down = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // ... and the events of its Gaussian slices (parameters uploaded, gradients
-    // final) and of the end of the gradient download
+    // ... the events of its Gaussian slices (parameters uploaded, gradients
+    // final), of the rendered image, and of the end of the downloads
     gs::SlicePipe pipe;
     cudaEvent_t ev_down = nullptr, ev_img = nullptr;
     // launch configuration of the last forward
@@ -983,7 +985,7 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
     rc = gs::render_forward_impl(ctx, sc, n_views, views, nullptr, dposes, &o2, fr, dimage, nullptr, nullptr, s, pipe);
     if (rc == GS_OK && host && n_views > 0) {
         if (image_out && n_img) {
-            // the rendered image goes down on the side stream while the backward runs
+            // the rendered image goes down on the download stream while the backward runs
             cudaError_t e = cudaEventRecord(fr->ev_img, s);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(fr->down, fr->ev_img, 0);
             if (e == cudaSuccess)
@@ -997,13 +999,18 @@ int gs_step(gs_ctx* ctx, gs_frames* fr, const gs_scene_desc* sd, int n_views, co
         rc = gs::render_backward_impl(ctx, sc, n_views, views, nullptr, dposes, &o2, fr, dimage, &dl,
                                       grads ? &dg : nullptr, dpose_grad, s, grads ? pipe : nullptr);
     gs_scene_free(sc);
-    if (rc != GS_OK) return rc;
+    if (rc != GS_OK) {
+        // a failed step still leaves nothing of it pending on the download stream
+        if (host && n_views > 0 && cudaEventRecord(fr->ev_down, fr->down) == cudaSuccess)
+            cudaStreamWaitEvent(s, fr->ev_down, 0);
+        return rc;
+    }
     if (host) {
         if (image_out && n_img && n_views == 0)
             CK(cudaMemcpyAsync(image_out, dimage, n_img * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (grads && n > 0) {
-            // slice by slice on the side stream as each slice's gradients become
-            // final (one slice on s without the pipeline); s then waits for them
+            // slice by slice on the download stream as each slice's gradients
+            // become final (one slice on s without the pipeline); s then waits
             const float* G = fr->st_grads.p;
             const int ns = pipe ? pipe->n_slices : 1;
             cudaStream_t ds = pipe ? fr->down : s;
