@@ -60,7 +60,9 @@ def _args():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms.  start()
+    returns once the sampler is producing rows, and stop() keeps only the rows
+    written after that, i.e. during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -77,10 +79,21 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (up to 5 s) for the first row, so that sampling covers the timed region
+        self.skip = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            with open(self.path) as fh:
+                n = sum(1 for _ in fh)
+            if n > 0:
+                self.skip = n
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -92,7 +105,9 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         rows = []
-        for line in open(self.path):
+        for k, line in enumerate(open(self.path)):
+            if k < getattr(self, "skip", 0):
+                continue   # written before the timed region began
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
