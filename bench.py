@@ -139,6 +139,18 @@ def _workload(args, rank: int):
     return w
 
 
+def _config(w, world: int) -> dict:
+    """The workload's description, the same for both arms."""
+    n = len(w["scene"]["opac"])
+    V = len(w["views"])
+    npix = sum(v["width"] * v["height"] for v in w["views"])
+    return {"workload": f"batched fwd+bwd: {n} Gaussians SH3, {V} views mixed 256x192/504x378/1008x756 "
+                        f"({npix / 1e6:.2f} Mpix/step/GPU), L1 loss, all Gaussian grads + {V} pose grads",
+            "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
+            "layout": "Gaussians in Morton order of their means (gs_spatial_order at scene load)",
+            "parallelism": f"views sharded over {world} GPU(s), scene replicated"}
+
+
 def _sample_views(w, n_views: int):
     """One view of each resolution first, then the next views in order."""
     pick, seen = [], set()
@@ -173,7 +185,8 @@ def _cpu_baseline(w, n_views: int):
     dt = time.perf_counter() - t0
     mpix = sum(v["width"] * v["height"] for v in views) / 1e6
     sample = (f"{n_views} view(s) ({', '.join(str(v['width']) + 'x' + str(v['height']) for v in views)}) of the "
-              f"{len(w['scene']['opac'])}-Gaussian scene, forward + L1 + backward incl. pose, FP64")
+              f"{len(w['scene']['opac'])}-Gaussian scene (in generation order), forward + L1 + backward incl. "
+              f"pose, FP64")
     return {"value": mpix / dt, "unit": UNIT, "cores": nthr, "kind": "oracle", "sample": sample,
             "seconds": dt}
 
@@ -195,7 +208,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(t_all)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"oracle sample of the batched workload ({nv} view(s))"},
+            "config": _config(w, 1),
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -454,11 +467,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"batched fwd+bwd: {n} Gaussians SH3, {V} views mixed 256x192/504x378/1008x756 "
-                                   f"({npix / 1e6:.2f} Mpix/step/GPU), L1 loss, all Gaussian grads + {V} pose grads",
-                       "l2": "inputs larger than L2 (scene 236 MB, per-(view,Gaussian) splats >3 GB)",
-                       "layout": "Gaussians in Morton order of their means (gs_spatial_order at scene load)",
-                       "parallelism": f"views sharded over {world} GPU(s), scene replicated"},
+            "config": _config(w, world),
             "plain_value": plain_value, "graph_value": graph_value, "serving": serving,
             "joint": joint, "trajectory": traj, "extras": extras,
             "tuning": tuned,
