@@ -476,9 +476,24 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     float mu[3] = {0, 0, 0}, s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qlen = 1.0f;
     // SH coefficients: the block's rows (48 floats per Gaussian) read row-major
     // (coalesced) into shared memory, then each thread takes its own
-    for (int e = threadIdx.x; e < m_blk * 48; e += PB_T) {
-        const int r = e / 48, c = e - r * 48;
-        if (c < NC3) sgf[c * SGS + r] = sc.sh[(size_t)i0 * 48 + e];
+    {
+        // eight loads per thread in flight before their stores
+        const int tot = m_blk * 48;
+        const float* src = sc.sh + (size_t)i0 * 48;
+        for (int e0 = threadIdx.x; e0 < tot; e0 += PB_T * 8) {
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * PB_T;
+                x[u] = e < tot ? src[e] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * PB_T;
+                const int r = e / 48, c = e - r * 48;
+                if (e < tot && c < NC3) sgf[c * SGS + r] = x[u];
+            }
+        }
     }
     __syncthreads();
     float f[NC * 3];
@@ -732,9 +747,22 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
     __syncthreads();
     if (!POSE_ONLY && grads.sh) {
         // SH gradients added row-major (coalesced) from the accumulators
-        for (int e = threadIdx.x; e < m_blk * 48; e += PB_T) {
-            const int r = e / 48, c = e - r * 48;
-            if (c < NC3) grads.sh[(size_t)i0 * 48 + e] += sgf[c * SGS + r];
+        const int tot = m_blk * 48;
+        float* dst = grads.sh + (size_t)i0 * 48;
+        for (int e0 = threadIdx.x; e0 < tot; e0 += PB_T * 8) {
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * PB_T;
+                const int c = e % 48;
+                x[u] = (e < tot && c < NC3) ? dst[e] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * PB_T;
+                const int r = e / 48, c = e - r * 48;
+                if (e < tot && c < NC3) dst[e] = x[u] + sgf[c * SGS + r];
+            }
         }
     }
     // block partial of every view's pose gradient, warps summed in order
