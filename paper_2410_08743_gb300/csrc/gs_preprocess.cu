@@ -727,22 +727,29 @@ __global__ void __launch_bounds__(PB_T, 3) k_preprocess_bwd(SceneDev sc, int i_b
         gq[3] = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
         const float dq = gq[0] * qn[0] + gq[1] * qn[1] + gq[2] * qn[2] + gq[3] * qn[3];
         const float iq = 1.0f / qlen;
+        // every old value is loaded before the first store, so the loads are in
+        // flight together (the arrays may alias as far as the compiler knows)
+        float om[3] = {0, 0, 0}, os[3] = {0, 0, 0}, oo = 0.0f;
+        float4 o4 = make_float4(0, 0, 0, 0);
+        float4* gqp = grads.quats ? reinterpret_cast<float4*>(grads.quats) + i : nullptr;
+        if (grads.means) { om[0] = grads.means[3 * i]; om[1] = grads.means[3 * i + 1]; om[2] = grads.means[3 * i + 2]; }
+        if (grads.scales) { os[0] = grads.scales[3 * i]; os[1] = grads.scales[3 * i + 1]; os[2] = grads.scales[3 * i + 2]; }
+        if (gqp) o4 = *gqp;
+        if (grads.opacities) oo = grads.opacities[i];
         if (grads.means) {
 #pragma unroll
-            for (int a = 0; a < 3; a++) grads.means[3 * i + a] += gmu[a];
+            for (int a = 0; a < 3; a++) grads.means[3 * i + a] = om[a] + gmu[a];
         }
         if (grads.scales) {
 #pragma unroll
-            for (int a = 0; a < 3; a++) grads.scales[3 * i + a] += gsc[a];
+            for (int a = 0; a < 3; a++) grads.scales[3 * i + a] = os[a] + gsc[a];
         }
-        if (grads.quats) {
-            float4* gqp = reinterpret_cast<float4*>(grads.quats) + i;
-            float4 o4 = *gqp;
+        if (gqp) {
             o4.x += (gq[0] - qn[0] * dq) * iq; o4.y += (gq[1] - qn[1] * dq) * iq;
             o4.z += (gq[2] - qn[2] * dq) * iq; o4.w += (gq[3] - qn[3] * dq) * iq;
             *gqp = o4;
         }
-        if (grads.opacities) grads.opacities[i] += gop;
+        if (grads.opacities) grads.opacities[i] = oo + gop;
     }
     __syncthreads();
     if (!POSE_ONLY && grads.sh) {
