@@ -717,7 +717,10 @@ TRAFFIC_PER_UNIT = {"blend_bwd": (41.87, 5)}
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # T lane-ops/s
+    alu_src = f"152 SMs x 128 FP32 lanes x max SM clock ({sm_mhz:.0f} MHz)"
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = ("fallback 6800 GB/s (of fallback)" if peaks.get("_fallback")
+               else "MEASURED_PEAKS.json hbm_gbs (of measured)")
     t = per_launch_ms * 1e-3
     lps = max(1, launches_per_step)
     ncoef = 3 * (sh_degree + 1) ** 2
@@ -725,14 +728,14 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
         ops = (OPS_FWD_EVAL * counters[0] + OPS_FWD_BLEND * counters[1]) / lps
         a = ops / t / 1e12
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+                "frac": a / alu_peak, "traffic": None, "peak_source": alu_src}
     if kname == "blend_bwd":
         ops = (OPS_BWD_EVAL * counters[2] + OPS_BWD_GRAD * counters[3]) / lps
         a = ops / t / 1e12
         tr = TRAFFIC_PER_UNIT.get("blend_bwd")
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
                 "frac": a / alu_peak, "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None,
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (2070 MHz)"}
+                "peak_source": alu_src}
     if kname == "preprocess_fwd":
         by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 60) / lps
     elif kname == "preprocess_bwd":
@@ -745,7 +748,7 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
         by = 0.0
     a = by / t / 1e9
     return {"kernel": kname, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+            "traffic": None, "peak_source": hbm_src}
 
 
 if __name__ == "__main__":
