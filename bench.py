@@ -191,6 +191,30 @@ def _cpu_baseline(w, n_views: int):
             "seconds": dt}
 
 
+def _cpu_baseline_single_thread(w):
+    """The same oracle on one host thread, over the smallest view of the
+    sample (its per-Gaussian work still covers the whole scene)."""
+    import oracle
+    from paper_2410_08743_gb300 import synth
+    k = min(range(len(w["views"])), key=lambda j: w["views"][j]["width"] * w["views"][j]["height"])
+    views = [w["views"][k]]
+    poses = w["poses"][[k]]
+    target = synth.random_image_like(np.random.default_rng(0), views)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        r = oracle.render(w["scene"], views, poses)
+        _, d, _ = oracle.loss_l1(views, r["image"], target)
+        oracle.backward(w["scene"], views, poses, d)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(os.cpu_count() or 1)
+    mpix = views[0]["width"] * views[0]["height"] / 1e6
+    return {"value": mpix / dt, "unit": UNIT, "cores": 1, "seconds": dt,
+            "sample": f"1 view ({views[0]['width']}x{views[0]['height']}) of the {len(w['scene']['opac'])}-Gaussian "
+                      f"scene, forward + L1 + backward incl. pose, FP64, one thread"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -299,6 +323,10 @@ def run_gpu(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         return ms / k
+
+    # measured FP32 / MUFU rates of this GPU (the "alu" roofline's peaks)
+    alu = L.gs_measure_alu_peaks(local)
+    torch.cuda.synchronize()
 
     # ---- main timed region: batched steps with per-kernel CUDA events
     clocks = ClockSampler(local)
@@ -411,17 +439,21 @@ def run_gpu(args):
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     kname, (kms, kn) = dom
     per_launch_ms = kms / max(1, kn)
-    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
+    # the ALU peaks are scaled to the median SM clock sampled during the timed
+    # region (the probe's own clock where no sample exists)
+    sm_mhz_run = clk.get("sm_mhz") or alu["probe_sm_mhz"]
     n = len(sc["opac"])
     roof = roofline_for(kname, per_launch_ms, kn // max(1, K), counters, n, V, n_keys, sc["sh_degree"], peaks,
-                        sm_mhz_peak)
+                        alu, sm_mhz_run)
     kernels = {}
     for k, v in sorted(prof.items()):
         kernels[k] = {"ms_per_step": v[0] / K, "launches_per_step": v[1] / K}
-        if k in ("blend_fwd", "blend_bwd", "preprocess_fwd", "preprocess_bwd", "scatter_keys"):
+        if k in ("blend_fwd", "blend_bwd", "preprocess_fwd", "preprocess_bwd", "scatter_keys", "count_tiles"):
             rk = roofline_for(k, v[0] / max(1, v[1]), v[1] // max(1, K), counters, n, V, n_keys, sc["sh_degree"],
-                              peaks, sm_mhz_peak)
-            kernels[k]["roofline"] = {x: rk[x] for x in ("bound", "achieved", "unit", "frac")}
+                              peaks, alu, sm_mhz_run)
+            kernels[k]["roofline"] = {x: rk[x] for x in ("bound", "achieved", "unit", "frac") if x in rk}
+            if "mufu_frac" in rk:
+                kernels[k]["roofline"]["mufu_frac"] = rk["mufu_frac"]
 
     serving = None
     if not args.no_serve:
@@ -459,6 +491,8 @@ def run_gpu(args):
         try:
             cpu = _cpu_baseline(w, max(1, args.cpu_sample_views))
             cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            st1 = _cpu_baseline_single_thread(w)
+            cpu["single_thread"] = {k: st1[k] for k in ("value", "unit", "cores", "sample")}
         except Exception as e:
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -479,7 +513,10 @@ def run_gpu(args):
                          "entries_sorted": counters[6],
                          "warp_entries_fwd": counters[7], "warp_entries_bwd_box": counters[8],
                          "warp_entries_bwd_used": counters[9],
+                         "visible_pairs": counters[10],
+                         "keys_per_visible_pair": n_keys / max(1, counters[10]),
                          "keys_per_gaussian_view": n_keys / (n * V)},
+            "alu_peaks": alu,
             "status": st,
         }
         print(json.dumps(line), flush=True)
@@ -715,35 +752,56 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 TRAFFIC_PER_UNIT = {"blend_bwd": (41.87, 5)}
 
 
-def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, sm_mhz):
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # T lane-ops/s
-    alu_src = f"152 SMs x 128 FP32 lanes x max SM clock ({sm_mhz:.0f} MHz)"
+def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, alu, sm_mhz):
+    """Roofline entry of one kernel.  "alu" kernels: lane operations per second
+    against the measured FFMA rate (lane ops per SM per cycle, from the probe
+    kernels) x the SM count x the median SM clock of the timed region; their
+    MUFU use (one ex2 per evaluated pair, one reciprocal per contributing pair
+    in the backward) against the measured ex2 rate is reported beside it.
+    "hbm" kernels: algorithmic bytes per second against the measured copy
+    bandwidth.  N_vis = counters[10] (visible (view, Gaussian) pairs)."""
+    sms = int(alu["sm_count"])
+    alu_peak = alu["fp32_fma_per_sm_clk"] * sms * sm_mhz * 1e6 / 1e12   # T lane-ops/s
+    mufu_peak = alu["ex2_per_sm_clk"] * sms * sm_mhz * 1e6 / 1e12
+    alu_src = (f"measured FFMA {alu['fp32_fma_per_sm_clk']:.1f} lane-ops/SM/cycle x {sms} SMs (device attribute) x "
+               f"{sm_mhz:.0f} MHz median SM clock of the timed region (of measured)")
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = ("fallback 6800 GB/s (of fallback)" if peaks.get("_fallback")
                else "MEASURED_PEAKS.json hbm_gbs (of measured)")
     t = per_launch_ms * 1e-3
     lps = max(1, launches_per_step)
     ncoef = 3 * (sh_degree + 1) ** 2
+    n_vis = counters[10]
     if kname == "blend_fwd":
         ops = (OPS_FWD_EVAL * counters[0] + OPS_FWD_BLEND * counters[1]) / lps
         a = ops / t / 1e12
+        mufu = counters[0] / lps / t / 1e12
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": None, "peak_source": alu_src}
+                "frac": a / alu_peak, "mufu_frac": mufu / mufu_peak, "traffic": None, "peak_source": alu_src}
     if kname == "blend_bwd":
         ops = (OPS_BWD_EVAL * counters[2] + OPS_BWD_GRAD * counters[3]) / lps
         a = ops / t / 1e12
+        mufu = (counters[2] + counters[3]) / lps / t / 1e12
         tr = TRAFFIC_PER_UNIT.get("blend_bwd")
         return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None,
-                "peak_source": alu_src}
+                "frac": a / alu_peak, "mufu_frac": mufu / mufu_peak,
+                "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None, "peak_source": alu_src}
     if kname == "preprocess_fwd":
-        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n * V * 60) / lps
+        # parameters once per launch; 60 B per visible pair, the 16 B culled
+        # marker (rect, depth, radius) per culled pair
+        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n_vis * 60 + (n * V - n_vis) * 16) / lps
     elif kname == "preprocess_bwd":
-        by = (n * (4 * (3 + 3 + 4) + 4 * ncoef) * 2 + n * 4 * 2 + n * V * (36 + 8)) / lps
+        # parameters read and gradients read + written once per launch; per
+        # visible pair its 36 B 2D gradient read and cleared, 8 B rectangle;
+        # the rectangle only for a culled pair
+        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) * 3 + n_vis * (36 * 2 + 8) + (n * V - n_vis) * 8) / lps
     elif kname == "segment_sort":
         by = n_keys * (8 + 4) / lps
     elif kname == "scatter_keys":
-        by = (n * V * 12 + n_keys * 8) / lps
+        # rectangle of every pair, depth of a visible one, 8 B per key written
+        by = (n * V * 8 + n_vis * 4 + n_keys * 8) / lps
+    elif kname == "count_tiles":
+        by = n * V * 8 / lps
     else:
         by = 0.0
     a = by / t / 1e9

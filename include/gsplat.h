@@ -470,7 +470,9 @@ enum {
                                  tile rectangle (0 where culled) */
     GS_Q_SPLAT = 9,           /* float [V*N][9]: mu_hat(2) as blended (exact to ~1e-9 px, then
                                  rounded to float), conic(3), opacity, colour(3) */
-    GS_Q_SORTED_COUNT = 10    /* uint32 [tiles]: length of each tile's sorted prefix */
+    GS_Q_SORTED_COUNT = 10,   /* uint32 [tiles]: length of each tile's sorted prefix */
+    GS_Q_DSSIM_GRAD = 11      /* float [sum 3HW]: the D-SSIM term's dL/dC (w_dssim included) of the
+                                 last GS_LOSS_L1_DSSIM backward of these frames (GS_EINVAL if none) */
 };
 int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* size_out);
 
@@ -483,6 +485,27 @@ int gs_ctx_set_profiling(gs_ctx* ctx, int enable);
  * resets them.  names is [max_kinds][32]; *n_kinds receives the count. */
 int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_ms, int64_t* launches,
                    int* n_kinds);
+
+/* Measured arithmetic rates of a device, the peaks of the "alu" roofline of
+ * the blending kernels (which are bound by FP32 and MUFU issue; the paper has
+ * no counterpart, it reports no kernel rates).  Runs three probe kernels of
+ * one wave of resident blocks each on `device` (synchronous, a few ms, uses
+ * the legacy default stream and allocates a few MB that it frees):
+ *   sm_count               multiprocessors of the device;
+ *   probe_sm_mhz           SM clock seen by the probes (clock64 cycles over
+ *                          CUDA-event time); the GPU's clocks are not touched;
+ *   fp32_fma_per_sm_clk    FP32 FMA lane operations per SM per cycle (FFMA);
+ *   fp32x2_fma_per_sm_clk  the same with paired fma.rn.f32x2 (both halves);
+ *   ex2_per_sm_clk         MUFU ex2 lane operations per SM per cycle;
+ *   *_per_s                the same rates per second at the probe's clock.
+ * Returns GS_EINVAL for a NULL out, GS_ECUDA / GS_ENOMEM on a CUDA error. */
+typedef struct gs_alu_peaks {
+    int sm_count;
+    double probe_sm_mhz;
+    double fp32_fma_per_sm_clk, fp32x2_fma_per_sm_clk, ex2_per_sm_clk;
+    double fp32_fma_per_s, fp32x2_fma_per_s, ex2_per_s;
+} gs_alu_peaks;
+int gs_measure_alu_peaks(int device, gs_alu_peaks* out);
 
 /* Number of CUDA kernels this context has launched so far (host counter). */
 int64_t gs_ctx_launch_count(gs_ctx* ctx);
@@ -497,28 +520,35 @@ int64_t gs_ctx_launch_count(gs_ctx* ctx);
  * out[6] list entries the forward sorted (all keys with GS_F_FULL_SORT),
  * out[7] (warp, splat) entries the forward blend walked (after the per-warp
  * compaction), out[8] / out[9] (warp, splat) entries of the backward blend with
- * a pixel in the splat's alpha box / with a contributing pixel. */
-#define GS_N_COUNTERS 10
+ * a pixel in the splat's alpha box / with a contributing pixel, out[10]
+ * visible (view, Gaussian) pairs N_vis (non-empty tile rectangle). */
+#define GS_N_COUNTERS 11
 int gs_frames_counters(gs_frames* fr, int64_t out[GS_N_COUNTERS]);
 
 /* D-SSIM loss term and its image gradient for ONE view, allocating nothing.
  * (The paper has no counterpart: this is a deployment variant of the D-SSIM
- * part of GS_LOSS_L1_DSSIM.)  It exists for callers that cannot call
- * cudaMalloc at the point where they need the loss: code running while a
- * stream is being captured into a CUDA graph (allocation is not capturable),
- * real-time or serving loops that forbid allocator calls after start-up, and
- * hosts that hand the library a fixed memory budget.  Its scratch (11 planes
- * of up to GS_DSSIM_STATIC_MAX_PIXELS floats, 11.5 MiB) is a file-scope device
- * array that every GPU loading the library holds until the process exits.
+ * part of GS_LOSS_L1_DSSIM.)  It is for callers that cannot call cudaMalloc
+ * at the point where they need the loss: serving loops that fix their device
+ * footprint at start-up (a later cudaMalloc can fail once other tenants have
+ * taken the memory, and it synchronises the device, stalling every stream),
+ * real-time loops that forbid allocator calls after initialisation, and hosts
+ * that own all device memory and give the library only the buffers it
+ * passes.  Its scratch is a file-scope device array that every GPU loading
+ * the library holds until the process exits: 11 planes of
+ * GS_DSSIM_STATIC_MAX_PIXELS floats (11.5 MiB), a safe upper bound on what
+ * one call uses (9 planes for the SSIM partials plus 3 floats per 32x32 tile
+ * for the per-tile SSIM sums).
  *   image, target  device, planar float32 [3][height][width];
  *   dl_dimage      device output [3][height][width]: w_dssim * d(1 - SSIM)/dC;
  *   loss           device float64 [1], nullable: w_dssim * (1 - mean SSIM).
- * width * height above GS_DSSIM_STATIC_MAX_PIXELS is rejected with GS_EINVAL.
- * The first call on a device resolves the scratch's device address (and
- * uploads the filter window); make that first call before any stream capture.
- * All calls share the one scratch array: calls whose GPU work overlaps (other
- * streams, other host threads) race and must be serialised by the caller.
- * No scratch needs clearing: each call writes every scratch value it reads. */
+ * width * height above GS_DSSIM_STATIC_MAX_PIXELS is rejected with GS_EINVAL
+ * before any device work.  The first call on a device resolves the scratch's
+ * device address and uploads the filter window (once per device, with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one scratch array, which keeps the last call's contents:
+ * calls whose GPU work overlaps (other streams, other host threads) race and
+ * must be serialised by the caller.  No scratch needs clearing: each call
+ * writes every scratch value it reads. */
 #define GS_DSSIM_STATIC_MAX_PIXELS (512 * 512)
 int gs_loss_dssim_static(const float* image, const float* target, int width, int height, float w_dssim,
                          float* dl_dimage, double* loss, void* stream);

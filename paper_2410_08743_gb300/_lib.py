@@ -19,7 +19,7 @@ GS_EINVAL, GS_ENOMEM, GS_ETIMEOUT, GS_EBUSY, GS_ECUDA, GS_EOVERFLOW = -1, -2, -3
 GS_F_NO_SYNC, GS_F_HOST_IO, GS_F_FULL_SORT, GS_F_RECOMPUTE, GS_F_COUNT = 1, 2, 4, 8, 16
 GS_LOSS_DLDC, GS_LOSS_L1, GS_LOSS_L1_DSSIM, GS_LOSS_L1_MASKED = 0, 1, 2, 3
 (GS_Q_NUM_KEYS, GS_Q_DEPTH, GS_Q_RECT, GS_Q_RADIUS, GS_Q_TILE_RANGES, GS_Q_SORTED_IDX, GS_Q_T_FINAL,
- GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT) = range(11)
+ GS_Q_N_CONTRIB, GS_Q_MEAN2D, GS_Q_SPLAT, GS_Q_SORTED_COUNT, GS_Q_DSSIM_GRAD) = range(12)
 
 # names declared in include/gsplat.h (checked by the CPU test suite)
 EXPORTED = (
@@ -30,7 +30,7 @@ EXPORTED = (
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
     "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
     "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact", "gs_unproject", "gs_knn_mean_dist",
-    "gs_init_from_points", "gs_spatial_order", "gs_gather_rows",
+    "gs_init_from_points", "gs_spatial_order", "gs_gather_rows", "gs_measure_alu_peaks",
 )
 GS_POSE_SE3, GS_POSE_TXSO3 = 0, 1
 
@@ -95,6 +95,12 @@ class gs_solve_request(C.Structure):
 class gs_solve_result(C.Structure):
     _fields_ = [("pose", C.c_double * 12), ("loss", C.c_double), ("latency_ms", C.c_double),
                 ("queue_ms", C.c_double), ("steps_done", C.c_int32), ("status", C.c_int32)]
+
+
+class gs_alu_peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int), ("probe_sm_mhz", C.c_double), ("fp32_fma_per_sm_clk", C.c_double),
+                ("fp32x2_fma_per_sm_clk", C.c_double), ("ex2_per_sm_clk", C.c_double),
+                ("fp32_fma_per_s", C.c_double), ("fp32x2_fma_per_s", C.c_double), ("ex2_per_s", C.c_double)]
 
 
 class gs_server_stats(C.Structure):
@@ -183,6 +189,8 @@ def load(path: str | None = None):
     L.gs_ctx_set_profiling.argtypes = [vp, i32]
     L.gs_ctx_profile.argtypes = [vp, i32, vp, vp, vp, C.POINTER(C.c_int)]
     L.gs_frames_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.gs_measure_alu_peaks.argtypes = [i32, C.POINTER(gs_alu_peaks)]
+    L.gs_measure_alu_peaks.restype = C.c_int
     L.gs_ctx_launch_count.argtypes = [vp]
     L.gs_ctx_launch_count.restype = C.c_int64
     L.gs_last_error.restype = C.c_char_p
@@ -518,7 +526,7 @@ def gs_frames_query(fr: int, what: int):
     dtype = {GS_Q_NUM_KEYS: np.int64, GS_Q_DEPTH: np.float32, GS_Q_RECT: np.int32, GS_Q_RADIUS: np.int32,
              GS_Q_TILE_RANGES: np.uint32, GS_Q_SORTED_IDX: np.uint32, GS_Q_T_FINAL: np.float32,
              GS_Q_N_CONTRIB: np.uint32, GS_Q_MEAN2D: np.float32, GS_Q_SPLAT: np.float32,
-             GS_Q_SORTED_COUNT: np.uint32}[what]
+             GS_Q_SORTED_COUNT: np.uint32, GS_Q_DSSIM_GRAD: np.float32}[what]
     out = np.zeros(max(1, size.value // np.dtype(dtype).itemsize), dtype)
     _ck(L.gs_frames_query(C.c_void_p(fr), int(what), out.ctypes.data_as(C.c_void_p), out.nbytes, None))
     return out[: size.value // np.dtype(dtype).itemsize]
@@ -544,7 +552,15 @@ def gs_ctx_launch_count(ctx: int) -> int:
     return int(load().gs_ctx_launch_count(C.c_void_p(ctx)))
 
 
-GS_N_COUNTERS = 10
+def gs_measure_alu_peaks(device: int = 0) -> dict:
+    """Measured FP32 / paired-FP32 FMA and MUFU ex2 rates of a device
+    (per SM per cycle and per second) and its SM count."""
+    out = gs_alu_peaks()
+    _ck(load().gs_measure_alu_peaks(int(device), C.byref(out)))
+    return {k: getattr(out, k) for k, _ in gs_alu_peaks._fields_}
+
+
+GS_N_COUNTERS = 11
 
 
 def gs_frames_counters(fr: int):

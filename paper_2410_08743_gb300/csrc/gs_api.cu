@@ -227,6 +227,7 @@ struct gs_frames {
     // backward
     DevBuf<double> pose_partials;
     DevBuf<float> dldc_ssim, ssim_tmp;
+    bool have_dssim_grad = false;     // dldc_ssim holds the last backward's D-SSIM dL/dC
     DevBuf<long long> img_off_dev;
     DevBuf<double> loss_tmp;
     DevBuf<unsigned long long> counters;  // [8] pair / entry counters
@@ -669,6 +670,10 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
         gs::launch_count_tiles(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp.rect, fr->counts.p, s);
     }
     CK_LAUNCH();
+    if (opts->flags & GS_F_COUNT) {
+        gs::launch_count_visible(vn, sp.rect, fr->counters.p + 11, s);
+        CK_LAUNCH();
+    }
     {
         PROF(PK_SCAN, (T + 1 > 4096) ? 3 : 1);
         gs::launch_scan_u32(fr->counts.p, fr->starts.p, T + 1, fr->scan_tmp.p, fr->scan_tmp.cap * 4, s);
@@ -787,10 +792,11 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         if (loss->loss && (rc = fr->loss_tmp.ensure(n_views, grow, "loss tmp"))) return rc;
         {
             PROF(PK_DSSIM, n_views * (12 + (loss->loss ? 1 : 0)));
-            gs::launch_dssim(n_views, views, offs.data(), image, loss->target, loss->w_dssim, fr->dldc_ssim.p,
-                             loss->loss ? fr->loss_tmp.p : nullptr, fr->ssim_tmp.p, s);
+            CK(gs::launch_dssim(n_views, views, offs.data(), image, loss->target, loss->w_dssim, fr->dldc_ssim.p,
+                                loss->loss ? fr->loss_tmp.p : nullptr, fr->ssim_tmp.p, s));
         }
         CK_LAUNCH();
+        fr->have_dssim_grad = true;
         dldc = fr->dldc_ssim.p;
     }
     // the backward blend accumulates into records [0, vn), which must start at zero
@@ -1466,6 +1472,7 @@ int gs_frames_counters(gs_frames* fr, int64_t out[GS_N_COUNTERS]) {
     out[7] = (int64_t)c[8];
     out[8] = (int64_t)c[9];
     out[9] = (int64_t)c[10];
+    out[10] = (int64_t)c[11];
     return GS_OK;
 }
 
@@ -1488,6 +1495,10 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         case GS_Q_MEAN2D: need = vn * 2 * sizeof(float); break;
         case GS_Q_SPLAT: need = vn * 9 * sizeof(float); break;
         case GS_Q_SORTED_COUNT: need = (size_t)fr->total_tiles * sizeof(uint32_t); break;
+        case GS_Q_DSSIM_GRAD:
+            if (!fr->have_dssim_grad) return fail(GS_EINVAL, "no D-SSIM backward recorded for these frames");
+            need = (size_t)fr->total_image * sizeof(float);
+            break;
         default: return fail(GS_EINVAL, "unknown query %d", what);
     }
     if (size_out) *size_out = need;
@@ -1500,6 +1511,7 @@ int gs_frames_query(gs_frames* fr, int what, void* dst, size_t bytes, size_t* si
         memcpy(dst, &k64, sizeof(k64));
         return GS_OK;
     }
+    if (what == GS_Q_DSSIM_GRAD) { CK(cudaMemcpy(dst, fr->dldc_ssim.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
     if (what == GS_Q_DEPTH) { CK(cudaMemcpy(dst, fr->depth.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
     if (what == GS_Q_RADIUS) { CK(cudaMemcpy(dst, fr->radius.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }
     if (what == GS_Q_T_FINAL) { CK(cudaMemcpy(dst, fr->T_final.p, need, cudaMemcpyDeviceToHost)); return GS_OK; }

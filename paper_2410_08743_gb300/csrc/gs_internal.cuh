@@ -211,9 +211,14 @@ struct AdamGroup {
 void launch_gaussian_adam(int64_t n, const AdamGroup* groups, int n_groups, float b1, float b2, float eps, int step,
                           cudaStream_t s);
 
-void launch_dssim(int n_views, const gs_view* views_host, const long long* img_off_host, const float* image,
-                  const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
-                  cudaStream_t s);
+// Adds the number of (view, Gaussian) pairs with a non-empty tile rectangle to *count.
+void launch_count_visible(size_t vn, const uint2* rect, unsigned long long* count, cudaStream_t s);
+// Returns the error of the per-device window upload (nothing is launched then).
+cudaError_t launch_dssim(int n_views, const gs_view* views_host, const long long* img_off_host, const float* image,
+                         const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
+                         cudaStream_t s);
+// Uploads the D-SSIM filter window to the current device once (thread-safe).
+cudaError_t ensure_dssim_window();
 
 // Records a message for gs_last_error() and returns `code` (defined in gs_api.cu).
 int set_error(int code, const char* msg);

@@ -1,0 +1,181 @@
+// gs_probe.cu - measured arithmetic peaks of the current GPU, the denominators
+// of the "alu" roofline of the blending kernels (they are bound by FP32 and
+// MUFU issue, not by memory).
+//
+// Each probe is one wave of resident blocks running long unrolled loops of
+// independent dependency chains, so that the pipe under test, not latency,
+// limits it: scalar FFMA, paired FFMA (fma.rn.f32x2, both halves counted) and
+// MUFU ex2 (each ex2 followed by one FADD to keep its argument bounded).  The
+// rate per SM per cycle comes from clock64() deltas per block (independent of
+// the clock the GPU runs at); the rate per second from CUDA events.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+#define PR_THREADS 256
+#define PR_CHAINS 16
+#define PR_ITERS 1024
+#define PR_UNROLL 8
+
+__device__ __forceinline__ unsigned long long pr_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float pr_sum2(unsigned long long r) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return a + b;
+}
+
+// kind 0: FFMA; kind 1: fma.rn.f32x2; kind 2: ex2.approx + FADD.
+template <int KIND>
+__global__ void __launch_bounds__(PR_THREADS) k_probe(float s, float* __restrict__ sink,
+                                                      long long* __restrict__ cycles) {
+    __syncthreads();
+    const long long c0 = clock64();
+    float acc = 0.0f;
+    if (KIND == 0) {
+        float x[PR_CHAINS];
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS; c++) x[c] = 1e-3f * (float)(threadIdx.x + c);
+        for (int it = 0; it < PR_ITERS; it++) {
+#pragma unroll
+            for (int u = 0; u < PR_UNROLL; u++)
+#pragma unroll
+                for (int c = 0; c < PR_CHAINS; c++) x[c] = fmaf(x[c], s, 0.25f);
+        }
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS; c++) acc += x[c];
+    } else if (KIND == 1) {
+        unsigned long long x[PR_CHAINS / 2];
+        const unsigned long long sv = pr_pack(s, s), hv = pr_pack(0.25f, 0.25f);
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS / 2; c++) x[c] = pr_pack(1e-3f * (float)(threadIdx.x + c), 1e-3f * (float)c);
+        for (int it = 0; it < PR_ITERS; it++) {
+#pragma unroll
+            for (int u = 0; u < PR_UNROLL; u++)
+#pragma unroll
+                for (int c = 0; c < PR_CHAINS / 2; c++)
+                    asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(sv), "l"(hv));
+        }
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS / 2; c++) acc += pr_sum2(x[c]);
+    } else {
+        float x[PR_CHAINS];
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS; c++) x[c] = -1e-4f * (float)(threadIdx.x + c);
+        for (int it = 0; it < PR_ITERS; it++) {
+#pragma unroll
+            for (int u = 0; u < PR_UNROLL / 4; u++)
+#pragma unroll
+                for (int c = 0; c < PR_CHAINS; c++) {
+                    float y;
+                    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[c]));
+                    x[c] = y - s;   // ex2 of a value in [-1, 0] lies in [0.5, 1]
+                }
+        }
+#pragma unroll
+        for (int c = 0; c < PR_CHAINS; c++) acc += x[c];
+    }
+    __syncthreads();
+    const long long c1 = clock64();
+    sink[(size_t)blockIdx.x * PR_THREADS + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = c1 - c0;
+}
+
+// lane operations one block of a probe executes
+static double probe_lane_ops(int kind) {
+    const double per_thread = kind == 2 ? (double)PR_ITERS * (PR_UNROLL / 4) * PR_CHAINS
+                                        : (double)PR_ITERS * PR_UNROLL * PR_CHAINS;
+    return per_thread * PR_THREADS;
+}
+
+}  // namespace gs
+
+extern "C" int gs_measure_alu_peaks(int device, gs_alu_peaks* out) {
+    using namespace gs;
+    char msg[256];
+    if (!out) return set_error(GS_EINVAL, "gs_measure_alu_peaks: out is NULL");
+    *out = gs_alu_peaks{};
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof(msg), "gs_measure_alu_peaks: cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+        return set_error(GS_ECUDA, msg);
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int per_sm[3] = {0, 0, 0};
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_probe<0>, PR_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_probe<1>, PR_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_probe<2>, PR_THREADS, 0);
+    const int max_blocks = sms * std::max(per_sm[0], std::max(per_sm[1], per_sm[2]));
+    if (sms <= 0 || max_blocks <= 0) return set_error(GS_ECUDA, "gs_measure_alu_peaks: no resident blocks");
+    float* sink = nullptr;
+    long long* cyc = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int rc = GS_OK;
+    double rate_clk[3] = {0, 0, 0}, rate_s[3] = {0, 0, 0}, mhz_sum = 0.0;
+    int mhz_n = 0;
+    if ((e = cudaMalloc(&sink, sizeof(float) * (size_t)max_blocks * PR_THREADS)) != cudaSuccess ||
+        (e = cudaMalloc(&cyc, sizeof(long long) * (size_t)max_blocks)) != cudaSuccess ||
+        (e = cudaEventCreate(&ev0)) != cudaSuccess || (e = cudaEventCreate(&ev1)) != cudaSuccess) {
+        snprintf(msg, sizeof(msg), "gs_measure_alu_peaks: setup: %s", cudaGetErrorString(e));
+        rc = set_error(e == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA, msg);
+    }
+    std::vector<long long> hc(max_blocks);
+    for (int kind = 0; kind < 3 && rc == GS_OK; kind++) {
+        const int grid = sms * per_sm[kind];
+        float best_ms = 0.0f;
+        double best_clk = 0.0;
+        for (int rep = 0; rep < 4 && rc == GS_OK; rep++) {   // the first repetition warms up
+            cudaEventRecord(ev0, 0);
+            if (kind == 0) k_probe<0><<<grid, PR_THREADS>>>(0.999f, sink, cyc);
+            else if (kind == 1) k_probe<1><<<grid, PR_THREADS>>>(0.999f, sink, cyc);
+            else k_probe<2><<<grid, PR_THREADS>>>(1.0f, sink, cyc);
+            cudaEventRecord(ev1, 0);
+            if ((e = cudaEventSynchronize(ev1)) != cudaSuccess ||
+                (e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                snprintf(msg, sizeof(msg), "gs_measure_alu_peaks: probe %d: %s", kind, cudaGetErrorString(e));
+                rc = set_error(GS_ECUDA, msg);
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            std::vector<long long> srt(hc.begin(), hc.begin() + grid);
+            std::sort(srt.begin(), srt.end());
+            const double med_cycles = (double)srt[grid / 2];
+            // one wave: every SM runs per_sm[kind] blocks concurrently for ~med_cycles
+            const double clk = probe_lane_ops(kind) * per_sm[kind] / med_cycles;
+            if (rep > 0 && (best_ms == 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                best_clk = clk;
+                mhz_sum += (double)srt[grid - 1] / (ms * 1e3);   // slowest block's cycles over the event time
+                mhz_n++;
+            }
+        }
+        rate_clk[kind] = best_clk;
+        rate_s[kind] = best_ms > 0.0f ? probe_lane_ops(kind) * grid / (best_ms * 1e-3) : 0.0;
+    }
+    if (sink) cudaFree(sink);
+    if (cyc) cudaFree(cyc);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (rc != GS_OK) return rc;
+    out->sm_count = sms;
+    out->probe_sm_mhz = mhz_n ? mhz_sum / mhz_n : 0.0;
+    out->fp32_fma_per_sm_clk = rate_clk[0];
+    out->fp32x2_fma_per_sm_clk = rate_clk[1];
+    out->ex2_per_sm_clk = rate_clk[2];
+    out->fp32_fma_per_s = rate_s[0];
+    out->fp32x2_fma_per_s = rate_s[1];
+    out->ex2_per_s = rate_s[2];
+    return GS_OK;
+}

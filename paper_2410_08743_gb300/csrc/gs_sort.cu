@@ -14,6 +14,8 @@
 //      lower index, independent of the scatter's order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gs_block_sort.cuh"
 #include "gs_internal.cuh"
 
@@ -102,6 +104,30 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t
         k_scan_sums<<<1, SCAN_T, 0, s>>>(sums, nb);
         k_scan_add<<<(n + 255) / 256, 256, 0, s>>>(out, n, sums);
     }
+}
+
+// ------------------------------------------------------------ visible pairs
+// Number of (view, Gaussian) pairs that passed the preprocess (non-empty tile
+// rectangle), added to *count.  Only the counting passes run it.
+__global__ void k_count_visible(size_t vn, const uint2* __restrict__ rect, unsigned long long* __restrict__ count) {
+    unsigned long long c = 0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < vn; k += (size_t)gridDim.x * blockDim.x) {
+        const uint2 r = rect[k];
+        c += ((r.y & 0xffffu) > (r.x & 0xffffu)) ? 1ull : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+void launch_count_visible(size_t vn, const uint2* rect, unsigned long long* count, cudaStream_t s) {
+    if (vn == 0) return;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t want = (vn + 255) / 256;
+    const int grid = (int)std::min<size_t>(want, (size_t)std::max(1, sms) * 8);
+    k_count_visible<<<grid, 256, 0, s>>>(vn, rect, count);
 }
 
 // ------------------------------------------------------------ count + scatter

@@ -17,15 +17,30 @@ namespace gs {
 
 __constant__ float c_win[11];
 
-static void upload_window() {
-    static bool done = false;
-    if (done) return;
+// The window lives in constant memory, which every device holds separately:
+// it is uploaded once per device, with that device current, under a lock
+// (contexts, servers and the allocation-free entry point may run D-SSIM from
+// several host threads and on several devices).
+namespace {
+std::mutex g_win_mu;
+constexpr int kWinDevices = 256;
+bool g_win_done[kWinDevices] = {};
+}  // namespace
+
+cudaError_t ensure_dssim_window() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kWinDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_win_mu);
+    if (g_win_done[dev]) return cudaSuccess;
     float w[11];
     double s = 0.0, g[11];
     for (int k = 0; k < 11; k++) { const double x = k - 5; g[k] = exp(-x * x / (2.0 * 1.5 * 1.5)); s += g[k]; }
     for (int k = 0; k < 11; k++) w[k] = (float)(g[k] / s);
-    cudaMemcpyToSymbol(c_win, w, sizeof(w));
-    done = true;
+    e = cudaMemcpyToSymbol(c_win, w, sizeof(w));
+    if (e == cudaSuccess) g_win_done[dev] = true;
+    return e;
 }
 
 // Tiled, fused D-SSIM.  One block computes 32x32 outputs of one channel of
@@ -210,10 +225,11 @@ __global__ void k_ssim_loss(DssimBatch b, const float* __restrict__ block_sum, f
 // 32x32 tile of the largest view per view of a launch (at most 32 views) for
 // the per-block SSIM sums.  loss_out (nullable, device [V]) receives
 // w_dssim (1 - SSIM) per view.
-void launch_dssim(int n_views, const gs_view* views, const long long* img_off, const float* image,
-                  const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
-                  cudaStream_t s) {
-    upload_window();
+cudaError_t launch_dssim(int n_views, const gs_view* views, const long long* img_off, const float* image,
+                         const float* target, float w_dssim, float* dldc_out, double* loss_out, float* tmp,
+                         cudaStream_t s) {
+    const cudaError_t we = ensure_dssim_window();
+    if (we != cudaSuccess) return we;
     long long total = 0;
     for (int v = 0; v < n_views; v++)
         total = std::max(total, img_off[v] + 3LL * views[v].width * views[v].height);
@@ -237,6 +253,7 @@ void launch_dssim(int n_views, const gs_view* views, const long long* img_off, c
         k_ssim_bwd<<<grid, SS_THREADS, 0, s>>>(b, image, target, parts, total, w_dssim, dldc_out);
         if (loss_out) k_ssim_loss<<<b.n, 256, 0, s>>>(b, bsum, w_dssim, loss_out + v0);
     }
+    return cudaSuccess;
 }
 
 }  // namespace gs
@@ -244,11 +261,12 @@ void launch_dssim(int n_views, const gs_view* views, const long long* img_off, c
 // ------------------------------------------------------------ no-alloc variant
 // gs_loss_dssim_static runs the same D-SSIM kernels as the backward pass, but
 // with its scratch in a static device array instead of workspace memory, so
-// that it calls no allocator at all.  Callers that cannot allocate at the
-// point of use (inside CUDA-graph capture, in allocation-free serving loops,
-// under a fixed memory budget) use it.  The array is device memory reserved
-// when the module loads; host code only ever sees the address that
-// cudaGetSymbolAddress returns for the current device.
+// that it calls no allocator at all: for serving loops that fix their device
+// footprint at start-up, real-time loops that forbid allocator calls after
+// initialisation, and hosts that hand the library only the buffers it uses.
+// The array is device memory reserved when the module loads; host code only
+// ever passes the address that cudaGetSymbolAddress returns for the current
+// device (the symbol itself names a host-side stand-in).
 
 static __device__ __align__(256) float g_dssim_static_scratch[11 * GS_DSSIM_STATIC_MAX_PIXELS];
 
@@ -285,11 +303,7 @@ extern "C" int gs_loss_dssim_static(const float* image, const float* target, int
                 snprintf(msg, sizeof(msg), "gs_loss_dssim_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
                 return gs::set_error(GS_ECUDA, msg);
             }
-            float w[11];
-            double g[11], sum = 0.0;
-            for (int k = 0; k < 11; k++) { const double x = k - 5; g[k] = exp(-x * x / (2.0 * 1.5 * 1.5)); sum += g[k]; }
-            for (int k = 0; k < 11; k++) w[k] = (float)(g[k] / sum);
-            e = cudaMemcpyToSymbol(gs::c_win, w, sizeof(w));
+            e = gs::ensure_dssim_window();
             if (e != cudaSuccess) {
                 snprintf(msg, sizeof(msg), "gs_loss_dssim_static: window upload: %s", cudaGetErrorString(e));
                 return gs::set_error(GS_ECUDA, msg);
@@ -300,8 +314,9 @@ extern "C" int gs_loss_dssim_static(const float* image, const float* target, int
     }
     const gs_view v = {1.0f, 1.0f, 0.0f, 0.0f, width, height};
     const long long off = 0;
-    gs::launch_dssim(1, &v, &off, image, target, w_dssim, dl_dimage, loss, scratch, static_cast<cudaStream_t>(stream));
-    e = cudaGetLastError();
+    e = gs::launch_dssim(1, &v, &off, image, target, w_dssim, dl_dimage, loss, scratch,
+                         static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(msg, sizeof(msg), "gs_loss_dssim_static: launch: %s", cudaGetErrorString(e));
         return gs::set_error(GS_ECUDA, msg);

@@ -58,3 +58,19 @@ def assert_grad_close(got, ref, name, rel=1e-3, abs_floor=1e-6, frac=1.0, mask=N
         f"({got.ravel()[w]:.4g}, {ref.ravel()[w]:.4g})" for w in worst)
     assert np.mean(ok) >= frac, msg
     return float(np.mean(ok))
+
+
+def assert_pose_close(got, ref, name="pose", rel=1e-3, abs_floor=1e-6, slack=None):
+    """The per-element rule on each of the 6 components of each view's pose
+    gradient: |got - ref| <= max(rel |ref|, abs_floor) (+ slack, an upper
+    bound on the share of pixels whose forward decision is near a threshold,
+    where a test has such pixels)."""
+    got = np.asarray(got, np.float64).reshape(-1, 6)
+    ref = np.asarray(ref, np.float64).reshape(-1, 6)
+    tol = np.maximum(rel * np.abs(ref), abs_floor)
+    if slack is not None:
+        tol = tol + np.asarray(slack, np.float64).reshape(-1, 6)
+    err = np.abs(got - ref)
+    ratio = err / tol
+    assert np.all(err <= tol), f"{name}: worst error / tolerance {ratio.max():.3g}; got {got.tolist()}, ref {ref.tolist()}"
+    return float(ratio.max())

@@ -35,24 +35,34 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"] == bench._config(w, 1)
 
 
+ALU = {"sm_count": 152, "probe_sm_mhz": 1900.0, "fp32_fma_per_sm_clk": 120.0, "fp32x2_fma_per_sm_clk": 121.0,
+       "ex2_per_sm_clk": 30.0, "fp32_fma_per_s": 0.0, "fp32x2_fma_per_s": 0.0, "ex2_per_s": 0.0}
+
+
 def test_roofline_arithmetic():
-    # blend_bwd: (16 eval + 33 contributing) lane-ops per pair over the launch time
-    c = [0, 0, 1_000_000, 500_000, 0, 2_000, 0, 0, 0, 0]
-    r = bench.roofline_for("blend_bwd", 1.0, 1, c, 10, 2, 100, 3, {"hbm_gbs": 5000.0}, 2000.0)
+    # blend_bwd: (16 eval + 33 contributing) lane-ops per pair over the launch
+    # time, against the measured FFMA rate x SM count x the run's SM clock
+    c = [0, 0, 1_000_000, 500_000, 0, 2_000, 0, 0, 0, 0, 0]
+    r = bench.roofline_for("blend_bwd", 1.0, 1, c, 10, 2, 100, 3, {"hbm_gbs": 5000.0}, ALU, 2000.0)
     ops = 16 * 1_000_000 + 33 * 500_000
     assert r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(ops / 1e-3 / 1e12)
-    assert r["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert r["peak"] == pytest.approx(120.0 * 152 * 2000e6 / 1e12)
+    assert r["mufu_frac"] == pytest.approx((1_000_000 + 500_000) / 1e-3 / (30.0 * 152 * 2000e6))
     tr = bench.TRAFFIC_PER_UNIT["blend_bwd"]
     assert r["traffic"] == pytest.approx(tr[0] * c[tr[1]])
-    assert "2000 MHz" in r["peak_source"]
-    # HBM kernels: algorithmic bytes over time against the measured (or fallback) peak
-    n, V = 1000, 4
-    r = bench.roofline_for("scatter_keys", 2.0, 2, c, n, V, 5000, 3, {"hbm_gbs": 5000.0}, 2000.0)
-    by = (n * V * 12 + 5000 * 8) / 2
+    assert "2000 MHz" in r["peak_source"] and "of measured" in r["peak_source"]
+    # HBM kernels: algorithmic bytes (visible pairs counted apart) over time
+    n, V, n_vis = 1000, 4, 1500
+    c[10] = n_vis
+    r = bench.roofline_for("scatter_keys", 2.0, 2, c, n, V, 5000, 3, {"hbm_gbs": 5000.0}, ALU, 2000.0)
+    by = (n * V * 8 + n_vis * 4 + 5000 * 8) / 2
     assert r["achieved"] == pytest.approx(by / 2e-3 / 1e9) and r["frac"] == pytest.approx(r["achieved"] / 5000.0)
     assert "of measured" in r["peak_source"]
-    r = bench.roofline_for("preprocess_fwd", 1.0, 1, c, n, V, 0, 3, {"hbm_gbs": 6800.0, "_fallback": True}, 2070.0)
+    r = bench.roofline_for("preprocess_fwd", 1.0, 1, c, n, V, 0, 3, {"hbm_gbs": 6800.0, "_fallback": True}, ALU,
+                           2070.0)
+    by = n * 236 + n_vis * 60 + (n * V - n_vis) * 16
+    assert r["achieved"] == pytest.approx(by / 1e-3 / 1e9)
     assert "of fallback" in r["peak_source"]
 
 

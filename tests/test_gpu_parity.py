@@ -17,7 +17,8 @@ from paper_2410_08743_gb300 import _lib as L
 from paper_2410_08743_gb300 import synth
 from paper_2410_08743_gb300.render import Renderer, render
 
-from .gpu_util import DEV, assert_grad_close, gpu_backward_dldc, gpu_forward, poses_dev, to_dev, zero_grads
+from .gpu_util import (DEV, assert_grad_close, assert_pose_close, gpu_backward_dldc, gpu_forward, poses_dev,
+                       to_dev, zero_grads)
 
 pytestmark = pytest.mark.gpu
 
@@ -242,8 +243,7 @@ def _backward_case(R, case):
     assert_grad_close(g["opac"].reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
     assert_grad_close(g["sh"][:, :nc].reshape(n, -1), go["sh"][:, :nc].reshape(n, -1), "sh", mask=keep)
     assert np.all(g["sh"][:, nc:] == 0)
-    for v in range(len(views)):
-        np.testing.assert_allclose(pg[v], go["pose"][v], rtol=1e-3, atol=1e-3 * np.abs(go["pose"][v]).max())
+    assert_pose_close(pg, go["pose"], f"pose ({case})")
 
 
 def test_fused_l1_loss_and_gradient(R):
@@ -276,8 +276,7 @@ def test_fused_l1_loss_and_gradient(R):
     assert_grad_close(g["means"].cpu().numpy(), go["means"], "means", mask=keep)
     assert_grad_close(g["scales"].cpu().numpy(), go["scales"], "scales", mask=keep)
     assert_grad_close(g["opac"].cpu().numpy().reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
-    gp = pg.cpu().numpy()[0]
-    assert np.all(np.abs(gp - go["pose"][0]) <= 1e-3 * np.abs(go["pose"][0]) + 1e-6 + pose_slack), (gp, go["pose"][0])
+    assert_pose_close(pg.cpu().numpy(), go["pose"], "pose (fused L1)", slack=pose_slack)
 
 
 @pytest.mark.parametrize("param", ["se3", "txso3"])
@@ -316,12 +315,67 @@ def test_dssim_loss_and_gradient(R):
     R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_L1_DSSIM, target=tgd, w_l1=0.8, w_dssim=0.2, loss_out=lo), g, pg)
     torch.cuda.synchronize()
     assert abs(lo.item() - (Ld + L1)) <= 2e-6
+    # the D-SSIM term's dL/dC itself, element by element
+    assert_dssim_grad_close(R.query(L.GS_Q_DSSIM_GRAD), dd, "D-SSIM dL/dC (64x48)")
     # the same backward through dL/dC from the oracle's combined gradient
     g2, pg2 = gpu_backward_dldc(R, p, views, P, img, (dd + d1).astype(np.float32))
     for k in ("means", "opac", "sh"):
         a = g[k].cpu().numpy().ravel(); b = g2[k].ravel()
         assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max() + 1e-9, k
     np.testing.assert_allclose(pg.cpu().numpy(), pg2, rtol=2e-3, atol=1e-3 * np.abs(pg2).max())
+
+
+def assert_dssim_grad_close(got, ref, name):
+    """dL/dC of the D-SSIM term per element: |got - ref| <= max(1e-3 |ref|,
+    1e-6 max|ref|).  The floor is relative because dL/dC carries the loss's
+    1/(3HW) normalisation (about 4e-7 per unit at 504x378)."""
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    assert got.shape == ref.shape
+    tol = np.maximum(1e-3 * np.abs(ref), 1e-6 * np.abs(ref).max())
+    err = np.abs(got - ref)
+    k = int(np.argmax(err / tol))
+    assert np.all(err <= tol), f"{name}: worst error / tolerance {err[k] / tol[k]:.3g} at {k} ({got[k]:.6g} vs {ref[k]:.6g})"
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dssim_gradient_per_element_504x378(R, seed):
+    """D-SSIM dL/dC of a 504x378 view (the joint-refinement resolution), from
+    the allocating path inside the backward (GS_Q_DSSIM_GRAD) and from the
+    allocation-free entry point, against the oracle on the same image."""
+    W, H = 504, 378
+    views = [dict(fx=0.8 * W, fy=0.8 * W, cx=W / 2, cy=H / 2, width=W, height=H)]
+    rng = np.random.default_rng(30 + seed)
+    # a rendered-like image: smooth blobs plus noise, and a target close to it
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = np.zeros((3, H, W))
+    for _ in range(40):
+        cx, cy, s = rng.uniform(0, W), rng.uniform(0, H), rng.uniform(5, 40)
+        img += rng.uniform(0, 0.5, (3, 1, 1)) * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * s * s))
+    img = np.clip(img + 0.02 * rng.standard_normal(img.shape), 0, 1).astype(np.float32).ravel()
+    target = np.clip(img + 0.05 * rng.standard_normal(img.size), 0, 1).astype(np.float32)
+    Ld, dd, _ = oracle.loss_dssim(views, img.astype(np.float64), target, weight=0.2)
+    imgd = torch.from_numpy(img).to(DEV)
+    tgd = torch.from_numpy(target).to(DEV)
+    # allocating path: a backward with the D-SSIM term only (L1 weight 0)
+    sc = synth.make_scene_box(7, 500, sh_degree=0, lo=(-1, -1, 3), hi=(1, 1, 5))
+    p = to_dev(sc)
+    P = poses_dev(synth.pose_from_center(np.eye(3), np.zeros(3))[None])
+    R.forward(p, views, P)
+    g = zero_grads(p)
+    pg = torch.zeros(1, 6, dtype=torch.float64, device=DEV)
+    lo = torch.zeros(1, dtype=torch.float64, device=DEV)
+    R.backward(p, views, P, imgd, L.make_loss(L.GS_LOSS_L1_DSSIM, target=tgd, w_l1=0.0, w_dssim=0.2, loss_out=lo), g, pg)
+    torch.cuda.synchronize()
+    assert abs(lo.item() - Ld) <= 1e-6 * max(1.0, Ld), (lo.item(), Ld)
+    assert_dssim_grad_close(R.query(L.GS_Q_DSSIM_GRAD), dd, "D-SSIM dL/dC, allocating path")
+    # allocation-free entry point
+    out = torch.full_like(imgd, float("nan"))
+    ls = torch.full((1,), float("nan"), dtype=torch.float64, device=DEV)
+    L.gs_loss_dssim_static(imgd, tgd, W, H, 0.2, out, ls)
+    torch.cuda.synchronize()
+    assert abs(ls.item() - Ld) <= 1e-6 * max(1.0, Ld), (ls.item(), Ld)
+    assert_dssim_grad_close(out.cpu().numpy(), dd, "D-SSIM dL/dC, allocation-free entry point")
 
 
 def test_autograd_function_matches_oracle(R):
@@ -344,10 +398,16 @@ def test_autograd_function_matches_oracle(R):
     (img * wts).sum().backward()
     go = oracle.backward(sc, views, poses, wts_np_masked.astype(np.float32).astype(np.float64))
     keep = ~go["fragile_g"].astype(bool)
+    n = len(sc["opac"])
+    nc = (sc["sh_degree"] + 1) ** 2
     assert_grad_close(leaves["means"].grad.cpu().numpy(), go["means"], "means", mask=keep)
+    assert_grad_close(leaves["scales"].grad.cpu().numpy(), go["scales"], "scales", mask=keep)
     assert_grad_close(leaves["quats"].grad.cpu().numpy(), go["quats"], "quats", mask=keep)
-    np.testing.assert_allclose(tau.grad.cpu().numpy()[0], go["pose"][0], rtol=1e-3,
-                               atol=1e-3 * np.abs(go["pose"]).max())
+    assert_grad_close(leaves["opac"].grad.cpu().numpy().reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
+    gsh = leaves["sh"].grad.cpu().numpy().reshape(n, 16, 3)
+    assert_grad_close(gsh[:, :nc].reshape(n, -1), go["sh"][:, :nc].reshape(n, -1), "sh", mask=keep)
+    assert np.all(gsh[:, nc:] == 0)
+    assert_pose_close(tau.grad.cpu().numpy(), go["pose"], "pose (autograd)")
 
 
 def test_batched_equals_per_view(R):
@@ -479,8 +539,7 @@ def test_masked_l1_loss_and_gradient(R):
     assert keep.mean() > 0.8
     assert_grad_close(g["means"].cpu().numpy(), go["means"], "means", mask=keep)
     assert_grad_close(g["opac"].cpu().numpy().reshape(-1, 1), go["opac"].reshape(-1, 1), "opac", mask=keep)
-    gp = pg.cpu().numpy()[0]
-    assert np.all(np.abs(gp - go["pose"][0]) <= 1e-3 * np.abs(go["pose"][0]) + 1e-6 + pose_slack), (gp, go["pose"][0])
+    assert_pose_close(pg.cpu().numpy(), go["pose"], "pose (fused L1)", slack=pose_slack)
     # masked-out pixels carry no gradient: an all-masked threshold gives zero
     g0 = zero_grads(p)
     pg0 = torch.zeros(1, 6, dtype=torch.float64, device=DEV)

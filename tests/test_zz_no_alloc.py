@@ -1,11 +1,12 @@
 """gs_loss_dssim_static: the D-SSIM loss term and image gradient of one view,
 with its scratch in a static device array so that it calls no allocator.
 
-It serves callers that cannot call cudaMalloc where they need the loss: code
-that runs while a stream is captured into a CUDA graph, serving loops that
-must not allocate after start-up, hosts that give the library a fixed memory
-budget.  Its results must equal the allocating D-SSIM path inside
-gs_render_backward, on consecutive calls that reuse the shared scratch.
+It serves callers that cannot call cudaMalloc where they need the loss:
+serving loops that fix their device footprint at start-up (a later
+allocation can fail, and it synchronises the device), real-time loops that
+forbid allocator calls after initialisation, hosts that own all device memory.
+Its results must equal the allocating D-SSIM path inside gs_render_backward,
+on consecutive calls that reuse the shared scratch.
 
 This file is collected last on purpose, and passes alone in a fresh process
 as well as after the rest of the suite."""
