@@ -69,6 +69,7 @@ def lib():
         L.or_loss_l1_masked.restype = C.c_double
         L.or_loss_dssim.argtypes = [C.c_int, I32P, F64P, F32P, C.c_double, F64P, F64P]
         L.or_loss_dssim.restype = C.c_double
+        L.or_loss_dssim_cond.argtypes = [C.c_int, I32P, F64P, F32P, C.c_double, F64P]
         L.or_ssim_filter.argtypes = [F64P, C.c_int, C.c_int, F64P]
         L.or_sh_eval.argtypes = [F64P, C.c_int, C.c_int, F64P]
         L.or_se3_exp.argtypes = [F64P, F64P]
@@ -248,6 +249,19 @@ def loss_dssim(views, image, target, weight=1.0):
     L = lib().or_loss_dssim(len(views), _p(wh, I32P), _p(img, F64P), _p(tgt, F32P), float(weight),
                             _p(d, F64P), _p(smap, F64P))
     return L, d, smap
+
+
+def loss_dssim_cond(views, image, target, weight=1.0):
+    """Per element, the sum of the magnitudes of the terms that loss_dssim's
+    dL/dC adds up (a conditioning diagnostic for tolerances: a computation
+    that rounds each term k times with unit roundoff u is off by about
+    k u cond)."""
+    img = np.ascontiguousarray(image, np.float64)
+    tgt = np.ascontiguousarray(target, np.float32)
+    out = np.zeros_like(img)
+    wh = _wh(views)
+    lib().or_loss_dssim_cond(len(views), _p(wh, I32P), _p(img, F64P), _p(tgt, F32P), float(weight), _p(out, F64P))
+    return out
 
 
 def ssim_filter(plane):

@@ -1143,6 +1143,61 @@ double or_loss_dssim(int V, const int* wh, const double* img, const float* targe
     return total;
 }
 
+/* Conditioning of the D-SSIM gradient (a diagnostic for tolerances, not part
+ * of the loss): per element, w/(3HW) times the sum of the magnitudes of the
+ * terms whose signed sum or_loss_dssim returns as dL/dC,
+ *   F(|dmu| + 2|mu_x dvx| + |mu_y dcxy|) + 2|x| F(|dvx|) + |y| F(|dcxy|),
+ * with the partials of f = SSIM at each window centre as in or_loss_dssim.
+ * A computation of dL/dC in a precision with unit roundoff u that rounds
+ * each of those terms a bounded number k of times is off by at most about
+ * k u cond (the classical bound for sums of n terms, (n - 1) u sum |t_i|). */
+void or_loss_dssim_cond(int V, const int* wh, const double* img, const float* target, double w, double* cond) {
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double g[11];
+    ssim_window(g);
+    size_t off = 0;
+    for (int v = 0; v < V; v++) {
+        int W = wh[2 * v], H = wh[2 * v + 1];
+        size_t np = (size_t)W * H;
+        double m = 3.0 * (double)np;
+        double* buf = (double*)malloc(sizeof(double) * np * 14);
+        double *X = buf, *Y = buf + np, *XX = buf + 2 * np, *YY = buf + 3 * np, *XY = buf + 4 * np;
+        double *mx = buf + 5 * np, *my = buf + 6 * np, *sxx = buf + 7 * np, *syy = buf + 8 * np, *sxy = buf + 9 * np;
+        double *aA = buf + 10 * np, *aB = buf + 11 * np, *aC = buf + 12 * np, *tmp = buf + 13 * np;
+        for (int ch = 0; ch < 3; ch++) {
+            for (size_t p = 0; p < np; p++) {
+                X[p] = img[off + ch * np + p]; Y[p] = (double)target[off + ch * np + p];
+                XX[p] = X[p] * X[p]; YY[p] = Y[p] * Y[p]; XY[p] = X[p] * Y[p];
+            }
+            filt2(X, W, H, g, mx); filt2(Y, W, H, g, my);
+            filt2(XX, W, H, g, sxx); filt2(YY, W, H, g, syy); filt2(XY, W, H, g, sxy);
+            for (size_t p = 0; p < np; p++) {
+                double ux = mx[p], uy = my[p];
+                double vx = sxx[p] - ux * ux, vy = syy[p] - uy * uy, cxy = sxy[p] - ux * uy;
+                double N1 = 2.0 * ux * uy + C1, N2 = 2.0 * cxy + C2;
+                double D1 = ux * ux + uy * uy + C1, D2 = vx + vy + C2;
+                double f = (N1 * N2) / (D1 * D2);
+                double dmu = 2.0 * uy * N2 / (D1 * D2) - f * 2.0 * ux / D1;
+                double dvx = -f / D2;
+                double dcxy = 2.0 * N1 / (D1 * D2);
+                aA[p] = fabs(dmu) + 2.0 * fabs(ux * dvx) + fabs(uy * dcxy);
+                aB[p] = fabs(dvx);
+                aC[p] = fabs(dcxy);
+            }
+            double* out = cond + off + ch * np;
+            filt2(aA, W, H, g, tmp);
+            for (size_t p = 0; p < np; p++) out[p] = tmp[p];
+            filt2(aB, W, H, g, tmp);
+            for (size_t p = 0; p < np; p++) out[p] += 2.0 * fabs(X[p]) * tmp[p];
+            filt2(aC, W, H, g, tmp);
+            for (size_t p = 0; p < np; p++) out[p] += fabs(Y[p]) * tmp[p];
+            for (size_t p = 0; p < np; p++) out[p] *= fabs(w) / m;
+        }
+        free(buf);
+        off += 3 * np;
+    }
+}
+
 /* Exposed for the window pin: zero-padded Gaussian filtering of one plane. */
 void or_ssim_filter(const double* x, int W, int H, double* out) {
     double g[11];

@@ -614,6 +614,7 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     const bool grow = !(opts->flags & GS_F_NO_SYNC);
     CK(cudaSetDevice(ctx->device));
     fr->have_forward = false;
+    fr->have_dssim_grad = false;     // a D-SSIM gradient belongs to the forward it followed
     if ((rc = upload_views(fr, n_views, views, img_offs, grow, s))) return rc;
     const int n = scene->d.n;
     const size_t vn = (size_t)n * n_views;

@@ -74,3 +74,29 @@ def assert_pose_close(got, ref, name="pose", rel=1e-3, abs_floor=1e-6, slack=Non
     ratio = err / tol
     assert np.all(err <= tol), f"{name}: worst error / tolerance {ratio.max():.3g}; got {got.tolist()}, ref {ref.tolist()}"
     return float(ratio.max())
+
+
+# FP32 roundings each term of the D-SSIM gradient goes through on the GPU:
+# the forward's two 11-tap filter passes (10 + 10 additions), the partials of
+# SSIM (4), the backward's two filter passes (10 + 10) and the final sum (4).
+DSSIM_FP32_ROUNDINGS = 48
+
+
+def assert_dssim_grad_close(got, ref, cond, name):
+    """The D-SSIM term's dL/dC per element:
+    |got - ref| <= max(1e-3 |ref|, 1e-6 max|ref|) + 48 * 2^-24 * cond,
+    cond = the oracle's sum of the magnitudes of the terms that make up the
+    element (oracle.loss_dssim_cond).  The gradient at a pixel is a sum of
+    terms of up to ~1/C2 that cancel to a far smaller value where the image is
+    smooth, so FP32 evaluation is accurate relative to cond, not to |ref|."""
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    cond = np.asarray(cond, np.float64).ravel()
+    assert got.shape == ref.shape == cond.shape
+    tol = np.maximum(1e-3 * np.abs(ref), 1e-6 * np.abs(ref).max()) + DSSIM_FP32_ROUNDINGS * 2.0 ** -24 * cond
+    err = np.abs(got - ref)
+    r = err / tol
+    k = int(np.argmax(r))
+    assert np.all(err <= tol), (f"{name}: worst error / tolerance {r[k]:.3g} at {k}: {got[k]:.6g} vs {ref[k]:.6g} "
+                                f"(max |ref| {np.abs(ref).max():.4g}, cond {cond[k]:.3g})")
+    return float(r.max())

@@ -229,3 +229,31 @@ def test_gaussian_adam_first_step_closed_form_and_chain():
     assert np.array_equal(raw["sh"][:, 12:], r0["sh"][:, 12:])      # above degree 1: untouched
     np.testing.assert_allclose(sc, np.exp(raw["log_scales"]), rtol=1e-15)
     np.testing.assert_allclose(op, 1 / (1 + np.exp(-raw["logit_opac"][:, 0])), rtol=1e-15)
+
+
+def test_dssim_conditioning_bounds_the_gradient_and_closed_form():
+    """The conditioning diagnostic is a sum of the magnitudes of the terms the
+    D-SSIM gradient adds up, so it bounds |dL/dC| (triangle inequality).  For
+    two equal constant images c inside the border band, SSIM's partials are
+    dmu = 0, dvx = -1/C2, dcxy = 2/C2, so the terms 2c/C2 + 2c/C2 (from the
+    folded mu term) + 2c/C2 + 2c/C2 cancel to a zero gradient while their
+    magnitudes add to 8 c w / (3 H W C2)."""
+    rng = np.random.default_rng(16)
+    W, H = 24, 20
+    views = _views(W, H)
+    img = rng.uniform(size=3 * W * H)
+    tgt = rng.uniform(size=3 * W * H).astype(np.float32)
+    _, d, _ = oracle.loss_dssim(views, img, tgt, weight=0.2)
+    cond = oracle.loss_dssim_cond(views, img, tgt, weight=0.2)
+    assert np.all(cond >= np.abs(d) * (1 - 1e-12))
+    assert np.median(cond / np.maximum(np.abs(d), 1e-300)) > 2.0      # it does cancel
+    c, w = 0.625, 0.2
+    W, H = 40, 36
+    views = _views(W, H)
+    flat = np.full(3 * W * H, c)
+    _, d0, _ = oracle.loss_dssim(views, flat, flat.astype(np.float32), weight=w)
+    cond0 = oracle.loss_dssim_cond(views, flat, flat.astype(np.float32), weight=w)
+    inner = cond0.reshape(3, H, W)[:, 10:-10, 10:-10]     # windows of windows inside the image
+    assert inner.size == 3 * 16 * 20
+    np.testing.assert_allclose(inner, 8 * c * w / (3 * W * H * 0.03 ** 2), rtol=1e-12)
+    assert np.abs(d0).max() < 1e-12

@@ -16,11 +16,12 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2410_08743_gb300 import _lib as L
 from paper_2410_08743_gb300 import synth
 from paper_2410_08743_gb300.render import Renderer
 
-from .gpu_util import DEV, assert_grad_close, poses_dev, to_dev, zero_grads
+from .gpu_util import DEV, assert_dssim_grad_close, assert_grad_close, poses_dev, to_dev, zero_grads
 
 pytestmark = pytest.mark.gpu
 
@@ -62,10 +63,20 @@ def test_static_dssim_matches_allocating_path_on_consecutive_calls(R):
         dldc = torch.full_like(img, float("nan"))
         lb = torch.full((1,), float("nan"), dtype=torch.float64, device=DEV)
         assert _direct_call(img, target, W, H, 0.2, dldc, lb) == L.GS_OK, L.gs_last_error()
+        torch.cuda.synchronize()
+        assert torch.isfinite(dldc).all()
+        # the same kernels on the same inputs: dL/dC equal bit for bit to the
+        # allocating path's, and within the D-SSIM tolerance of the oracle's
+        ref_dldc = R.query(L.GS_Q_DSSIM_GRAD)
+        assert np.array_equal(dldc.cpu().numpy(), ref_dldc), call
+        img64 = img.cpu().numpy().astype(np.float64)
+        tg_np = target.cpu().numpy()
+        _, od, _ = oracle.loss_dssim(views, img64, tg_np, weight=0.2)
+        assert_dssim_grad_close(dldc.cpu().numpy(), od, oracle.loss_dssim_cond(views, img64, tg_np, 0.2),
+                                f"static D-SSIM dL/dC (call {call})")
         gb, pgb = zero_grads(p), torch.zeros(1, 6, dtype=torch.float64, device=DEV)
         R.backward(p, views, P, img, L.make_loss(L.GS_LOSS_DLDC, dl_dimage=dldc), gb, pgb)
         torch.cuda.synchronize()
-        assert torch.isfinite(dldc).all()
         assert abs(lb.item() - la.item()) <= 1e-6 * max(1.0, abs(la.item())), (call, lb.item(), la.item())
         for k in ("means", "scales", "quats", "opac", "sh"):
             assert_grad_close(gb[k].cpu().numpy().reshape(len(sc["opac"]), -1),
