@@ -235,7 +235,7 @@ def test_joint_300k_l1_dssim_one_view_parity(R):
     gf = oracle.backward(sc, v, init, np.where(m, dl_gpu, 0.0), want_g2d=True)
     ind = oracle.backward(sc, v, init, np.where(m, 1.0, 0.0), want_g2d=True)
     keep = ~(go_g["fragile_g"].astype(bool) | (np.abs(ind["g2d"]).sum(1) > 0))
-    assert keep.mean() > 0.95, keep.mean()
+    assert keep.mean() > 0.9, keep.mean()
     gg = {k_: v_.cpu().numpy() for k_, v_ in g.items()}
     _check_grads_large(gg, go_g, n, sc["sh_degree"], keep=keep)
     assert_pose_close(pg.cpu().numpy(), go_g["pose"], "pose (GPU L1 + D-SSIM)", slack=2.0 * np.abs(gf["pose"]))
