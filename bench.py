@@ -791,10 +791,11 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
         # marker (rect, depth, radius) per culled pair
         by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) + n_vis * 60 + (n * V - n_vis) * 16) / lps
     elif kname == "preprocess_bwd":
-        # parameters read and gradients read + written once per launch; per
-        # visible pair its 36 B 2D gradient read and cleared, 8 B rectangle;
-        # the rectangle only for a culled pair
-        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) * 3 + n_vis * (36 * 2 + 8) + (n * V - n_vis) * 8) / lps
+        # parameters read and the caller's gradients read + written once per
+        # launch; the 8 B rectangle of every pair, the 36 B 2D gradient of a
+        # visible one (the zeros it writes back over the records it consumed
+        # replace a clearing pass and are not counted)
+        by = (n * (4 * (3 + 3 + 4 + 1) + 4 * ncoef) * 3 + n_vis * 36 + n * V * 8) / lps
     elif kname == "segment_sort":
         by = n_keys * (8 + 4) / lps
     elif kname == "scatter_keys":

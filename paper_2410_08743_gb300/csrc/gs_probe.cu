@@ -6,8 +6,11 @@
 // independent dependency chains, so that the pipe under test, not latency,
 // limits it: scalar FFMA, paired FFMA (fma.rn.f32x2, both halves counted) and
 // MUFU ex2 (each ex2 followed by one FADD to keep its argument bounded).  The
-// rate per SM per cycle comes from clock64() deltas per block (independent of
-// the clock the GPU runs at); the rate per second from CUDA events.
+// rate per SM per cycle comes from clock64() readings (independent of the
+// clock the GPU runs at): per SM, the work of its blocks over the span from
+// its first block's start to its last block's end (the warp scheduler favours
+// older warps, so the blocks of one SM finish at different times); the rate
+// per second from CUDA events.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +39,7 @@ __device__ __forceinline__ float pr_sum2(unsigned long long r) {
 }
 
 // kind 0: FFMA; kind 1: fma.rn.f32x2; kind 2: ex2.approx + FADD.
+// cycles[3 * block + 0..2] = start clock, end clock, SM id
 template <int KIND>
 __global__ void __launch_bounds__(PR_THREADS) k_probe(float s, float* __restrict__ sink,
                                                       long long* __restrict__ cycles) {
@@ -88,7 +92,13 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(float s, float* __restrict
     __syncthreads();
     const long long c1 = clock64();
     sink[(size_t)blockIdx.x * PR_THREADS + threadIdx.x] = acc;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = c1 - c0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        cycles[3 * blockIdx.x] = c0;
+        cycles[3 * blockIdx.x + 1] = c1;
+        cycles[3 * blockIdx.x + 2] = (long long)smid;
+    }
 }
 
 // lane operations one block of a probe executes
@@ -125,12 +135,12 @@ extern "C" int gs_measure_alu_peaks(int device, gs_alu_peaks* out) {
     double rate_clk[3] = {0, 0, 0}, rate_s[3] = {0, 0, 0}, mhz_sum = 0.0;
     int mhz_n = 0;
     if ((e = cudaMalloc(&sink, sizeof(float) * (size_t)max_blocks * PR_THREADS)) != cudaSuccess ||
-        (e = cudaMalloc(&cyc, sizeof(long long) * (size_t)max_blocks)) != cudaSuccess ||
+        (e = cudaMalloc(&cyc, sizeof(long long) * 3 * (size_t)max_blocks)) != cudaSuccess ||
         (e = cudaEventCreate(&ev0)) != cudaSuccess || (e = cudaEventCreate(&ev1)) != cudaSuccess) {
         snprintf(msg, sizeof(msg), "gs_measure_alu_peaks: setup: %s", cudaGetErrorString(e));
         rc = set_error(e == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA, msg);
     }
-    std::vector<long long> hc(max_blocks);
+    std::vector<long long> hc(3 * (size_t)max_blocks);
     for (int kind = 0; kind < 3 && rc == GS_OK; kind++) {
         const int grid = sms * per_sm[kind];
         float best_ms = 0.0f;
@@ -142,22 +152,45 @@ extern "C" int gs_measure_alu_peaks(int device, gs_alu_peaks* out) {
             else k_probe<2><<<grid, PR_THREADS>>>(1.0f, sink, cyc);
             cudaEventRecord(ev1, 0);
             if ((e = cudaEventSynchronize(ev1)) != cudaSuccess ||
-                (e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                (e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * 3 * grid, cudaMemcpyDeviceToHost)) != cudaSuccess) {
                 snprintf(msg, sizeof(msg), "gs_measure_alu_peaks: probe %d: %s", kind, cudaGetErrorString(e));
                 rc = set_error(GS_ECUDA, msg);
                 break;
             }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, ev0, ev1);
-            std::vector<long long> srt(hc.begin(), hc.begin() + grid);
-            std::sort(srt.begin(), srt.end());
-            const double med_cycles = (double)srt[grid / 2];
-            // one wave: every SM runs per_sm[kind] blocks concurrently for ~med_cycles
-            const double clk = probe_lane_ops(kind) * per_sm[kind] / med_cycles;
+            // per SM: its blocks' work over [first start, last end] (clock64 is per
+            // SM; SM ids need not be dense, so the tables span the largest id seen)
+            long long n_ids = 0;
+            for (int b = 0; b < grid; b++) n_ids = std::max(n_ids, hc[3 * (size_t)b + 2] + 1);
+            n_ids = std::min<long long>(n_ids, 4096);
+            std::vector<long long> lo(n_ids, -1), hi(n_ids, -1);
+            std::vector<int> nb(n_ids, 0);
+            for (int b = 0; b < grid; b++) {
+                const long long id = hc[3 * (size_t)b + 2];
+                if (id < 0 || id >= n_ids) continue;
+                const long long t0 = hc[3 * (size_t)b], t1 = hc[3 * (size_t)b + 1];
+                if (nb[id] == 0 || t0 < lo[id]) lo[id] = t0;
+                if (nb[id] == 0 || t1 > hi[id]) hi[id] = t1;
+                nb[id]++;
+            }
+            std::vector<double> rates;
+            double span_max = 0.0;
+            for (long long id = 0; id < n_ids; id++) {
+                if (nb[id] == 0 || hi[id] <= lo[id]) continue;
+                rates.push_back(probe_lane_ops(kind) * nb[id] / (double)(hi[id] - lo[id]));
+                span_max = std::max(span_max, (double)(hi[id] - lo[id]));
+            }
+            if (rates.empty()) {
+                rc = set_error(GS_ECUDA, "gs_measure_alu_peaks: no block timings");
+                break;
+            }
+            std::sort(rates.begin(), rates.end());
+            const double clk = rates[rates.size() / 2];
             if (rep > 0 && (best_ms == 0.0f || ms < best_ms)) {
                 best_ms = ms;
                 best_clk = clk;
-                mhz_sum += (double)srt[grid - 1] / (ms * 1e3);   // slowest block's cycles over the event time
+                mhz_sum += span_max / (ms * 1e3);   // longest SM span in cycles over the event time
                 mhz_n++;
             }
         }
