@@ -331,12 +331,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
     if (e > cap) e = cap;
     const uint32_t n_list = e - s;
     const size_t vbase = (size_t)v * n;
-    float T[PX], C0[PX], C1[PX], C2[PX];
+    float pT[PX], C0[PX], C1[PX], C2[PX];
     uint32_t last[PX];
     bool done[PX];
 #pragma unroll
     for (int q = 0; q < PX; q++) {
-        T[q] = 1.0f; C0[q] = C1[q] = C2[q] = 0.0f; last[q] = 0;
+        pT[q] = 1.0f; C0[q] = C1[q] = C2[q] = 0.0f; last[q] = 0;
         done[q] = !(tx0 + lx < W && ty0 + ly + WARP_H * q < H);
     }
     auto all_done = [&]() -> bool {
@@ -366,43 +366,52 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
             __syncthreads();
             unsigned char* wl = sm.wl[wid];
             const int nw = warp_compact(sm.u.sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
-            const bool live = !all_done();
-            if (__any_sync(0xffffffffu, live)) n_went += (uint32_t)nw;
-            if (live) {
-                for (int qq = 0; qq < nw; qq++) {
-                    const int jj = wl[qq];
-                    const float4 a = sm.u.sb.A[jj];
-                    const float2 h = sm.u.sb.H[jj];
-                    const float dx = __fsub_rn(fpx, a.x);
-                    if (fabsf(dx) > h.x) continue;
-                    float dy[PX];
-                    bool inbox[PX], any = false;
+            // the warp walks its entries in lock step; a pixel that has stopped
+            // or is outside the splat's box blends nothing (weight 0)
+            if (CNT && __any_sync(0xffffffffu, !all_done())) n_went += (uint32_t)nw;
+            for (int qq = 0; qq < nw; qq++) {
+                if (__all_sync(0xffffffffu, all_done())) break;
+                const int jj = wl[qq];
+                const uint32_t pos1 = base + (uint32_t)jj + 1u;
+                const float4 a = sm.u.sb.A[jj];
+                const float2 h = sm.u.sb.H[jj];
+                const float dx = __fsub_rn(fpx, a.x);
+                const bool inx = fabsf(dx) <= h.x;
+                float dy[PX];
+                bool u[PX];
+                bool any = false;
 #pragma unroll
-                    for (int q = 0; q < PX; q++) {
-                        dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
-                        inbox[q] = !done[q] && fabsf(dy[q]) <= h.y;
-                        any |= inbox[q];
-                    }
-                    if (!any) continue;
-                    const float4 b = sm.u.sb.B[jj];
+                for (int q = 0; q < PX; q++) {
+                    dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
+                    u[q] = !done[q] && inx && fabsf(dy[q]) <= h.y;
+                    any = any || u[q];
+                    if (CNT) n_eval += u[q];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                const float4 b = sm.u.sb.B[jj];
+                const float cb = sm.u.sb.Cb[jj];
+                // alpha of each pixel (Eq. 3) with pair_alpha's operation sequence
+                const float qx = __fmul_rn(a.z, __fmul_rn(dx, dx));
 #pragma unroll
-                    for (int q = 0; q < PX; q++) {
-                        if (!inbox[q]) continue;
-                        n_eval++;
-                        float G, alpha;
-                        bool cl;
-                        if (!pair_alpha(a, b, dx, dy[q], rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
-                        const float Tn = T[q] * (1.0f - alpha);
-                        if (Tn < rp.t_min) { done[q] = true; continue; }
-                        n_blend++;
-                        const float w = alpha * T[q];
-                        C0[q] = fmaf(b.z, w, C0[q]);
-                        C1[q] = fmaf(b.w, w, C1[q]);
-                        C2[q] = fmaf(sm.u.sb.Cb[jj], w, C2[q]);
-                        T[q] = Tn;
-                        last[q] = base + jj + 1;
-                    }
-                    if (all_done()) break;
+                for (int q = 0; q < PX; q++) {
+                    const float pw = __fmaf_rn(-a.w, __fmul_rn(dx, dy[q]),
+                                               __fmul_rn(-0.5f, __fmaf_rn(b.x, __fmul_rn(dy[q], dy[q]), qx)));
+                    const float ar = __fmul_rn(b.y, fast_exp2(__fmul_rn(pw, GS_LOG2E)));
+                    const float alpha = ar > rp.alpha_max ? rp.alpha_max : ar;
+                    const bool ok = u[q] && !(pw > 0.0f) && alpha >= rp.alpha_min;
+                    // Eq. 4 front to back; stop before the splat that would take
+                    // the transmittance below t_min
+                    const float Tn = pT[q] * (1.0f - alpha);
+                    const bool stop = ok && Tn < rp.t_min;
+                    const bool blend = ok && !stop;
+                    done[q] = done[q] || stop;
+                    const float w = blend ? alpha * pT[q] : 0.0f;
+                    C0[q] = fmaf(b.z, w, C0[q]);
+                    C1[q] = fmaf(b.w, w, C1[q]);
+                    C2[q] = fmaf(cb, w, C2[q]);
+                    pT[q] = blend ? Tn : pT[q];
+                    last[q] = blend ? pos1 : last[q];
+                    if (CNT) n_blend += blend;
                 }
             }
         }
@@ -525,13 +534,13 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
             const size_t p = (size_t)py * W + px;
             const size_t np = (size_t)W * H;
             float* img = image + vd.img_off;
-            const float c0 = fmaf(T[q], rp.bg[0], C0[q]);
-            const float c1 = fmaf(T[q], rp.bg[1], C1[q]);
-            const float c2 = fmaf(T[q], rp.bg[2], C2[q]);
+            const float c0 = fmaf(pT[q], rp.bg[0], C0[q]);
+            const float c1 = fmaf(pT[q], rp.bg[1], C1[q]);
+            const float c2 = fmaf(pT[q], rp.bg[2], C2[q]);
             img[p] = c0;
             img[np + p] = c1;
             img[2 * np + p] = c2;
-            T_final[vd.pix_off + p] = T[q];
+            T_final[vd.pix_off + p] = pT[q];
             n_contrib[vd.pix_off + p] = last[q];
             if (target) {
                 const float* tg = target + vd.img_off;
@@ -767,6 +776,19 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
     uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
     // component held by this lane after the transposed reduction
     const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    // per-pixel state in registers, walked in lock step: a pixel that takes no
+    // part in an entry gets alpha 0, so its state is unchanged and its share of
+    // every sum is 0; the warp leaves an entry early only when no pixel of the
+    // warp is in the splat's box, or none gets an alpha above alpha_min
+    float pT[PX], psg[PX], pg0[PX], pg1[PX], pg2[PX], fpy[PX];
+    uint32_t plast[PX];
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        pT[q] = pix[q].T; psg[q] = pix[q].sg; plast[q] = pix[q].last;
+        pg0[q] = pix[q].g0; pg1[q] = pix[q].g1; pg2[q] = pix[q].g2;
+        fpy[q] = (float)(ly + WARP_H * q);
+    }
+    const float amin = rp.alpha_min, amax = rp.alpha_max;
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
@@ -791,58 +813,77 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
             const float4 a = sb.A[jj];
             const float2 h = sb.H[jj];
             const float dx = __fsub_rn(fpx, a.x);
-            bool use[PX];
+            const bool inx = fabsf(dx) <= h.x;
             float dy[PX];
+            bool u[PX];
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PX; q++) {
-                dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
-                use[q] = pos < pix[q].last && fabsf(dx) <= h.x && fabsf(dy[q]) <= h.y;
-                n_eval += use[q];
-                any |= use[q];
+                dy[q] = __fsub_rn(fpy[q], a.y);
+                u[q] = inx && fabsf(dy[q]) <= h.y && pos < plast[q];
+                any = any || u[q];
+                if (CNT) n_eval += u[q];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
-            n_w1++;
+            if (CNT) n_w1++;
+            // alpha of each pixel (Eq. 3) with pair_alpha's operation sequence
             const float4 b = sb.B[jj];
-            float G[PX], alpha[PX];
+            const float dxx = __fmul_rn(dx, dx);
+            const float qx = __fmul_rn(a.z, dxx);
+            float G[PX], al[PX], yy[PX];
             bool cl[PX];
             any = false;
 #pragma unroll
             for (int q = 0; q < PX; q++) {
-                G[q] = 0.f; alpha[q] = 0.f; cl[q] = false;
-                if (use[q]) use[q] = pair_alpha(a, b, dx, dy[q], rp.alpha_min, rp.alpha_max, G[q], alpha[q], cl[q]);
-                any |= use[q];
+                yy[q] = __fmul_rn(dy[q], dy[q]);
+                const float pw = __fmaf_rn(-a.w, __fmul_rn(dx, dy[q]), __fmul_rn(-0.5f, __fmaf_rn(b.x, yy[q], qx)));
+                G[q] = fast_exp2(__fmul_rn(pw, GS_LOG2E));
+                const float ar = __fmul_rn(b.y, G[q]);
+                cl[q] = ar > amax;
+                al[q] = cl[q] ? amax : ar;
+                u[q] = u[q] && !(pw > 0.0f) && al[q] >= amin;
+                any = any || u[q];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
-            n_w2++;
-            float r[8], r8 = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 8; c++) r[c] = 0.0f;
+            if (CNT) n_w2++;
+            // Per pixel, back to front: T_i = T_{i+1} / (1 - alpha_i), weight
+            // w = alpha T_i, dL/dalpha = T_i (c . g) - S / (1 - alpha) with S the
+            // colour behind (incl. background) dotted with g.  dL/dpower =
+            // alpha dL/dalpha where alpha is not clamped.  Per entry the lane
+            // sums dp = dL/dpower into the moments D = sum dp, My = sum dp dy,
+            // Myy = sum dp dy^2 (its pixels share dx); the conic and mean
+            // gradients are linear in the moments and formed once per splat.
             const float cb = sb.Cb[jj];
+            float r[9];
+            float D = 0.0f, My = 0.0f, Myy = 0.0f;
+            r[5] = 0.0f; r[6] = 0.0f; r[7] = 0.0f; r[8] = 0.0f;
 #pragma unroll
             for (int q = 0; q < PX; q++) {
-                if (!use[q]) continue;
-                n_used++;
-                BwdPixel& P = pix[q];
-                const float inv_om = __fdividef(1.0f, 1.0f - alpha[q]);
-                const float Ti = P.T * inv_om;
-                const float wgt = alpha[q] * Ti;
-                r[6] += wgt * P.g0; r[7] += wgt * P.g1; r8 += wgt * P.g2;
-                const float cg = b.z * P.g0 + b.w * P.g1 + cb * P.g2;
-                const float dLda = Ti * cg - P.sg * inv_om;
-                P.sg = fmaf(wgt, cg, P.sg);
-                P.T = Ti;
-                if (!cl[q]) {
-                    r[5] += G[q] * dLda;
-                    const float dp = alpha[q] * dLda;
-                    const float y = dy[q];
-                    r[0] += dp * (a.z * dx + a.w * y);
-                    r[1] += dp * (a.w * dx + b.x * y);
-                    r[2] += -0.5f * dp * dx * dx;
-                    r[3] += -dp * dx * y;
-                    r[4] += -0.5f * dp * y * y;
-                }
+                if (CNT) n_used += u[q];
+                const float alq = u[q] ? al[q] : 0.0f;
+                const float Gq = (u[q] && !cl[q]) ? G[q] : 0.0f;
+                const float inv = __fdividef(1.0f, 1.0f - alq);
+                const float Ti = pT[q] * inv;
+                const float w = alq * Ti;
+                r[6] = fmaf(w, pg0[q], r[6]);
+                r[7] = fmaf(w, pg1[q], r[7]);
+                r[8] = fmaf(w, pg2[q], r[8]);
+                const float cg = fmaf(cb, pg2[q], fmaf(b.w, pg1[q], b.z * pg0[q]));
+                const float dL = fmaf(Ti, cg, -(psg[q] * inv));
+                psg[q] = fmaf(w, cg, psg[q]);
+                pT[q] = u[q] ? Ti : pT[q];
+                const float t = Gq * dL;            // dL/do contribution
+                r[5] += t;
+                const float dp = b.y * t;           // dL/dpower
+                D += dp;
+                My = fmaf(dp, dy[q], My);
+                Myy = fmaf(dp, yy[q], Myy);
             }
+            r[0] = dx * D;      // sum dp dx
+            r[1] = My;          // sum dp dy
+            r[2] = dxx * D;     // sum dp dx^2
+            r[3] = dx * My;     // sum dp dx dy
+            r[4] = Myy;         // sum dp dy^2
             // transposed reduce-scatter of r[0..7]: afterwards lane L (L % 4 == 0)
             // holds the warp sum of component comp(L)
 #pragma unroll
@@ -867,16 +908,21 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
             }
             r[0] += __shfl_xor_sync(0xffffffffu, r[0], 2);
             r[0] += __shfl_xor_sync(0xffffffffu, r[0], 1);
-            r8 = warp_sum(r8);
+            const float r8 = warp_sum(r[8]);
             if ((lane & 3) == 0) atomicAdd(&s_acc[jj * 9 + comp], r[0]);
             if (lane == 1) atomicAdd(&s_acc[jj * 9 + 8], r8);
         }
         __syncthreads();
-        // one set of vector atomics per (tile, splat) of the batch
+        // one set of vector atomics per (tile, splat) of the batch: the conic
+        // and mean gradients from the moments (power = -1/2 (a dx^2 + c dy^2)
+        // - b dx dy, d = p - mu: dpower/dmu = (a dx + b dy, b dx + c dy),
+        // dpower/d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2))
         for (int j = threadIdx.x; j < cnt; j += NT) {
             const float* acc = s_acc + j * 9;
-            const float4 ga = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            const float4 gb = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            const float ca = sb.A[j].z, cb_ = sb.A[j].w, cc = sb.B[j].x;
+            const float Mx = acc[0], My = acc[1];
+            const float4 ga = make_float4(fmaf(ca, Mx, cb_ * My), fmaf(cb_, Mx, cc * My), -0.5f * acc[2], -acc[3]);
+            const float4 gb = make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]);
             const bool nz = (ga.x != 0.f) | (ga.y != 0.f) | (ga.z != 0.f) | (ga.w != 0.f) | (gb.x != 0.f) |
                             (gb.y != 0.f) | (gb.z != 0.f) | (gb.w != 0.f) | (acc[8] != 0.f);
             if (nz) {
