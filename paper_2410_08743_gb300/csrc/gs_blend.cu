@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
                 if (CNT) n_used += u[q];
                 const float alq = u[q] ? al[q] : 0.0f;
                 const float Gq = (u[q] && !cl[q]) ? G[q] : 0.0f;
-                const float inv = __fdividef(1.0f, 1.0f - alq);
+                const float inv = fast_rcp(1.0f - alq);    // 1 - alpha lies in [0.01, 1]
                 const float Ti = pT[q] * inv;
                 const float w = alq * Ti;
                 r[6] = fmaf(w, pg0[q], r[6]);

@@ -100,6 +100,13 @@ __device__ __forceinline__ float fast_exp2(float x) {
 
 #define GS_LOG2E 1.4426950408889634f
 
+// Approximate reciprocal (MUFU); for arguments in normal range.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------ kernel entry
 // Host-side launchers (defined in the .cu files).
 namespace gs {
