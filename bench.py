@@ -458,13 +458,27 @@ def run_gpu(args):
     serving = None
     if not args.no_serve:
         # the paper's offered load (200/s of 100-step solves at ~0.4 Mpix) exceeds
-        # one GPU (about 15 solves/s), so its latencies include the backlog; a
-        # second replay at a load both forms sustain shows latency without it
+        # one GPU, so its latencies include the backlog; a sweep of Poisson
+        # rates finds the largest one the batched server sustains (completions
+        # keep pace, p99 within 1 s), where both forms are measured again
         tt = tuned["tuning"]
         serving = run_serving(p, dev, args, 64, tuning=tt)
         serving["plain"] = run_serving(p, dev, args, 1, tuning=tt)
-        serving["sustainable"] = {"batched": run_serving(p, dev, args, 64, rate_hz=6.0, n_requests=30, tuning=tt),
-                                  "plain": run_serving(p, dev, args, 1, rate_hz=6.0, n_requests=30, tuning=tt)}
+        sweep, best = [], None
+        for rate in (4.0, 8.0, 12.0, 16.0, 20.0, 24.0, 32.0):
+            n_req = int(max(24, 3.0 * rate))
+            r_ = run_serving(p, dev, args, 64, rate_hz=rate, n_requests=n_req, tuning=tt)
+            ok = r_["solves_per_s"] >= 0.9 * rate and r_["p99_ms"] <= 1000.0
+            sweep.append({k: r_[k] for k in ("rate_hz", "requests", "p50_ms", "p99_ms", "solves_per_s")} |
+                         {"sustained": ok})
+            if not ok:
+                break
+            best = r_
+        serving["rate_sweep"] = sweep
+        if best is not None:
+            serving["sustainable"] = {"rate_hz": best["rate_hz"], "batched": best,
+                                      "plain": run_serving(p, dev, args, 1, rate_hz=best["rate_hz"],
+                                                           n_requests=best["requests"], tuning=tt)}
 
     extras = None
     if not args.no_extras:
@@ -506,6 +520,7 @@ def run_gpu(args):
             "joint": joint, "trajectory": traj, "extras": extras,
             "tuning": tuned,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches * K),
+            **_serving_keys(serving),
             "roofline": roof, "cpu_baseline": cpu, "kernels": kernels,
             "counters": {"keys": n_keys, "pairs_eval_fwd": counters[0], "pairs_blend_fwd": counters[1],
                          "pairs_eval_bwd": counters[2], "pairs_grad_bwd": counters[3],
@@ -524,6 +539,27 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _serving_keys(serving):
+    """Top-level serving figures: p50/p99 latency and solves/s of the batched
+    and the plain (one solve at a time) server at the offered 200/s and at the
+    largest sustained rate of the sweep."""
+    if not serving:
+        return {}
+    out = {"serve_rate_hz": serving["rate_hz"],
+           "serve_p50_ms": serving["p50_ms"], "serve_p99_ms": serving["p99_ms"],
+           "serve_solves_per_s": serving["solves_per_s"],
+           "serve_plain_p50_ms": serving["plain"]["p50_ms"], "serve_plain_p99_ms": serving["plain"]["p99_ms"],
+           "serve_plain_solves_per_s": serving["plain"]["solves_per_s"]}
+    sus = serving.get("sustainable")
+    if sus:
+        out.update({"serve_max_sustained_rate_hz": sus["rate_hz"],
+                    "serve_sustained_p50_ms": sus["batched"]["p50_ms"],
+                    "serve_sustained_p99_ms": sus["batched"]["p99_ms"],
+                    "serve_sustained_plain_p50_ms": sus["plain"]["p50_ms"],
+                    "serve_sustained_plain_p99_ms": sus["plain"]["p99_ms"]})
+    return out
 
 
 def run_extras(r, p, views, P, image, tgt, grads, pose_grad, npix, dev, K):
@@ -702,8 +738,8 @@ def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_reques
     imgs = [r.forward(p, [q["view"]], torch.from_numpy(q["gt_pose"][None]).to(dev)).cpu().numpy() for q in reqs]
     r.close()
     sh = L.gs_scene_borrow(p["means"], p["scales"], p["quats"], p["opac"], p["sh"], p["sh_degree"])
-    srv = L.gs_server_create(dev.index or 0, sh, L.gs_default_opts(), slots, 1280, 720, 200 * (1 << 30), 1 << 20,
-                             tuning=tuning)
+    # mem_budget 0: admission by the device memory that is free
+    srv = L.gs_server_create(dev.index or 0, sh, L.gs_default_opts(), slots, 1280, 720, 0, 1 << 20, tuning=tuning)
     # warm the worker (workspaces) with one small solve
     q0 = reqs[0]
     L.gs_solve_wait(srv, L.gs_solve_submit(srv, q0["view"], imgs[0], q0["init_pose"], 2, 1e-2, 1e-4), 600000)
@@ -730,7 +766,8 @@ def run_serving(p, dev, args, slots: int, rate_hz: float | None = None, n_reques
     return {"slots": slots, "requests": len(reqs), "rate_hz": rate_hz, "steps": args.serve_steps,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "solves_per_s": len(reqs) / (t_end - t_start), "fwd_bwd_mpix_s": px / (t_end - t_start) / 1e6,
-            "views_per_iteration": st["views_per_iteration"],
+            "views_per_iteration": st["views_per_iteration"], "max_active": st["max_active"],
+            "admission_budget_gb": st["budget_bytes"] / 1e9, "requeued": st["requeued"],
             "failed": int(sum(1 for x in res if x["status"] != 0))}
 
 
@@ -749,7 +786,7 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # ncu capture of the current kernel on the 4-view small case, scaled to a launch by
 # the run's units; re-measure when the kernel changes.
 # k_blend_bwd<2, 0>: 35,698,176 B for 852,644 list entries read, 4 views at 1M Gaussians.
-TRAFFIC_PER_UNIT = {"blend_bwd": (41.87, 5)}
+TRAFFIC_PER_UNIT = {}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, alu, sm_mhz):

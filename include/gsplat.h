@@ -401,7 +401,11 @@ typedef struct {
     int32_t max_slots;        /* solves batched per iteration (1 = one solve at a time) */
     int32_t max_width;        /* largest accepted query image */
     int32_t max_height;
-    int64_t mem_budget;       /* device bytes the active solves' working set may use (0: no limit) */
+    int64_t mem_budget;       /* admission by memory: 0 (default) admits while the modelled working
+                                 set of the batch fits the device memory that is free (queried before
+                                 each admission) plus what the server's workspaces hold, less a
+                                 reserve of max(256 MiB, 2% of the device); > 0 also caps it at this
+                                 many bytes; < 0 admits without a memory check */
     int32_t queue_capacity;   /* pending requests beyond which submit returns GS_EBUSY */
     float mask_alpha;         /* 0: plain L1; > 0: confidence-masked L1 (GS_LOSS_L1_MASKED)
                                  with this accumulated-alpha threshold (the paper uses 0.99) */
@@ -430,6 +434,9 @@ typedef struct {
     int64_t submitted, completed, failed, iterations, active, queued;
     double busy_ms;           /* wall time spent in iterations */
     double views_per_iteration; /* mean batch size */
+    int64_t max_active;       /* largest batch so far */
+    int64_t budget_bytes;     /* working-set limit at the last admission decision (-1: none) */
+    int64_t requeued;         /* admitted requests put back in the queue after GS_ENOMEM */
 } gs_server_stats;
 
 /* Starts a server on `scene` (which must outlive it).  The server owns its own
@@ -449,6 +456,10 @@ int gs_solve_cancel(gs_server* srv, uint64_t ticket);
 int gs_server_stats_get(gs_server* srv, gs_server_stats* out);
 /* Stops the worker (running solves end with GS_EBUSY) and frees the server. */
 void gs_server_destroy(gs_server* srv);
+/* Test hook for the out-of-memory path, made on the host: the next
+ * `iterations` iterations report GS_ENOMEM before any device work, as a failed
+ * workspace growth would, so their new solves go back to the queue. */
+int gs_server_inject_enomem(gs_server* srv, int iterations);
 
 /* Synchronises `stream`, returns and clears the context's device status word
  * (GS_OK, GS_EOVERFLOW from a GS_F_NO_SYNC call, ...). */

@@ -30,7 +30,7 @@ EXPORTED = (
     "gs_gaussian_adam", "gs_server_create", "gs_solve_submit", "gs_solve_poll", "gs_solve_wait", "gs_solve_cancel",
     "gs_server_stats_get", "gs_server_destroy", "gs_ctx_set_tuning", "gs_ctx_get_tuning", "gs_autotune",
     "gs_pose_step_txso3", "gs_regularize", "gs_prune_threshold", "gs_compact", "gs_unproject", "gs_knn_mean_dist",
-    "gs_init_from_points", "gs_spatial_order", "gs_gather_rows", "gs_measure_alu_peaks",
+    "gs_init_from_points", "gs_spatial_order", "gs_gather_rows", "gs_measure_alu_peaks", "gs_server_inject_enomem",
 )
 GS_POSE_SE3, GS_POSE_TXSO3 = 0, 1
 
@@ -106,7 +106,8 @@ class gs_alu_peaks(C.Structure):
 class gs_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("iterations", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64), ("busy_ms", C.c_double),
-                ("views_per_iteration", C.c_double)]
+                ("views_per_iteration", C.c_double), ("max_active", C.c_int64), ("budget_bytes", C.c_int64),
+                ("requeued", C.c_int64)]
 
 
 _lib = None
@@ -488,6 +489,15 @@ def gs_server_stats_get(srv: int) -> dict:
 
 def gs_server_destroy(srv: int) -> None:
     load().gs_server_destroy(C.c_void_p(srv))
+
+
+def gs_server_inject_enomem(srv: int, iterations: int) -> None:
+    """Test hook: the next `iterations` server iterations fail as a workspace
+    growth would (GS_ENOMEM), made on the host."""
+    L = load()
+    L.gs_server_inject_enomem.argtypes = [C.c_void_p, C.c_int]
+    L.gs_server_inject_enomem.restype = C.c_int
+    _ck(L.gs_server_inject_enomem(C.c_void_p(srv), int(iterations)))
 
 
 def gs_ctx_set_tuning(ctx: int, scatter_chunk: int, sort_chunk: int, preprocess_threads: int,

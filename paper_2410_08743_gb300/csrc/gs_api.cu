@@ -1581,3 +1581,17 @@ int gs::scene_count(const gs_scene* scene) { return scene ? scene->d.n : 0; }
 
 uint32_t gs::frames_num_keys(const gs_frames* fr) { return fr ? fr->n_keys : 0u; }
 
+size_t gs::frames_device_bytes(const gs_frames* fr) {
+    if (!fr) return 0;
+    size_t b = 0;
+    auto add = [&](const auto& buf) { b += buf.cap * sizeof(*buf.p); };
+    add(fr->A); add(fr->B); add(fr->gA); add(fr->gB); add(fr->Cb); add(fr->depth); add(fr->gC); add(fr->rect);
+    add(fr->Mlo); add(fr->radius); add(fr->counts); add(fr->starts); add(fr->cursor); add(fr->scan_tmp);
+    add(fr->sort_lists); add(fr->sort_counters); add(fr->sorted_count); add(fr->tile_loss); add(fr->keys);
+    add(fr->tmp_keys); add(fr->sorted_idx); add(fr->T_final); add(fr->n_contrib); add(fr->pose_partials);
+    add(fr->dldc_ssim); add(fr->ssim_tmp); add(fr->img_off_dev); add(fr->loss_tmp); add(fr->counters);
+    add(fr->st_params); add(fr->st_target); add(fr->st_image); add(fr->st_grads); add(fr->st_poses);
+    add(fr->st_pose_grad); add(fr->st_loss);
+    return b;
+}
+

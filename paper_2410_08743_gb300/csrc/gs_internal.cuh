@@ -233,6 +233,8 @@ int set_error(int code, const char* msg);
 // Accessors of the opaque ABI objects (gs_api.cu).
 int scene_count(const gs_scene* scene);
 uint32_t frames_num_keys(const gs_frames* fr);
+// Device bytes the frames' workspaces hold (they grow on demand and are kept).
+size_t frames_device_bytes(const gs_frames* fr);
 
 // Slices of the Gaussians for a step whose parameters arrive from and whose
 // gradients return to host memory: the forward preprocess of slice c waits

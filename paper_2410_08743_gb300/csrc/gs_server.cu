@@ -4,10 +4,15 @@
 //
 // A worker thread owns a private context, stream and forward state.  Each
 // iteration it (1) admits queued requests into free slots while the modelled
-// device working set stays within the memory budget, (2) runs ONE batched
+// device working set of the batch fits the memory the server may use (by
+// default the device memory that is free, plus what its workspaces already
+// hold, less a reserve; queried before each admission), (2) runs ONE batched
 // forward + L1 + pose-only backward + per-slot Adam step over every active
-// solve, and (3) completes the solves whose step count is reached.  Query
-// images, poses and Adam moments stay on the device in fixed per-slot
+// solve, and (3) completes the solves whose step count is reached.  If the
+// workspaces cannot grow (GS_ENOMEM), the requests admitted for that
+// iteration go back to the head of the queue and the iteration runs without
+// them; a running solve that no longer fits goes back too and restarts later.
+// Query images, poses and Adam moments stay on the device in fixed per-slot
 // storage; only the batch bookkeeping (which slot is view k, its step and
 // learning rate) is uploaded per iteration.
 #include <cuda_runtime.h>
@@ -44,6 +49,7 @@ struct Req {
     double lr0 = 0.0, lr1 = 0.0;
     int slot = -1;
     int done_steps = 0;
+    int enomem = 0;          // consecutive iterations that failed to grow the workspaces with it alone
     bool finished = false;
     bool cancelled = false;
     int status = GS_OK;
@@ -95,21 +101,51 @@ struct gs_server {
     gs_server_stats st{};
     double views_sum = 0.0;
     double keys_per_pixel = 30.0;  // running estimate for the memory model
+    double model_scale = 1.0;      // raised after a failed growth, decays back
+    int inject_enomem = 0;         // test hook: iterations that report GS_ENOMEM before any device work
 };
 
 static int srv_fail(int code, const char* msg) { return gs::set_error(code, msg); }
 
 // Modelled device bytes of a batch: per view the per-(view, Gaussian) splat
-// and 2D-gradient records, per pixel the keys (three arrays) and the
-// per-pixel state.
+// and 2D-gradient records (96 B), per pixel the keys (20 B each in three
+// arrays, at the running keys-per-pixel estimate) and the per-pixel state
+// (8 B); workspaces grow by a quarter beyond the request.
 static double model_bytes(const gs_server* s, const std::vector<const gs_view*>& views) {
     double b = 0.0;
     const double n = (double)gs::scene_count(s->scene);
     for (const gs_view* v : views) {
         const double px = (double)v->width * v->height;
-        b += n * 88.0 + s->keys_per_pixel * px * 20.0 + px * 8.0;
+        b += n * 96.0 + s->keys_per_pixel * px * 20.0 + px * 8.0;
     }
-    return b;
+    return 1.25 * s->model_scale * b;
+}
+
+// Bytes the batch's working set may occupy: the configured budget, and unless
+// the budget is negative (no limit) at most what the workspaces hold plus the
+// device memory that is free now, less a reserve of max(256 MiB, 2% of the
+// device) for everything else on it.
+static double admission_limit(gs_server* s) {
+    if (s->cfg.mem_budget < 0) return 1e300;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return s->cfg.mem_budget > 0 ? (double)s->cfg.mem_budget : 1e300;
+    }
+    const double reserve = std::max(256.0 * (1 << 20), 0.02 * (double)total_b);
+    const double avail = std::max(0.0, (double)gs::frames_device_bytes(s->fr) + (double)free_b - reserve);
+    return s->cfg.mem_budget > 0 ? std::min((double)s->cfg.mem_budget, avail) : avail;
+}
+
+// Puts an admitted request back at the head of the queue (its slot freed);
+// it restarts from its initial pose when admitted again.
+static void requeue_locked(gs_server* s, Req* r) {
+    if (r->slot >= 0 && r->slot < (int)s->slots.size() && s->slots[r->slot] == r) s->slots[r->slot] = nullptr;
+    r->slot = -1;
+    r->done_steps = 0;
+    r->t_admit = Clock::time_point{};
+    s->queue.push_front(r);
+    s->st.requeued++;
 }
 
 static void finish_locked(gs_server* s, Req* r, int status) {
@@ -138,6 +174,8 @@ static void worker_main(gs_server* s) {
             std::vector<const gs_view*> act;
             for (int k = 0; k < S; k++)
                 if (s->slots[k]) act.push_back(&s->slots[k]->view);
+            double limit = 0.0;
+            bool have_limit = false;
             while (!s->queue.empty()) {
                 Req* r = s->queue.front();
                 if (r->cancelled) {
@@ -149,8 +187,15 @@ static void worker_main(gs_server* s) {
                 for (int k = 0; k < S; k++)
                     if (!s->slots[k]) { free_slot = k; break; }
                 if (free_slot < 0) break;
+                if (!have_limit) {
+                    limit = admission_limit(s);
+                    have_limit = true;
+                    s->st.budget_bytes = limit >= 1e299 ? -1 : (int64_t)limit;
+                }
                 act.push_back(&r->view);
-                if (s->cfg.mem_budget > 0 && act.size() > 1 && model_bytes(s, act) > (double)s->cfg.mem_budget) {
+                // the first solve is always admitted (its growth may still fail
+                // and send it back); later ones wait until the batch fits
+                if (act.size() > 1 && model_bytes(s, act) > limit) {
                     act.pop_back();
                     break;
                 }
@@ -172,6 +217,7 @@ static void worker_main(gs_server* s) {
             for (int k = 0; k < S; k++)
                 if (s->slots[k]) batch.push_back(s->slots[k]);
             s->st.active = (int64_t)batch.size();
+            s->st.max_active = std::max(s->st.max_active, s->st.active);
         }
         const Clock::time_point t0 = Clock::now();
         int rc = GS_OK;
@@ -204,6 +250,10 @@ static void worker_main(gs_server* s) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_steps, s->h_steps, sizeof(int) * A, cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_lrs, s->h_lrs, sizeof(double) * A, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) rc = GS_ECUDA;
+        if (rc == GS_OK && s->inject_enomem > 0) {
+            s->inject_enomem--;
+            rc = gs::set_error(GS_ENOMEM, "server: injected workspace growth failure");
+        }
         if (rc == GS_OK) {
             gs::launch_gather_poses(A, s->d_slot_of, s->d_pose_slot, s->d_pose_packed, s->stream);
             rc = gs::render_forward_impl(s->ctx, s->scene, A, views.data(), offs.data(), s->d_pose_packed, &s->opts,
@@ -235,6 +285,32 @@ static void worker_main(gs_server* s) {
         } else {
             cudaStreamSynchronize(s->stream);
         }
+        if (rc == GS_ENOMEM) {
+            // the workspaces could not grow: this iteration's new solves go back
+            // to the queue; without new ones, the most recently admitted running
+            // solve does; a solve that fails alone three times in a row fails
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->model_scale = std::min(8.0, s->model_scale * 1.25);
+                if (A == 1) {
+                    if (++batch[0]->enomem >= 3) finish_locked(s, batch[0], GS_ENOMEM);
+                    else requeue_locked(s, batch[0]);
+                } else if (!fresh.empty()) {
+                    for (auto it = fresh.rbegin(); it != fresh.rend(); ++it) requeue_locked(s, *it);
+                } else {
+                    Req* last = batch[0];
+                    for (Req* r : batch)
+                        if (r->t_admit > last->t_admit) last = r;
+                    requeue_locked(s, last);
+                }
+                s->st.queued = (int64_t)s->queue.size();
+                s->st.busy_ms += ms_between(t0, Clock::now());
+            }
+            s->cv_done.notify_all();
+            std::this_thread::sleep_for(std::chrono::milliseconds(5));   // let memory come free
+            continue;
+        }
+        s->model_scale = std::max(1.0, s->model_scale * 0.98);
         uint32_t nk = gs::frames_num_keys(s->fr);
         double px = 0.0;
         for (const gs_view& v : views) px += (double)v.width * v.height;
@@ -251,6 +327,7 @@ static void worker_main(gs_server* s) {
                     continue;
                 }
                 r->done_steps++;
+                r->enomem = 0;
                 r->loss = s->h_loss[k];
                 if (r->done_steps >= r->steps) {
                     memcpy(r->pose, s->h_pose + 12 * (size_t)r->slot, sizeof(r->pose));
@@ -394,6 +471,16 @@ int gs_solve_cancel(gs_server* s, uint64_t ticket) {
         auto it = s->reqs.find(ticket);
         if (it == s->reqs.end()) return srv_fail(GS_EINVAL, "gs_solve_cancel: unknown ticket");
         it->second->cancelled = true;
+    }
+    s->cv.notify_one();
+    return GS_OK;
+}
+
+int gs_server_inject_enomem(gs_server* s, int iterations) {
+    if (!s || iterations < 0) return srv_fail(GS_EINVAL, "gs_server_inject_enomem: bad argument");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->inject_enomem = iterations;
     }
     s->cv.notify_one();
     return GS_OK;

@@ -49,8 +49,9 @@ def test_roofline_arithmetic():
     assert r["achieved"] == pytest.approx(ops / 1e-3 / 1e12)
     assert r["peak"] == pytest.approx(120.0 * 152 * 2000e6 / 1e12)
     assert r["mufu_frac"] == pytest.approx((1_000_000 + 500_000) / 1e-3 / (30.0 * 152 * 2000e6))
-    tr = bench.TRAFFIC_PER_UNIT["blend_bwd"]
-    assert r["traffic"] == pytest.approx(tr[0] * c[tr[1]])
+    tr = bench.TRAFFIC_PER_UNIT.get("blend_bwd")
+    # traffic: DRAM bytes per unit from a capture of the kernel as it stands, else null
+    assert r["traffic"] == (pytest.approx(tr[0] * c[tr[1]]) if tr else None)
     assert "2000 MHz" in r["peak_source"] and "of measured" in r["peak_source"]
     # HBM kernels: algorithmic bytes (visible pairs counted apart) over time
     n, V, n_vis = 1000, 4, 1500

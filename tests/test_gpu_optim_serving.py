@@ -162,6 +162,84 @@ def test_server_admission_by_memory_budget(R):
     assert st["completed"] == 4
 
 
+def test_server_admission_by_free_device_memory(R):
+    """With the default budget the server admits solves while the modelled
+    working set of the batch fits the device memory that is free (less a
+    reserve): with most of the device taken by another allocation, a burst of
+    requests is served a few at a time, none fails, and each result equals the
+    same solve run alone."""
+    sc = synth.make_scene_box(55, 1_000_000, sh_degree=1, lo=(-1.5, -1.2, 3.0), hi=(1.5, 1.2, 6.0))
+    p = to_dev(sc)
+    rng = np.random.default_rng(55)
+    reqs = []
+    for k in range(12):
+        view = synth.intrinsics(504, 378)
+        gt = synth.pose_from_center(synth.yaw_pitch(rng.uniform(-3, 3), rng.uniform(-3, 3)),
+                                    np.array([rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1), 0.0]))
+        img = R.forward(p, [view], poses_dev(gt[None])).cpu().numpy().copy()
+        reqs.append(dict(view=view, image=img, init=synth.perturb_normal(rng, gt, 2.0, 0.02)))
+    steps = 4
+    sh, srv = _server(p, sc, 1, maxw=504, maxh=378)
+    try:                                    # reference: the first solve alone
+        alone = L.gs_solve_wait(srv, L.gs_solve_submit(srv, reqs[0]["view"], reqs[0]["image"], reqs[0]["init"],
+                                                       steps, 1e-2, 1e-3), 120000)
+    finally:
+        L.gs_server_destroy(srv)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info()
+    reserve = max(256 << 20, int(0.02 * total))
+    # leave the reserve plus about 1.5 GB: room for a handful of these views
+    # (each about 0.25 GB modelled) but not for twelve
+    take = free - reserve - (1536 << 20)
+    filler = torch.empty(max(0, take), dtype=torch.uint8, device=DEV) if take > 0 else None
+    srv = None
+    try:
+        free1, _ = torch.cuda.mem_get_info()
+        srv = L.gs_server_create(0, sh, L.gs_default_opts(), 12, 504, 378, 0, 1024)
+        ts = [L.gs_solve_submit(srv, r["view"], r["image"], r["init"], steps, 1e-2, 1e-3) for r in reqs]
+        out = [L.gs_solve_wait(srv, t, 300000) for t in ts]
+        st = L.gs_server_stats_get(srv)
+    finally:
+        if srv:
+            L.gs_server_destroy(srv)
+        L.gs_scene_free(sh)
+        del filler
+        torch.cuda.empty_cache()
+    assert all(o["status"] == 0 for o in out), [o["status"] for o in out]
+    assert 2 <= st["max_active"] < 12, st
+    assert 0 < st["budget_bytes"] <= free1, (st["budget_bytes"], free1)
+    np.testing.assert_allclose(np.array(out[0]["pose"]), np.array(alone["pose"]), atol=1e-5)
+
+
+def test_server_requeues_solves_when_workspaces_cannot_grow(R):
+    """A failed workspace growth (GS_ENOMEM, injected on the host) sends the
+    iteration's new solves back to the queue; they finish later with the
+    results of an undisturbed run.  A solve that fails alone three times in a
+    row ends with GS_ENOMEM."""
+    sc, p, reqs = _scene_and_targets(R, 3, seed=56)
+    steps = 6
+    sh, srv = _server(p, sc, 4)
+    try:
+        ref = [L.gs_solve_wait(srv, L.gs_solve_submit(srv, r["view"], r["image"], r["init"], steps, 1e-2, 1e-3),
+                               60000) for r in reqs]
+        L.gs_server_inject_enomem(srv, 2)
+        ts = [L.gs_solve_submit(srv, r["view"], r["image"], r["init"], steps, 1e-2, 1e-3) for r in reqs]
+        out = [L.gs_solve_wait(srv, t, 60000) for t in ts]
+        st = L.gs_server_stats_get(srv)
+        L.gs_server_inject_enomem(srv, 3)
+        lone = L.gs_solve_wait(srv, L.gs_solve_submit(srv, reqs[0]["view"], reqs[0]["image"], reqs[0]["init"],
+                                                      steps, 1e-2, 1e-3), 60000)
+    finally:
+        L.gs_server_destroy(srv)
+        L.gs_scene_free(sh)
+    assert all(o["status"] == 0 and o["steps_done"] == steps for o in out)
+    assert st["requeued"] >= 1 and st["failed"] == 0
+    for a, b in zip(out, ref):
+        np.testing.assert_allclose(np.array(a["pose"]), np.array(b["pose"]), atol=1e-5)
+    assert lone["status"] == L.GS_ENOMEM
+
+
 def test_server_errors_cancel_and_timeout(R):
     sc, p, reqs = _scene_and_targets(R, 3, seed=54)
     sh, srv = _server(p, sc, 1, maxw=160, maxh=120, qcap=1)
