@@ -465,10 +465,12 @@ def run_gpu(args):
         serving = run_serving(p, dev, args, 64, tuning=tt)
         serving["plain"] = run_serving(p, dev, args, 1, tuning=tt)
         sweep, best = [], None
-        for rate in (4.0, 8.0, 12.0, 16.0, 20.0, 24.0, 32.0):
-            n_req = int(max(24, 3.0 * rate))
+        for rate in (4.0, 8.0, 12.0, 16.0, 20.0, 24.0, 32.0, 40.0):
+            # about 5 s of arrivals: beyond capacity the backlog then lifts p99
+            # above 1 s; within it, latency stays near one solve's time
+            n_req = int(max(24, 5.0 * rate))
             r_ = run_serving(p, dev, args, 64, rate_hz=rate, n_requests=n_req, tuning=tt)
-            ok = r_["solves_per_s"] >= 0.9 * rate and r_["p99_ms"] <= 1000.0
+            ok = r_["p99_ms"] <= 1000.0 and r_["failed"] == 0
             sweep.append({k: r_[k] for k in ("rate_hz", "requests", "p50_ms", "p99_ms", "solves_per_s")} |
                          {"sustained": ok})
             if not ok:

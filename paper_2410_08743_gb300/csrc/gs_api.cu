@@ -216,6 +216,8 @@ struct gs_frames {
     DevBuf<int> radius;
     // per tile
     DevBuf<uint32_t> counts, starts, cursor, scan_tmp, sort_lists, sort_counters, sorted_count;
+    DevBuf<uint2> cta_lists;          // per (view, chunk) CTA: (tile, offset) of its keys in the tile
+    DevBuf<uint32_t> cta_list_len;
     bool full_sort = false;           // the last forward sorted whole lists
     DevBuf<float> tile_loss;
     // per key
@@ -251,6 +253,7 @@ struct gs_frames {
         DevBuf<float>* f1[] = {&Cb, &depth, &gC, &tile_loss, &T_final, &dldc_ssim, &ssim_tmp};
         for (auto* b : f1) b->release();
         rect.release(); Mlo.release(); radius.release(); counts.release(); starts.release(); cursor.release(); scan_tmp.release();
+        cta_lists.release(); cta_list_len.release();
         sort_lists.release(); sort_counters.release(); sorted_count.release();
         keys.release(); tmp_keys.release(); sorted_idx.release(); n_contrib.release(); pose_partials.release();
         loss_tmp.release(); counters.release();
@@ -632,6 +635,12 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     SplatArrays sp = fr->splats();
     if ((rc = fr->counters.ensure(12, grow, "counters"))) return rc;
     {
+        const int chunk = ctx->tune.scatter_chunk;
+        if ((rc = fr->cta_lists.ensure(std::max<size_t>(gs::cta_list_entries(n, chunk, T), 1), grow, "CTA tile lists")) ||
+            (rc = fr->cta_list_len.ensure((size_t)((n + chunk - 1) / chunk) * n_views + 1, grow, "CTA list lengths")))
+            return rc;
+    }
+    {
         PROF(PK_SETUP, 1);
         gs::launch_setup_views(views, n_views, poses, fr->vdev.p, rp, s);
     }
@@ -668,7 +677,8 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     }
     {
         PROF(PK_COUNT_TILES, 1);
-        gs::launch_count_tiles(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp.rect, fr->counts.p, s);
+        gs::launch_count_tiles(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp.rect, fr->counts.p,
+                               fr->cta_lists.p, fr->cta_list_len.p, s);
     }
     CK_LAUNCH();
     if (opts->flags & GS_F_COUNT) {
@@ -690,7 +700,8 @@ int gs::render_forward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, con
     const uint32_t cap = (uint32_t)std::min<size_t>(fr->keys.cap, 0xffffffffu);
     {
         PROF(PK_SCATTER, 1);
-        gs::launch_scatter_keys(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p, fr->keys.p, cap,
+        gs::launch_scatter_keys(n, ctx->tune.scatter_chunk, n_views, fr->vdev.p, sp, fr->starts.p, fr->cursor.p,
+                                fr->cta_lists.p, fr->cta_list_len.p, fr->keys.p, cap,
                                 ctx->status, s);
     }
     CK_LAUNCH();
@@ -1588,6 +1599,7 @@ size_t gs::frames_device_bytes(const gs_frames* fr) {
     add(fr->A); add(fr->B); add(fr->gA); add(fr->gB); add(fr->Cb); add(fr->depth); add(fr->gC); add(fr->rect);
     add(fr->Mlo); add(fr->radius); add(fr->counts); add(fr->starts); add(fr->cursor); add(fr->scan_tmp);
     add(fr->sort_lists); add(fr->sort_counters); add(fr->sorted_count); add(fr->tile_loss); add(fr->keys);
+    add(fr->cta_lists); add(fr->cta_list_len);
     add(fr->tmp_keys); add(fr->sorted_idx); add(fr->T_final); add(fr->n_contrib); add(fr->pose_partials);
     add(fr->dldc_ssim); add(fr->ssim_tmp); add(fr->img_off_dev); add(fr->loss_tmp); add(fr->counters);
     add(fr->st_params); add(fr->st_target); add(fr->st_image); add(fr->st_grads); add(fr->st_poses);

@@ -121,11 +121,17 @@ void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const V
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int n, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t scan_tmp_bytes(int n);
 
+// Per-CTA (tile, offset) lists of the count pass, read back by the scatter
+// pass of the same chunking: entries needed for n Gaussians in chunks of
+// `chunk` over views with total_tiles tiles; plus one length per (view, chunk).
+size_t cta_list_entries(int n, int chunk, int total_tiles);
+
 void launch_scatter_keys(int n, int chunk, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
-                         uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s);
+                         uint32_t* cursor, const uint2* cta_lists, const uint32_t* cta_list_len,
+                         unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s);
 
 void launch_count_tiles(int n, int chunk, int n_views, const ViewDev* views, const uint2* rect,
-                        uint32_t* tile_counts, cudaStream_t s);
+                        uint32_t* tile_counts, uint2* cta_lists, uint32_t* cta_list_len, cudaStream_t s);
 
 // lists: [3][n_tiles] work lists; counters: 6 words (list lengths, work cursors)
 void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys,

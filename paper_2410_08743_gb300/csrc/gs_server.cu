@@ -110,13 +110,15 @@ static int srv_fail(int code, const char* msg) { return gs::set_error(code, msg)
 // Modelled device bytes of a batch: per view the per-(view, Gaussian) splat
 // and 2D-gradient records (96 B), per pixel the keys (20 B each in three
 // arrays, at the running keys-per-pixel estimate) and the per-pixel state
-// (8 B); workspaces grow by a quarter beyond the request.
+// (8 B), per (chunk of 1024 Gaussians, tile) the key pass's 8 B CTA list
+// entry; workspaces grow by a quarter beyond the request.
 static double model_bytes(const gs_server* s, const std::vector<const gs_view*>& views) {
     double b = 0.0;
     const double n = (double)gs::scene_count(s->scene);
     for (const gs_view* v : views) {
         const double px = (double)v->width * v->height;
-        b += n * 96.0 + s->keys_per_pixel * px * 20.0 + px * 8.0;
+        const double tiles = (double)((v->width + 15) / 16) * (double)((v->height + 15) / 16);
+        b += n * 96.0 + s->keys_per_pixel * px * 20.0 + px * 8.0 + std::ceil(n / 1024.0) * tiles * 8.0;
     }
     return 1.25 * s->model_scale * b;
 }

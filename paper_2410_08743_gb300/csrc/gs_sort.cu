@@ -131,13 +131,16 @@ void launch_count_visible(size_t vn, const uint2* rect, unsigned long long* coun
 }
 
 // ------------------------------------------------------------ count + scatter
-// One CTA per (view, chunk of `chunk` Gaussians; a tuning knob).  The CTA first builds a
-// shared-memory histogram of its keys over the view's tiles, so that global
-// atomics go per (CTA, tile) instead of per key:
-//   count:   tile_counts[t] += hist[t]
-//   scatter: base = cursor[t] += hist[t]; each key takes starts[t] + base + a
-//            shared-memory slot.
-// Views with more than SMEM_TILES tiles fall back to one global atomic per key.
+// One CTA per (view, chunk of `chunk` Gaussians; a tuning knob).  The count
+// CTA builds a shared-memory histogram of its keys over the view's tiles and
+// reserves its range in every touched tile with one global atomic per (CTA,
+// tile): tile_counts[t] += hist[t] returns the CTA's offset inside tile t,
+// which it records as (t, offset) in its own list.  After the scan of the
+// counts, the scatter CTA of the same chunk loads that list as its per-tile
+// cursors (starts[t] + offset) and places each key with a shared-memory
+// atomic: it neither rebuilds the histogram nor touches a global counter.
+// Views with more than SMEM_TILES tiles use one global atomic per key in both
+// passes instead (a per-tile cursor).
 #define SMEM_TILES 8192
 #define CS_THREADS 256
 
@@ -169,10 +172,19 @@ __device__ __forceinline__ void chunk_histogram(const uint2* __restrict__ rect, 
     }
 }
 
+// First entry of the (tile, offset) list of the CTA of chunk c of view v: the
+// lists of view v hold n_chunks * ntile(v) entries from n_chunks * tile_base(v).
+__device__ __forceinline__ size_t cta_list_base(int n_chunks, int tile_base, int chunk_idx, int ntile) {
+    return (size_t)n_chunks * (size_t)tile_base + (size_t)chunk_idx * (size_t)ntile;
+}
+
 __global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, int chunk, const ViewDev* __restrict__ views,
                                                            const uint2* __restrict__ rect,
-                                                           uint32_t* __restrict__ tile_counts) {
+                                                           uint32_t* __restrict__ tile_counts,
+                                                           uint2* __restrict__ cta_lists,
+                                                           uint32_t* __restrict__ cta_list_len) {
     __shared__ uint32_t hist[SMEM_TILES];
+    __shared__ uint32_t s_len;
     const int v = blockIdx.y;
     const int gw = views[v].gw, ntile = gw * views[v].gh, tb = views[v].tile_base;
     const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -187,11 +199,27 @@ __global__ void __launch_bounds__(CS_THREADS) k_count_tiles(int n, int chunk, co
         return;
     }
     for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
+    if (threadIdx.x == 0) s_len = 0u;
     __syncthreads();
     chunk_histogram(rect, vb, i0, i1, gw, hist);
     __syncthreads();
-    for (int t = threadIdx.x; t < ntile; t += CS_THREADS)
-        if (hist[t]) atomicAdd(tile_counts + tb + t, hist[t]);
+    // reserve the CTA's range in each touched tile; record (tile, offset)
+    uint2* list = cta_lists + cta_list_base(gridDim.x, tb, blockIdx.x, ntile);
+    const int lane = threadIdx.x & 31;
+    for (int t0 = 0; t0 < ntile; t0 += CS_THREADS) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t c = t < ntile ? hist[t] : 0u;
+        const unsigned m = __ballot_sync(0xffffffffu, c != 0u);
+        uint32_t w = 0u;
+        if (lane == 0 && m) w = atomicAdd(&s_len, (uint32_t)__popc(m));
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (c) {
+            const uint32_t off = atomicAdd(tile_counts + tb + t, c);
+            list[w + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)t, off);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cta_list_len[(size_t)v * gridDim.x + blockIdx.x] = s_len;
 }
 
 __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, const ViewDev* __restrict__ views,
@@ -199,6 +227,8 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, 
                                                              const float* __restrict__ depth,
                                                              const uint32_t* __restrict__ starts,
                                                              uint32_t* __restrict__ cursor,
+                                                             const uint2* __restrict__ cta_lists,
+                                                             const uint32_t* __restrict__ cta_list_len,
                                                              unsigned long long* __restrict__ keys, uint32_t cap,
                                                              int* __restrict__ status) {
     __shared__ uint32_t hist[SMEM_TILES];
@@ -226,14 +256,14 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, 
         if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
         return;
     }
-    for (int t = threadIdx.x; t < ntile; t += CS_THREADS) hist[t] = 0u;
-    __syncthreads();
-    chunk_histogram(rect, vb, i0, i1, gw, hist);
-    __syncthreads();
-    // reserve this CTA's range in every touched tile
-    for (int t = threadIdx.x; t < ntile; t += CS_THREADS) {
-        const uint32_t c = hist[t];
-        if (c) hist[t] = starts[tb + t] + atomicAdd(cursor + tb + t, c);
+    // this CTA's cursor in every tile it touches (the tiles its keys go to)
+    {
+        const uint2* list = cta_lists + cta_list_base(gridDim.x, tb, blockIdx.x, ntile);
+        const uint32_t len = cta_list_len[(size_t)v * gridDim.x + blockIdx.x];
+        for (uint32_t k = threadIdx.x; k < len; k += CS_THREADS) {
+            const uint2 e = list[k];
+            hist[e.x] = starts[tb + e.x] + e.y;
+        }
     }
     __syncthreads();
     for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS * CS_PREFETCH) {
@@ -262,18 +292,24 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, 
     if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
 }
 
+size_t cta_list_entries(int n, int chunk, int total_tiles) {
+    return (size_t)((n + chunk - 1) / chunk) * (size_t)total_tiles;
+}
+
 void launch_count_tiles(int n, int chunk, int n_views, const ViewDev* views, const uint2* rect, uint32_t* tile_counts,
-                        cudaStream_t s) {
+                        uint2* cta_lists, uint32_t* cta_list_len, cudaStream_t s) {
     if (n <= 0 || n_views <= 0) return;
     dim3 grid((n + chunk - 1) / chunk, n_views);
-    k_count_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, rect, tile_counts);
+    k_count_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, rect, tile_counts, cta_lists, cta_list_len);
 }
 
 void launch_scatter_keys(int n, int chunk, int n_views, const ViewDev* views, SplatArrays sp, const uint32_t* starts,
-                         uint32_t* cursor, unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s) {
+                         uint32_t* cursor, const uint2* cta_lists, const uint32_t* cta_list_len,
+                         unsigned long long* keys, uint32_t cap, int* status, cudaStream_t s) {
     if (n <= 0 || n_views <= 0) return;
     dim3 grid((n + chunk - 1) / chunk, n_views);
-    k_scatter_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, sp.rect, sp.depth, starts, cursor, keys, cap, status);
+    k_scatter_tiles<<<grid, CS_THREADS, 0, s>>>(n, chunk, views, sp.rect, sp.depth, starts, cursor, cta_lists,
+                                                cta_list_len, keys, cap, status);
 }
 
 // ------------------------------------------------------------ segment sort
