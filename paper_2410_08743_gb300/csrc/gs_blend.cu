@@ -789,12 +789,6 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         fpy[q] = (float)(ly + WARP_H * q);
     }
     const float amin = rp.alpha_min, amax = rp.alpha_max;
-    // list positions at or beyond this warp's longest prefix concern only other warps
-    uint32_t warp_last = 0;
-#pragma unroll
-    for (int q = 0; q < PX; q++) warp_last = max(warp_last, plast[q]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
@@ -812,8 +806,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         for (int q = threadIdx.x; q < BATCH * 9; q += NT) s_acc[q] = 0.0f;
         __syncthreads();
         unsigned char* wl = s_wl[wid];
-        const int cnt_w = min(cnt, max(0, (int)warp_last - bstart));
-        const int nw = warp_compact(sb, cnt_w, (float)wx0, (float)wy0, wl, WARP_H * PX);
+        const int nw = warp_compact(sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
         for (int qq = nw - 1; qq >= 0; qq--) {
             const int jj = wl[qq];
             const uint32_t pos = (uint32_t)(bstart + jj);
