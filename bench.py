@@ -132,6 +132,33 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_fallback": True}
 
 
+def _bind_to_gpu_local_cpus(device: int) -> str:
+    """Restricts the process to the CPUs the GPU's PCI device lists as local
+    (sysfs local_cpulist), if that is a proper subset of the allowed CPUs, so
+    that pinned host memory allocated afterwards is first touched on the
+    nearby memory.  Returns what was done."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(device)
+        bdf = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        txt = open(f"/sys/bus/pci/devices/{bdf}/local_cpulist").read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        allowed = os.sched_getaffinity(0)
+        use = cpus & allowed
+        if use and use != allowed:
+            os.sched_setaffinity(0, use)
+            return f"bound to {len(use)} of {len(allowed)} CPUs local to GPU {bdf}"
+        return f"unchanged ({len(use)} of {len(allowed)} allowed CPUs local to GPU {bdf})"
+    except Exception as e:  # report, do not hide
+        return f"unchanged ({type(e).__name__})"
+
+
 # ------------------------------------------------------------------ workload
 def _workload(args, rank: int):
     from paper_2410_08743_gb300 import synth
@@ -407,6 +434,9 @@ def run_gpu(args):
     # ---- end to end through gs_step with host buffers
     e2e = None
     if not args.no_e2e:
+        # pinned host buffers on the memory next to this GPU: the process runs
+        # on the GPU's local cores while they are first touched
+        host_aff = _bind_to_gpu_local_cpus(local)
         r.set_flags(L.GS_F_HOST_IO)
         hp = {k: p[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
         hposes = torch.from_numpy(poses).pin_memory()
@@ -426,12 +456,31 @@ def run_gpu(args):
         e2e_step()
         torch.cuda.synchronize()
         r.set_flags(L.GS_F_HOST_IO | L.GS_F_NO_SYNC)
-        ems = timed(e2e_step, max(1, K // 2))
+        # K back-to-back steps with an event at every step boundary: the value
+        # is the median step, the mean and the spread are reported beside it
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        evs[0].record(stream)
+        for k_ in range(K):
+            e2e_step()
+            evs[k_ + 1].record(stream)
+        torch.cuda.synchronize()
+        step_ms = [evs[k_].elapsed_time(evs[k_ + 1]) for k_ in range(K)]
+        med = float(np.median(step_ms))
+        if world > 1:
+            t = torch.tensor([med], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            med = float(t.item())
         L.gs_status(r.ctx)
         h2d = sum(t.numel() * t.element_size() for t in hp.values()) + hposes.numel() * 8 + htgt.numel() * 4
         d2h = sum(t.numel() * t.element_size() for t in hg.values()) + hpg.numel() * 8 + hloss.numel() * 8
-        e2e = {"value": world * npix / (ems * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": world * npix / (med * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": K, "statistic": "median step",
+               "mean_value": world * npix / (float(np.mean(step_ms)) * 1e-3) / 1e6,
+               "step_ms": {"min": min(step_ms), "median": med, "max": max(step_ms)},
+               "host_affinity": host_aff}
         r.set_flags(L.GS_F_NO_SYNC)
 
     # ---- roofline of the dominant kernel
@@ -583,6 +632,25 @@ def run_extras(r, p, views, P, image, tgt, grads, pose_grad, npix, dev, K):
     pose_only(0)
     ms = _time_iters(pose_only, K)
     out["masked_l1_pose_only_mpix_s"] = npix / (ms / K * 1e-3) / 1e6
+    # the per-tile sort on its own: forwards that sort every tile's whole list
+    # in separate kernels (GS_F_FULL_SORT) beside the lazy forward, which sorts
+    # inside the blend only the prefixes the pixels consume
+    flags0 = r.opts.flags
+    prof = {}
+    for name, fl in (("lazy", 0), ("full_sort", L.GS_F_FULL_SORT)):
+        r.set_flags(L.GS_F_NO_SYNC | fl)
+        r.forward(p, views, P, image=image)
+        torch.cuda.synchronize()
+        L.gs_ctx_set_profiling(r.ctx, True)
+        L.gs_ctx_profile(r.ctx)
+        for _ in range(K):
+            r.forward(p, views, P, image=image)
+        prof[name] = L.gs_ctx_profile(r.ctx)
+        L.gs_ctx_set_profiling(r.ctx, False)
+    r.set_flags(flags0)
+    out["sort"] = {"full_sort_all_keys_ms": prof["full_sort"].get("segment_sort", (0.0, 1))[0] / K,
+                   "blend_fwd_after_full_sort_ms": prof["full_sort"]["blend_fwd"][0] / K,
+                   "blend_fwd_lazy_incl_sort_ms": prof["lazy"]["blend_fwd"][0] / K}
     m = torch.zeros(V, 6, dtype=torch.float64, device=dev); v = torch.zeros_like(m)
     Pc = P.clone()
     ms = _time_iters(lambda i: r.pose_step(Pc, m, v, pose_grad, 1e-4, i + 1, param=L.GS_POSE_TXSO3), 20)
