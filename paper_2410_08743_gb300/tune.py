@@ -44,6 +44,16 @@ def autotune(renderer, params: dict, views, poses, image, loss, grads=None, pose
         t = cache[key]["tuning"]
         L.gs_ctx_set_tuning(renderer.ctx, t["scatter_chunk"], t["sort_chunk"], t["preprocess_threads"],
                             t.get("bwd_pixels_per_thread", 1), t.get("fwd_pixels_per_thread", 1))
+        # one synchronising step with the new tuning grows the workspaces it
+        # needs (a GS_F_NO_SYNC call cannot), as the tuner's own trials would;
+        # like them it accumulates into grads / pose_grad
+        flags = renderer.opts.flags
+        renderer.set_flags(flags & ~L.GS_F_NO_SYNC)
+        try:
+            renderer.forward(params, views, poses, image=image)
+            renderer.backward(params, views, poses, image, loss, grads, pose_grad)
+        finally:
+            renderer.set_flags(flags)
         return dict(tuning=t, ms=cache[key]["ms"], cached=True, key=key)
     sc = L.gs_scene_borrow(params["means"], params["scales"], params["quats"], params["opac"], params["sh"],
                            params["sh_degree"])
