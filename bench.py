@@ -319,6 +319,8 @@ def run_gpu(args):
         if len(kv) != 5:
             raise SystemExit("--tuning wants five comma-separated integers")
         L.gs_ctx_set_tuning(r.ctx, **kv)
+        step()                       # grows the workspaces this tuning needs
+        torch.cuda.synchronize()
         tuned = dict(tuning=kv, ms=None, cached=False, fixed=True)
     else:
         tuned = tune.autotune(r, p, views, P, image, l1, grads, pose_grad, repeats=1)

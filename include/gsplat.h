@@ -312,6 +312,9 @@ typedef struct {
     int32_t fwd_pixels_per_thread;  /* forward blend: 1 or 2, likewise */
 } gs_tuning;
 
+/* A GS_F_NO_SYNC call after a tuning change needs workspaces grown by one
+ * synchronising call with the new tuning (a smaller scatter_chunk needs more
+ * per-CTA tile-list entries); otherwise it fails with GS_EOVERFLOW. */
 int gs_ctx_set_tuning(gs_ctx* ctx, const gs_tuning* t);
 int gs_ctx_get_tuning(gs_ctx* ctx, gs_tuning* t);
 
