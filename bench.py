@@ -855,10 +855,10 @@ OPS_FWD_EVAL, OPS_FWD_BLEND = 16, 7
 OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 
 # kernel -> (DRAM bytes, read + write, per unit; counter index of the unit) from one
-# ncu capture of the current kernel on the 4-view small case, scaled to a launch by
-# the run's units; re-measure when the kernel changes.
-# k_blend_bwd<2, 0>: 35,698,176 B for 852,644 list entries read, 4 views at 1M Gaussians.
-TRAFFIC_PER_UNIT = {}
+# ncu capture of the current kernel on the 16-view case, scaled to a launch by the
+# run's units; re-measure when the kernel changes.
+# k_blend_bwd<2, 0>: 218.4 MB for 4,860,428 list entries read, 16 views at 1M Gaussians.
+TRAFFIC_PER_UNIT = {"blend_bwd": (44.94, 5)}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, alu, sm_mhz):
