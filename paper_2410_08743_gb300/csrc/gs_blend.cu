@@ -34,13 +34,18 @@ struct SplatBatch {
 // of the alpha test), so a pixel outside the box is certainly skipped by
 // pair_alpha and the box changes no decision.  Conics with det < 1e-4 a c get
 // no box: there FP32 cancellation in det (relative error ~1e-7 a c / det)
-// could approach the 1% margin.
+// could approach the 1% margin.  The hardware approximations used here (log,
+// quotient, reciprocal square root) are off by a few units in the last place,
+// relatively far inside the 1% margin; R^2 gets 2e-6 more, above the
+// logarithm's absolute error near o = alpha_min.
 __device__ __forceinline__ float2 alpha_box(const float4 a, const float4 b, float amin) {
     if (!(b.y >= amin)) return make_float2(-1.0f, -1.0f);
-    const float R2 = 2.0f * logf(b.y / amin);
+    const float R2 = fmaf(2.0f, __logf(__fdividef(b.y, amin)), 2e-6f);
     const float dq = a.z * b.x - a.w * a.w;
     if (!(dq > 1e-4f * a.z * b.x)) return make_float2(INFINITY, INFINITY);
-    const float hx = sqrtf(R2 * b.x / dq), hy = sqrtf(R2 * a.z / dq);
+    const float s = __fdividef(R2, dq);
+    const float hx2 = s * b.x, hy2 = s * a.z;
+    const float hx = hx2 * rsqrtf(hx2), hy = hy2 * rsqrtf(hy2);
     return make_float2(fmaf(hx, 1.01f, 0.01f), fmaf(hy, 1.01f, 0.01f));
 }
 
@@ -54,7 +59,7 @@ __device__ __forceinline__ float ellipse_bound(const float4 a, const float4 b, f
     if (!(b.y >= amin)) return INFINITY;
     const float dq = a.z * b.x - a.w * a.w;
     if (!(a.z > 0.0f && b.x > 0.0f && dq >= 1e-2f * a.z * b.x)) return INFINITY;
-    return fmaf(2.0f * logf(b.y / amin), 1.02f, 1e-3f);
+    return fmaf(2.0f * __logf(__fdividef(b.y, amin)), 1.02f, 1e-3f);   // 1e-3 >> the approximations' error
 }
 
 // Stages the culling bounds of batch entry j.
@@ -120,14 +125,17 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
                 float best = 0.0f;
                 const bool ox = dxl > 0.0f || dxr < 0.0f, oy = dyl > 0.0f || dyr < 0.0f;
                 if (ox || oy) best = INFINITY;
+                // (the 1D minimiser needs no exact quotient: an error e in it
+                // raises q by only c e^2, far inside the bound's 2% margin, and
+                // the q evaluated is that of a point of the edge either way)
                 if (ox) {
                     const float dx = dxl > 0.0f ? dxl : dxr;
-                    const float dy = fminf(fmaxf(-a.w * dx / bb.x, dyl), dyr);
+                    const float dy = fminf(fmaxf(__fdividef(-a.w * dx, bb.x), dyl), dyr);
                     best = fminf(best, fmaf(a.z * dx, dx, fmaf(2.0f * a.w * dx, dy, bb.x * dy * dy)));
                 }
                 if (oy) {
                     const float dy = dyl > 0.0f ? dyl : dyr;
-                    const float dx = fminf(fmaxf(-a.w * dy / a.z, dxl), dxr);
+                    const float dx = fminf(fmaxf(__fdividef(-a.w * dy, a.z), dxl), dxr);
                     best = fminf(best, fmaf(a.z * dx, dx, fmaf(2.0f * a.w * dx, dy, bb.x * dy * dy)));
                 }
                 hit = best <= qt;
