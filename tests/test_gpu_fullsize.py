@@ -130,14 +130,48 @@ def _check_grads_large(g, go, n, sh_degree, keep=None):
     assert np.all(np.asarray(g["sh"])[:, nc:] == 0)
 
 
+def _bench_configuration(R, p, views, P):
+    """The launch configuration bench.py times: the autotuner's choice for the
+    workload class (a fresh cache, so it tunes as the bench does on a new box)."""
+    import tempfile
+
+    from paper_2410_08743_gb300 import tune
+    image = torch.empty(Renderer.image_numel(views), device=DEV)
+    tgt = torch.zeros_like(image)
+    g = zero_grads(p)
+    pg = torch.zeros(len(views), 6, dtype=torch.float64, device=DEV)
+    l1 = L.make_loss(L.GS_LOSS_L1, target=tgt, w_l1=1.0)
+    R.forward(p, views, P, image=image)
+    with tempfile.TemporaryDirectory() as d:
+        return tune.autotune(R, p, views, P, image, l1, g, pg, repeats=1, cache_path=os.path.join(d, "t.json"))
+
+
 def test_batched_1M_64_views_sampled_parity(R):
+    """In the bench's configuration: the scene loaded in Morton order of its
+    means, the autotuned launch parameters (two pixels per thread in the
+    blends where it picks them), one launch over all 64 views."""
     w = synth.batched_workload()
-    sc, views, poses = w["scene"], w["views"], w["poses"]
-    n = len(sc["opac"])
+    sc0, views, poses = w["scene"], w["views"], w["poses"]
+    n = len(sc0["opac"])
     res = [(v["width"], v["height"]) for v in views]
     idx = sorted({res.index(r) for r in set(res)} | {len(views) - 1})
     assert len(idx) >= 3
-    p, P, img, _, _ = gpu_forward(R, sc, views, poses)
+    p, perm = L.spatially_ordered(R.ctx, to_dev(sc0))
+    perm = perm.cpu().numpy().astype(np.int64)
+    sc = {k_: np.ascontiguousarray(sc0[k_][perm]) for k_ in ("means", "scales", "quats", "opac", "sh")}
+    sc["sh_degree"] = sc0["sh_degree"]
+    P = poses_dev(poses)
+    tuned = _bench_configuration(R, p, views, P)
+    try:
+        _batched_sampled_parity(R, sc, p, views, poses, P, idx, n)
+    finally:
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, 1, 1)
+    print("tuning", tuned["tuning"])
+
+
+def _batched_sampled_parity(R, sc, p, views, poses, P, idx, n):
+    img = R.forward(p, views, P)
+    torch.cuda.synchronize()
     vs, ps = _sub(views, poses, idx)
     _oracle_threads(len(idx) * n)
 
@@ -255,6 +289,8 @@ def test_joint_300k_l1_dssim_one_view_parity(R):
 
 
 def test_trajectory_3M_8_frames_recompute_sampled_parity(R):
+    """With the launch parameters the trajectory leg's autotuner picks for an
+    8-frame batch (a fresh cache)."""
     w = synth.trajectory_workload()
     sc, views, poses = w["scene"], w["views"], w["poses"]
     n = len(sc["opac"])
@@ -263,6 +299,14 @@ def test_trajectory_3M_8_frames_recompute_sampled_parity(R):
     vA, pA = _sub(views, poses, A)
     vB, pB = _sub(views, poses, B)
     PA, PB = poses_dev(pA), poses_dev(pB)
+    _bench_configuration(R, p, vA, PA)
+    try:
+        _trajectory_parity(R, sc, p, vA, pA, PA, vB, PB, n)
+    finally:
+        L.gs_ctx_set_tuning(R.ctx, 4096, 2048, 256, 1, 1)
+
+
+def _trajectory_parity(R, sc, p, vA, pA, PA, vB, PB, n):
     img = R.forward(p, vA, PA).clone()
     torch.cuda.synchronize()
     idx = [1, 6]
