@@ -634,6 +634,15 @@ def run_extras(r, p, views, P, image, tgt, grads, pose_grad, npix, dev, K):
     pose_only(0)
     ms = _time_iters(pose_only, K)
     out["masked_l1_pose_only_mpix_s"] = npix / (ms / K * 1e-3) / 1e6
+    # where its time goes: the pose-only backward preprocess (the pass a fold of
+    # the 2D gradients into the pose inside the backward blend would replace)
+    L.gs_ctx_set_profiling(r.ctx, True)
+    L.gs_ctx_profile(r.ctx)
+    for i in range(K):
+        pose_only(i)
+    pp = L.gs_ctx_profile(r.ctx)
+    L.gs_ctx_set_profiling(r.ctx, False)
+    out["masked_l1_pose_only_kernels_ms"] = {k: v[0] / K for k, v in sorted(pp.items(), key=lambda kv: -kv[1][0])}
     # the per-tile sort on its own: forwards that sort every tile's whole list
     # in separate kernels (GS_F_FULL_SORT) beside the lazy forward, which sorts
     # inside the blend only the prefixes the pixels consume
