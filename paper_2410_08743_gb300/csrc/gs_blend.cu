@@ -62,10 +62,27 @@ __device__ __forceinline__ float ellipse_bound(const float4 a, const float4 b, f
     return fmaf(2.0f * __logf(__fdividef(b.y, amin)), 1.02f, 1e-3f);   // 1e-3 >> the approximations' error
 }
 
-// Stages the culling bounds of batch entry j.
-__device__ __forceinline__ void stage_bounds(SplatBatch& sb, int j, const float4 a, const float4 b, float amin) {
+// The staged conic is scaled so that the exponent of Eq. 3 comes out in base
+// 2, ready for ex2: with L = log2(e),
+//   a' = -L a / 2, b' = -L b, c' = -L c / 2, and
+//   power2 = a' dx^2 + b' dx dy + c' dy^2 = L power, alpha = o 2^power2.
+// The ellipse bound is staged in the same units (q <= Qt iff power2 >= Qt').
+#define GS_KA (-0.72134752044448170f)   // -L / 2
+#define GS_KB (-1.44269504088896340f)   // -L
+#define GS_IKA (-1.38629436111989061f)  // 1 / GS_KA = -2 ln 2
+#define GS_IKB (-0.69314718055994531f)  // 1 / GS_KB = -ln 2
+
+// Stages batch entry j: splat records a = (mu.x, mu.y, a, b), b = (c, o, r, g),
+// cb = blue; the culling bounds from the unscaled conic, then the scaled one.
+__device__ __forceinline__ void stage_entry(SplatBatch& sb, int j, float4 a, float4 b, float cb, float amin) {
     sb.H[j] = alpha_box(a, b, amin);
-    sb.Qt[j] = ellipse_bound(a, b, amin);
+    sb.Qt[j] = GS_KA * ellipse_bound(a, b, amin);   // -INFINITY: no bound
+    a.z *= GS_KA;
+    a.w *= GS_KB;
+    b.x *= GS_KA;
+    sb.A[j] = a;
+    sb.B[j] = b;
+    sb.Cb[j] = cb;
 }
 
 // Splat record A of entry k with its projected mean moved to the tile origin
@@ -115,30 +132,31 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
             hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx1) &&
                   (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy1);
             const float qt = sb.Qt[e];
-            if (hit && qt < INFINITY) {
-                // Minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2 over the footprint
-                // (d = p - mu).  With the centre outside, a convex q is least on
+            if (hit && qt > -INFINITY) {
+                // Maximum of the scaled exponent p(d) = a' dx^2 + b' dx dy + c' dy^2
+                // (d = p - mu; -L/2 times the quadratic form q) over the
+                // footprint.  With the centre outside, a concave p is largest on
                 // an edge whose outside holds the centre: on such an edge the
-                // other offset is the 1D minimiser clamped to the edge.
+                // other offset is the 1D maximiser clamped to the edge.
                 const float4 bb = sb.B[e];
                 const float dxl = fx0 - a.x, dxr = fx1 - a.x, dyl = fy0 - a.y, dyr = fy1 - a.y;
                 float best = 0.0f;
                 const bool ox = dxl > 0.0f || dxr < 0.0f, oy = dyl > 0.0f || dyr < 0.0f;
-                if (ox || oy) best = INFINITY;
-                // (the 1D minimiser needs no exact quotient: an error e in it
-                // raises q by only c e^2, far inside the bound's 2% margin, and
-                // the q evaluated is that of a point of the edge either way)
+                if (ox || oy) best = -INFINITY;
+                // (the 1D maximiser needs no exact quotient: an error e in it
+                // lowers p by only |c'| e^2, far inside the bound's 2% margin,
+                // and the p evaluated is that of a point of the edge either way)
                 if (ox) {
                     const float dx = dxl > 0.0f ? dxl : dxr;
-                    const float dy = fminf(fmaxf(__fdividef(-a.w * dx, bb.x), dyl), dyr);
-                    best = fminf(best, fmaf(a.z * dx, dx, fmaf(2.0f * a.w * dx, dy, bb.x * dy * dy)));
+                    const float dy = fminf(fmaxf(__fdividef(-0.5f * a.w * dx, bb.x), dyl), dyr);
+                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, bb.x * dy * dy)));
                 }
                 if (oy) {
                     const float dy = dyl > 0.0f ? dyl : dyr;
-                    const float dx = fminf(fmaxf(__fdividef(-a.w * dy, a.z), dxl), dxr);
-                    best = fminf(best, fmaf(a.z * dx, dx, fmaf(2.0f * a.w * dx, dy, bb.x * dy * dy)));
+                    const float dx = fminf(fmaxf(__fdividef(-0.5f * a.w * dy, a.z), dxl), dxr);
+                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, bb.x * dy * dy)));
                 }
-                hit = best <= qt;
+                hit = best >= qt;
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -149,17 +167,20 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
     return n;
 }
 
-// alpha of one (pixel, splat) pair with a fixed operation sequence, so that
-// the forward and the backward take the same skip decisions.
-//   power = -1/2 (a dx^2 + c dy^2) - b dx dy with d = p - mu_hat (Eq. 3)
+// alpha of one (pixel, splat) pair from the staged (scaled) conic with a fixed
+// operation sequence, which every blend uses, so that the forward and the
+// backward take the same skip decisions:
+//   power2 = (a' dx^2 + c' dy^2) + b' dx dy = log2(e) power, d = p - mu_hat,
+//   power = -1/2 (a dx^2 + c dy^2) - b dx dy (Eq. 3), alpha = o 2^power2;
 //   returns false when the pair is skipped (power > 0 or alpha < alpha_min).
+__device__ __forceinline__ float pair_power2(const float4 a, const float4 b, float dxx_a, float dx, float dy) {
+    return __fmaf_rn(a.w, __fmul_rn(dx, dy), __fmaf_rn(b.x, __fmul_rn(dy, dy), dxx_a));
+}
 __device__ __forceinline__ bool pair_alpha(const float4 a, const float4 b, float dx, float dy, float amin, float amax,
                                            float& G, float& alpha, bool& clamped) {
-    float q = __fmul_rn(a.z, __fmul_rn(dx, dx));
-    q = __fmaf_rn(b.x, __fmul_rn(dy, dy), q);
-    const float power = __fmaf_rn(-a.w, __fmul_rn(dx, dy), __fmul_rn(-0.5f, q));
-    if (power > 0.0f) return false;
-    G = fast_exp2(__fmul_rn(power, GS_LOG2E));
+    const float pw = pair_power2(a, b, __fmul_rn(a.z, __fmul_rn(dx, dx)), dx, dy);
+    if (pw > 0.0f) return false;
+    G = fast_exp2(pw);
     const float ar = __fmul_rn(b.y, G);
     clamped = ar > amax;
     alpha = clamped ? amax : ar;
@@ -201,11 +222,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
         if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)min((uint32_t)BATCH, e - base));
         if (j < e) {
             const size_t k = vbase + sorted_idx[j];
-            const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
-            sb.A[threadIdx.x] = a;
-            sb.B[threadIdx.x] = b;
-            sb.Cb[threadIdx.x] = sp.Cb[k];
-            stage_bounds(sb, threadIdx.x, a, b, rp.alpha_min);
+            stage_entry(sb, threadIdx.x, stage_mean(sp, k, ox, oy), sp.B[k], sp.Cb[k], rp.alpha_min);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)BATCH, e - base);
@@ -365,18 +382,17 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
             const int cnt = (int)min((uint32_t)BATCH, p1 - base);
             for (int j = threadIdx.x; j < cnt; j += NT) {
                 const size_t k = vbase + sorted_idx[s + base + j];
-                const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
-                sm.u.sb.A[j] = a;
-                sm.u.sb.B[j] = b;
-                sm.u.sb.Cb[j] = sp.Cb[k];
-                stage_bounds(sm.u.sb, j, a, b, rp.alpha_min);
+                stage_entry(sm.u.sb, j, stage_mean(sp, k, ox, oy), sp.B[k], sp.Cb[k], rp.alpha_min);
             }
             __syncthreads();
             unsigned char* wl = sm.wl[wid];
-            const int nw = warp_compact(sm.u.sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
+            // a warp whose pixels have all stopped skips the batch
+            const int nw = __all_sync(0xffffffffu, all_done())
+                               ? 0
+                               : warp_compact(sm.u.sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
             // the warp walks its entries in lock step; a pixel that has stopped
             // or is outside the splat's box blends nothing (weight 0)
-            if (CNT && __any_sync(0xffffffffu, !all_done())) n_went += (uint32_t)nw;
+            if (CNT) n_went += (uint32_t)nw;
             for (int qq = 0; qq < nw; qq++) {
                 if (__all_sync(0xffffffffu, all_done())) break;
                 const int jj = wl[qq];
@@ -402,9 +418,8 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
                 const float qx = __fmul_rn(a.z, __fmul_rn(dx, dx));
 #pragma unroll
                 for (int q = 0; q < PX; q++) {
-                    const float pw = __fmaf_rn(-a.w, __fmul_rn(dx, dy[q]),
-                                               __fmul_rn(-0.5f, __fmaf_rn(b.x, __fmul_rn(dy[q], dy[q]), qx)));
-                    const float ar = __fmul_rn(b.y, fast_exp2(__fmul_rn(pw, GS_LOG2E)));
+                    const float pw = pair_power2(a, b, qx, dx, dy[q]);
+                    const float ar = __fmul_rn(b.y, fast_exp2(pw));
                     const float alpha = ar > rp.alpha_max ? rp.alpha_max : ar;
                     const bool ok = u[q] && !(pw > 0.0f) && alpha >= rp.alpha_min;
                     // Eq. 4 front to back; stop before the splat that would take
@@ -804,12 +819,8 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         for (int j = threadIdx.x; j < cnt; j += NT) {
             const uint32_t id = sorted_idx[s + bstart + j];
             const size_t k = vbase + id;
-            const float4 a = stage_mean(sp, k, ox, oy), b = sp.B[k];
             s_idx[j] = id;
-            sb.A[j] = a;
-            sb.B[j] = b;
-            sb.Cb[j] = sp.Cb[k];
-            stage_bounds(sb, j, a, b, rp.alpha_min);
+            stage_entry(sb, j, stage_mean(sp, k, ox, oy), sp.B[k], sp.Cb[k], rp.alpha_min);
         }
         for (int q = threadIdx.x; q < BATCH * 9; q += NT) s_acc[q] = 0.0f;
         __syncthreads();
@@ -844,8 +855,8 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
 #pragma unroll
             for (int q = 0; q < PX; q++) {
                 yy[q] = __fmul_rn(dy[q], dy[q]);
-                const float pw = __fmaf_rn(-a.w, __fmul_rn(dx, dy[q]), __fmul_rn(-0.5f, __fmaf_rn(b.x, yy[q], qx)));
-                G[q] = fast_exp2(__fmul_rn(pw, GS_LOG2E));
+                const float pw = __fmaf_rn(a.w, __fmul_rn(dx, dy[q]), __fmaf_rn(b.x, yy[q], qx));
+                G[q] = fast_exp2(pw);
                 const float ar = __fmul_rn(b.y, G[q]);
                 cl[q] = ar > amax;
                 al[q] = cl[q] ? amax : ar;
@@ -927,7 +938,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         // dpower/d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2))
         for (int j = threadIdx.x; j < cnt; j += NT) {
             const float* acc = s_acc + j * 9;
-            const float ca = sb.A[j].z, cb_ = sb.A[j].w, cc = sb.B[j].x;
+            const float ca = sb.A[j].z * GS_IKA, cb_ = sb.A[j].w * GS_IKB, cc = sb.B[j].x * GS_IKA;
             const float Mx = acc[0], My = acc[1];
             const float4 ga = make_float4(fmaf(ca, Mx, cb_ * My), fmaf(cb_, Mx, cc * My), -0.5f * acc[2], -acc[3]);
             const float4 gb = make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]);
