@@ -83,6 +83,20 @@ def _needle_case(n=6000, seed=33):
     return sc, views, poses
 
 
+def _wide_view_case(n=6000, seed=34):
+    """A view with more than the 8192 tiles the shared-memory tile histograms
+    hold (2050 x 1090: 129 x 69 tiles, ragged on both edges), which takes the
+    per-key global-atomic path of the key count and scatter, in one launch
+    with a small view that takes the shared-memory path."""
+    rng = np.random.default_rng(seed)
+    sc = synth.make_scene_box(seed, n, sh_degree=1, lo=(-1.2, -0.7, 2.5), hi=(1.2, 0.7, 5.0))
+    views = [dict(fx=1640.0, fy=1640.0, cx=1025.0, cy=545.0, width=2050, height=1090),
+             dict(fx=60.0, fy=60.0, cx=32.0, cy=24.0, width=64, height=48)]
+    base = synth.pose_from_center(np.eye(3), np.zeros(3))
+    poses = np.stack([synth.perturb_normal(rng, base, 2.0, 0.03) for _ in views])
+    return sc, views, poses
+
+
 CASES = {
     "tiny": lambda: (lambda w: (w["scene"], w["views"], w["poses"]))(synth.tiny_workload(0)),
     "ragged_sh3": lambda: _ragged_case(),
@@ -91,8 +105,9 @@ CASES = {
     "dense_large": lambda: _dense_case(120000),
     "same_depth": lambda: _same_depth_case(),
     "needles": lambda: _needle_case(),
+    "wide_view": lambda: _wide_view_case(),
 }
-GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium"]
+GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium", "wide_view"]
 
 
 @pytest.mark.parametrize("full", [True, False], ids=["full_sort", "lazy_sort"])
