@@ -437,7 +437,9 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         # pinned host buffers on the memory next to this GPU: the process runs
-        # on the GPU's local cores while they are first touched
+        # on the GPU's local cores while they are allocated and first touched
+        # (the original CPU set comes back after this leg)
+        aff0 = os.sched_getaffinity(0)
         host_aff = _bind_to_gpu_local_cpus(local)
         r.set_flags(L.GS_F_HOST_IO)
         hp = {k: p[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opac", "sh")}
@@ -484,6 +486,7 @@ def run_gpu(args):
                "step_ms": {"min": min(step_ms), "median": med, "max": max(step_ms)},
                "host_affinity": host_aff}
         r.set_flags(L.GS_F_NO_SYNC)
+        os.sched_setaffinity(0, aff0)
 
     # ---- roofline of the dominant kernel
     peaks = _peaks()
