@@ -294,11 +294,14 @@ __device__ __forceinline__ void cam_coord_ff(const ViewDev& vd, int a, const flo
 // f * (x / z) + c as a pair
 __device__ __forceinline__ void project_ff(float xh, float xl, float zh, float zl, float f, float c, float& hi,
                                            float& lo) {
-    const float q = __fdiv_rn(xh, zh);
+    // q need not be the rounded quotient: the residual below is exact for any q
+    // within a few units in the last place of x / z, and the correction ql
+    // carries it (the pair keeps its ~2^-44 relative error)
+    const float q = __fdividef(xh, zh);
     float p, pe;
     two_prod(q, zh, p, pe);
     const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(xh, p), pe), xl), __fmul_rn(q, zl));
-    const float ql = __fdiv_rn(r, zh);
+    const float ql = __fdividef(r, zh);
     float m, me, s, se;
     two_prod(f, q, m, me);
     me = __fmaf_rn(f, ql, me);
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int i_begin
             continue;
         }
         // value path: conic and view-dependent colour
-        float inv_det = 1.0f / ko.det;
+        float inv_det = fast_rcp(ko.det);   // value path: a unit in the last place is far inside its tolerance
         float ca = ko.C * inv_det, cb = -ko.B * inv_det, cc = ko.A * inv_det;
         float dx = mu[0] - vd.oc[0], dy = mu[1] - vd.oc[1], dz = mu[2] - vd.oc[2];
         float il = rsqrtf(dx * dx + dy * dy + dz * dz);
