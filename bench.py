@@ -870,7 +870,7 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # ncu capture of the current kernel on the 16-view case, scaled to a launch by the
 # run's units; re-measure when the kernel changes.
 # k_blend_bwd<2, 0>: 218.2 MB for 4,860,428 list entries read, 16 views at 1M Gaussians.
-TRAFFIC_PER_UNIT = {"blend_bwd": (44.89, 5)}
+TRAFFIC_PER_UNIT = {"blend_bwd": (44.92, 5)}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, alu, sm_mhz):

@@ -16,17 +16,76 @@
 
 namespace gs {
 
-#define BATCH 256
+#define BATCH 128
 
-// Shared-memory splat batch: A = (mu.x, mu.y, conic.a, conic.b),
-// B = (conic.c, opacity, r, g), Cb = b.
+// ------------------------------------------------------------ paired FP32
+// add/sub/mul/fma.rn.f32x2 (sm_100 and later) compute two IEEE
+// round-to-nearest results in one instruction, bit for bit those of the
+// scalar operations, so the two pixels of a lane share their issue slots and
+// every decision stays the one the scalar sequence takes.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2_t x) {
+    float lo;
+    asm("{.reg .f32 hi;\n\tmov.b64 {%0, hi}, %1;}" : "=f"(lo) : "l"(x));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2_t x) {
+    float hi;
+    asm("{.reg .f32 lo;\n\tmov.b64 {lo, %0}, %1;}" : "=f"(hi) : "l"(x));
+    return hi;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Shared-memory splat batch.  The fields of the per-pixel arithmetic are
+// stored twice, as (x, x) pairs, so that the paired operations of the
+// two-pixel blends take a splat operand straight from one (broadcast) load:
+//   P0 = (mu.x, mu.x, a', a'), P1 = (mu.y, mu.y, b', b'), P2 = (c', c', o, o),
+//   P3 = (r, r, g, g), P4 = (blue, blue), with (a', b', c') the scaled conic.
 struct SplatBatch {
-    float4 A[BATCH];
-    float4 B[BATCH];
-    float Cb[BATCH];
+    ulonglong2 P0[BATCH];
+    ulonglong2 P1[BATCH];
+    ulonglong2 P2[BATCH];
+    ulonglong2 P3[BATCH];
+    f2_t P4[BATCH];
     float2 H[BATCH];   // half-extents of the box holding every pixel with alpha >= alpha_min
     float Qt[BATCH];   // widened bound on the conic's quadratic form at such pixels (INFINITY: no bound)
 };
+
+// Entry j as the scalar records A = (mu.x, mu.y, a', b'), B = (c', o, r, g)
+// and blue.
+__device__ __forceinline__ float4 sb_A(const SplatBatch& sb, int j) {
+    const ulonglong2 p0 = sb.P0[j], p1 = sb.P1[j];
+    return make_float4(f2_lo(p0.x), f2_lo(p1.x), f2_lo(p0.y), f2_lo(p1.y));
+}
+__device__ __forceinline__ float4 sb_B(const SplatBatch& sb, int j) {
+    const ulonglong2 p2 = sb.P2[j], p3 = sb.P3[j];
+    return make_float4(f2_lo(p2.x), f2_lo(p2.y), f2_lo(p3.x), f2_lo(p3.y));
+}
+__device__ __forceinline__ float sb_Cb(const SplatBatch& sb, int j) { return f2_lo(sb.P4[j]); }
 
 // Conservative half-extents of {d : o exp(-1/2 d^T Q d) >= alpha_min}, the
 // ellipse d^T Q d <= R^2 with R^2 = 2 ln(o / alpha_min): |dx| <= R sqrt(Q^-1_xx),
@@ -77,12 +136,12 @@ __device__ __forceinline__ float ellipse_bound(const float4 a, const float4 b, f
 __device__ __forceinline__ void stage_entry(SplatBatch& sb, int j, float4 a, float4 b, float cb, float amin) {
     sb.H[j] = alpha_box(a, b, amin);
     sb.Qt[j] = GS_KA * ellipse_bound(a, b, amin);   // -INFINITY: no bound
-    a.z *= GS_KA;
-    a.w *= GS_KB;
-    b.x *= GS_KA;
-    sb.A[j] = a;
-    sb.B[j] = b;
-    sb.Cb[j] = cb;
+    const float ca = a.z * GS_KA, cbb = a.w * GS_KB, cc = b.x * GS_KA;
+    sb.P0[j] = make_ulonglong2(f2_pack(a.x, a.x), f2_pack(ca, ca));
+    sb.P1[j] = make_ulonglong2(f2_pack(a.y, a.y), f2_pack(cbb, cbb));
+    sb.P2[j] = make_ulonglong2(f2_pack(cc, cc), f2_pack(b.y, b.y));
+    sb.P3[j] = make_ulonglong2(f2_pack(b.z, b.z), f2_pack(b.w, b.w));
+    sb.P4[j] = f2_pack(cb, cb);
 }
 
 // Splat record A of entry k with its projected mean moved to the tile origin
@@ -126,7 +185,7 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
         const int e = r + lane;
         bool hit = false;
         if (e < cnt) {
-            const float4 a = sb.A[e];
+            const float4 a = sb_A(sb, e);
             const float2 h = sb.H[e];
             const float fx1 = fx0 + (float)(WARP_W - 1), fy1 = fy0 + (float)(fh - 1);
             hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx1) &&
@@ -138,7 +197,7 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
                 // footprint.  With the centre outside, a concave p is largest on
                 // an edge whose outside holds the centre: on such an edge the
                 // other offset is the 1D maximiser clamped to the edge.
-                const float4 bb = sb.B[e];
+                const float cc = f2_lo(sb.P2[e].x);
                 const float dxl = fx0 - a.x, dxr = fx1 - a.x, dyl = fy0 - a.y, dyr = fy1 - a.y;
                 float best = 0.0f;
                 const bool ox = dxl > 0.0f || dxr < 0.0f, oy = dyl > 0.0f || dyr < 0.0f;
@@ -148,13 +207,13 @@ __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float
                 // and the p evaluated is that of a point of the edge either way)
                 if (ox) {
                     const float dx = dxl > 0.0f ? dxl : dxr;
-                    const float dy = fminf(fmaxf(__fdividef(-0.5f * a.w * dx, bb.x), dyl), dyr);
-                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, bb.x * dy * dy)));
+                    const float dy = fminf(fmaxf(__fdividef(-0.5f * a.w * dx, cc), dyl), dyr);
+                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
                 }
                 if (oy) {
                     const float dy = dyl > 0.0f ? dyl : dyr;
                     const float dx = fminf(fmaxf(__fdividef(-0.5f * a.w * dy, a.z), dxl), dxr);
-                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, bb.x * dy * dy)));
+                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
                 }
                 hit = best >= qt;
             }
@@ -220,7 +279,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
         if (__syncthreads_count(done) == GS_TILE_PIX) break;
         const uint32_t j = base + threadIdx.x;
         if (counters && threadIdx.x == 0) atomicAdd(counters + 4, (unsigned long long)min((uint32_t)BATCH, e - base));
-        if (j < e) {
+        if (threadIdx.x < BATCH && j < e) {
             const size_t k = vbase + sorted_idx[j];
             stage_entry(sb, threadIdx.x, stage_mean(sp, k, ox, oy), sp.B[k], sp.Cb[k], rp.alpha_min);
         }
@@ -228,12 +287,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
         const int cnt = (int)min((uint32_t)BATCH, e - base);
         if (!done) {
             for (int jj = 0; jj < cnt; jj++) {
-                const float4 a = sb.A[jj];
+                const float4 a = sb_A(sb, jj);
                 const float2 h = sb.H[jj];
                 n_eval++;
                 const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
                 if (fabsf(dx) > h.x || fabsf(dy) > h.y) continue;
-                const float4 b = sb.B[jj];
+                const float4 b = sb_B(sb, jj);
                 float G, alpha;
                 bool cl;
                 if (!pair_alpha(a, b, dx, dy, rp.alpha_min, rp.alpha_max, G, alpha, cl)) continue;
@@ -243,7 +302,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
                 const float w = alpha * T;
                 C0 = fmaf(b.z, w, C0);
                 C1 = fmaf(b.w, w, C1);
-                C2 = fmaf(sb.Cb[jj], w, C2);
+                C2 = fmaf(sb_Cb(sb, jj), w, C2);
                 T = Tn;
                 last = base - s + jj + 1;
             }
@@ -372,6 +431,11 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
     };
     uint32_t n_eval = 0, n_blend = 0, n_read = 0, n_went = 0;
     uint32_t n_sorted = 0;
+    // two-pixel state in pairs: (transmittance, colour) of the lane's pixels
+    const float amin = rp.alpha_min, amax = rp.alpha_max, tmin = rp.t_min;
+    const f2_t fpx2 = f2_pack(fpx, fpx), fpy2 = f2_pack((float)ly, (float)(ly + WARP_H));
+    const f2_t one2 = f2_pack(1.0f, 1.0f);
+    f2_t pT2 = one2, Cr2 = f2_pack(0.0f, 0.0f), Cg2 = Cr2, Cb2 = Cr2;
 
     // Blends list positions [p0, p1) read from sorted_idx; returns true when
     // every pixel of the tile has stopped.
@@ -391,49 +455,76 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
                                ? 0
                                : warp_compact(sm.u.sb, cnt, (float)wx0, (float)wy0, wl, WARP_H * PX);
             // the warp walks its entries in lock step; a pixel that has stopped
-            // or is outside the splat's box blends nothing (weight 0)
+            // or whose alpha is below alpha_min blends nothing (weight 0)
             if (CNT) n_went += (uint32_t)nw;
-            for (int qq = 0; qq < nw; qq++) {
-                if (__all_sync(0xffffffffu, all_done())) break;
-                const int jj = wl[qq];
-                const uint32_t pos1 = base + (uint32_t)jj + 1u;
-                const float4 a = sm.u.sb.A[jj];
-                const float2 h = sm.u.sb.H[jj];
-                const float dx = __fsub_rn(fpx, a.x);
-                const bool inx = fabsf(dx) <= h.x;
-                float dy[PX];
-                bool u[PX];
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < PX; q++) {
-                    dy[q] = __fsub_rn((float)(ly + WARP_H * q), a.y);
-                    u[q] = !done[q] && inx && fabsf(dy[q]) <= h.y;
-                    any = any || u[q];
-                    if (CNT) n_eval += u[q];
-                }
-                if (!__any_sync(0xffffffffu, any)) continue;
-                const float4 b = sm.u.sb.B[jj];
-                const float cb = sm.u.sb.Cb[jj];
-                // alpha of each pixel (Eq. 3) with pair_alpha's operation sequence
-                const float qx = __fmul_rn(a.z, __fmul_rn(dx, dx));
-#pragma unroll
-                for (int q = 0; q < PX; q++) {
-                    const float pw = pair_power2(a, b, qx, dx, dy[q]);
-                    const float ar = __fmul_rn(b.y, fast_exp2(pw));
-                    const float alpha = ar > rp.alpha_max ? rp.alpha_max : ar;
-                    const bool ok = u[q] && !(pw > 0.0f) && alpha >= rp.alpha_min;
+            if constexpr (PX == 2) {
+                for (int qq = 0; qq < nw; qq++) {
+                    if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+                    const int jj = wl[qq];
+                    const uint32_t pos1 = base + (uint32_t)jj + 1u;
+                    const ulonglong2 p0 = sm.u.sb.P0[jj], p1 = sm.u.sb.P1[jj], p2 = sm.u.sb.P2[jj];
+                    // alpha of both pixels (Eq. 3) with pair_alpha's operation
+                    // sequence, paired: the lanes of each pair share dx
+                    const f2_t dx2 = f2_sub(fpx2, p0.x), dy2 = f2_sub(fpy2, p1.x);
+                    const f2_t pw2 =
+                        f2_fma(p1.y, f2_mul(dx2, dy2), f2_fma(p2.x, f2_mul(dy2, dy2), f2_mul(p0.y, f2_mul(dx2, dx2))));
+                    const float pw0 = f2_lo(pw2), pw1 = f2_hi(pw2);
+                    const f2_t ar2 = f2_mul(p2.y, f2_pack(fast_exp2(pw0), fast_exp2(pw1)));
+                    const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
+                    const float al0 = ar0 > amax ? amax : ar0, al1 = ar1 > amax ? amax : ar1;
+                    const bool ok0 = !done[0] && !(pw0 > 0.0f) && al0 >= amin;
+                    const bool ok1 = !done[1] && !(pw1 > 0.0f) && al1 >= amin;
+                    if (CNT) {
+                        const float2 h = sm.u.sb.H[jj];
+                        const bool inx = fabsf(f2_lo(dx2)) <= h.x;
+                        n_eval += (!done[0] && inx && fabsf(f2_lo(dy2)) <= h.y) +
+                                  (!done[1] && inx && fabsf(f2_hi(dy2)) <= h.y);
+                    }
+                    if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
                     // Eq. 4 front to back; stop before the splat that would take
                     // the transmittance below t_min
-                    const float Tn = pT[q] * (1.0f - alpha);
-                    const bool stop = ok && Tn < rp.t_min;
+                    const f2_t Tn2 = f2_mul(pT2, f2_sub(one2, f2_pack(al0, al1)));
+                    const float Tn0 = f2_lo(Tn2), Tn1 = f2_hi(Tn2);
+                    const bool st0 = ok0 && Tn0 < tmin, st1 = ok1 && Tn1 < tmin;
+                    const bool bl0 = ok0 && !st0, bl1 = ok1 && !st1;
+                    done[0] = done[0] || st0;
+                    done[1] = done[1] || st1;
+                    const f2_t w2 = f2_mul(f2_pack(bl0 ? al0 : 0.0f, bl1 ? al1 : 0.0f), pT2);
+                    const ulonglong2 p3 = sm.u.sb.P3[jj];
+                    Cr2 = f2_fma(p3.x, w2, Cr2);
+                    Cg2 = f2_fma(p3.y, w2, Cg2);
+                    Cb2 = f2_fma(sm.u.sb.P4[jj], w2, Cb2);
+                    pT2 = f2_pack(bl0 ? Tn0 : f2_lo(pT2), bl1 ? Tn1 : f2_hi(pT2));
+                    last[0] = bl0 ? pos1 : last[0];
+                    last[1] = bl1 ? pos1 : last[1];
+                    if (CNT) n_blend += bl0 + bl1;
+                }
+            } else {
+                for (int qq = 0; qq < nw; qq++) {
+                    if (__all_sync(0xffffffffu, done[0])) break;
+                    const int jj = wl[qq];
+                    const uint32_t pos1 = base + (uint32_t)jj + 1u;
+                    const float4 a = sb_A(sm.u.sb, jj);
+                    const float2 h = sm.u.sb.H[jj];
+                    const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn((float)ly, a.y);
+                    const bool u = !done[0] && fabsf(dx) <= h.x && fabsf(dy) <= h.y;
+                    if (CNT) n_eval += u;
+                    if (!__any_sync(0xffffffffu, u)) continue;
+                    const float4 b = sb_B(sm.u.sb, jj);
+                    const float pw = pair_power2(a, b, __fmul_rn(a.z, __fmul_rn(dx, dx)), dx, dy);
+                    const float ar = __fmul_rn(b.y, fast_exp2(pw));
+                    const float alpha = ar > amax ? amax : ar;
+                    const bool ok = u && !(pw > 0.0f) && alpha >= amin;
+                    const float Tn = pT[0] * (1.0f - alpha);
+                    const bool stop = ok && Tn < tmin;
                     const bool blend = ok && !stop;
-                    done[q] = done[q] || stop;
-                    const float w = blend ? alpha * pT[q] : 0.0f;
-                    C0[q] = fmaf(b.z, w, C0[q]);
-                    C1[q] = fmaf(b.w, w, C1[q]);
-                    C2[q] = fmaf(cb, w, C2[q]);
-                    pT[q] = blend ? Tn : pT[q];
-                    last[q] = blend ? pos1 : last[q];
+                    done[0] = done[0] || stop;
+                    const float w = blend ? alpha * pT[0] : 0.0f;
+                    C0[0] = fmaf(b.z, w, C0[0]);
+                    C1[0] = fmaf(b.w, w, C1[0]);
+                    C2[0] = fmaf(sb_Cb(sm.u.sb, jj), w, C2[0]);
+                    pT[0] = blend ? Tn : pT[0];
+                    last[0] = blend ? pos1 : last[0];
                     if (CNT) n_blend += blend;
                 }
             }
@@ -549,6 +640,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
         }
     }
     if (threadIdx.x == 0) sorted_count[t] = n_sorted;
+    if constexpr (PX == 2) {
+        pT[0] = f2_lo(pT2); pT[1] = f2_hi(pT2);
+        C0[0] = f2_lo(Cr2); C0[1] = f2_hi(Cr2);
+        C1[0] = f2_lo(Cg2); C1[1] = f2_hi(Cg2);
+        C2[0] = f2_lo(Cb2); C2[1] = f2_hi(Cb2);
+    }
     float l1 = 0.0f;
 #pragma unroll
     for (int q = 0; q < PX; q++) {
@@ -812,6 +909,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         fpy[q] = (float)(ly + WARP_H * q);
     }
     const float amin = rp.alpha_min, amax = rp.alpha_max;
+    // two-pixel state in pairs (used when PX == 2)
+    const f2_t fpx2 = f2_pack(fpx, fpx), fpy2 = f2_pack(fpy[0], fpy[PX - 1]);
+    const f2_t one2 = f2_pack(1.0f, 1.0f);
+    const f2_t g0_2 = f2_pack(pg0[0], pg0[PX - 1]), g1_2 = f2_pack(pg1[0], pg1[PX - 1]),
+               g2_2 = f2_pack(pg2[0], pg2[PX - 1]);
+    f2_t pT2 = f2_pack(pT[0], pT[PX - 1]), S2 = f2_pack(psg[0], psg[PX - 1]);
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
@@ -829,42 +932,6 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         for (int qq = nw - 1; qq >= 0; qq--) {
             const int jj = wl[qq];
             const uint32_t pos = (uint32_t)(bstart + jj);
-            const float4 a = sb.A[jj];
-            const float2 h = sb.H[jj];
-            const float dx = __fsub_rn(fpx, a.x);
-            const bool inx = fabsf(dx) <= h.x;
-            float dy[PX];
-            bool u[PX];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < PX; q++) {
-                dy[q] = __fsub_rn(fpy[q], a.y);
-                u[q] = inx && fabsf(dy[q]) <= h.y && pos < plast[q];
-                any = any || u[q];
-                if (CNT) n_eval += u[q];
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            if (CNT) n_w1++;
-            // alpha of each pixel (Eq. 3) with pair_alpha's operation sequence
-            const float4 b = sb.B[jj];
-            const float dxx = __fmul_rn(dx, dx);
-            const float qx = __fmul_rn(a.z, dxx);
-            float G[PX], al[PX], yy[PX];
-            bool cl[PX];
-            any = false;
-#pragma unroll
-            for (int q = 0; q < PX; q++) {
-                yy[q] = __fmul_rn(dy[q], dy[q]);
-                const float pw = __fmaf_rn(a.w, __fmul_rn(dx, dy[q]), __fmaf_rn(b.x, yy[q], qx));
-                G[q] = fast_exp2(pw);
-                const float ar = __fmul_rn(b.y, G[q]);
-                cl[q] = ar > amax;
-                al[q] = cl[q] ? amax : ar;
-                u[q] = u[q] && !(pw > 0.0f) && al[q] >= amin;
-                any = any || u[q];
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            if (CNT) n_w2++;
             // Per pixel, back to front: T_i = T_{i+1} / (1 - alpha_i), weight
             // w = alpha T_i, dL/dalpha = T_i (c . g) - S / (1 - alpha) with S the
             // colour behind (incl. background) dotted with g.  dL/dpower =
@@ -872,37 +939,98 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
             // sums dp = dL/dpower into the moments D = sum dp, My = sum dp dy,
             // Myy = sum dp dy^2 (its pixels share dx); the conic and mean
             // gradients are linear in the moments and formed once per splat.
-            const float cb = sb.Cb[jj];
             float r[9];
-            float D = 0.0f, My = 0.0f, Myy = 0.0f;
-            r[5] = 0.0f; r[6] = 0.0f; r[7] = 0.0f; r[8] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < PX; q++) {
-                if (CNT) n_used += u[q];
-                const float alq = u[q] ? al[q] : 0.0f;
-                const float Gq = (u[q] && !cl[q]) ? G[q] : 0.0f;
+            if constexpr (PX == 2) {
+                const bool u0 = pos < plast[0], u1 = pos < plast[1];
+                if (!__any_sync(0xffffffffu, u0 || u1)) continue;
+                // alpha of both pixels (Eq. 3) with pair_alpha's operation
+                // sequence, paired: the lanes of each pair share dx
+                const ulonglong2 p0 = sb.P0[jj], p1 = sb.P1[jj], p2 = sb.P2[jj];
+                const f2_t dx2 = f2_sub(fpx2, p0.x), dy2 = f2_sub(fpy2, p1.x);
+                const f2_t dxx2 = f2_mul(dx2, dx2), yy2 = f2_mul(dy2, dy2);
+                const f2_t pw2 = f2_fma(p1.y, f2_mul(dx2, dy2), f2_fma(p2.x, yy2, f2_mul(p0.y, dxx2)));
+                const float pw0 = f2_lo(pw2), pw1 = f2_hi(pw2);
+                const float G0 = fast_exp2(pw0), G1 = fast_exp2(pw1);
+                const f2_t ar2 = f2_mul(p2.y, f2_pack(G0, G1));
+                const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
+                const bool cl0 = ar0 > amax, cl1 = ar1 > amax;
+                const float al0 = cl0 ? amax : ar0, al1 = cl1 ? amax : ar1;
+                const bool v0 = u0 && !(pw0 > 0.0f) && al0 >= amin;
+                const bool v1 = u1 && !(pw1 > 0.0f) && al1 >= amin;
+                if (CNT) {
+                    const float2 h = sb.H[jj];
+                    const bool inx = fabsf(f2_lo(dx2)) <= h.x;
+                    const bool b0 = u0 && inx && fabsf(f2_lo(dy2)) <= h.y;
+                    const bool b1 = u1 && inx && fabsf(f2_hi(dy2)) <= h.y;
+                    n_eval += b0 + b1;
+                    n_w1 += __any_sync(0xffffffffu, b0 || b1) ? 1u : 0u;
+                }
+                if (!__any_sync(0xffffffffu, v0 || v1)) continue;
+                if (CNT) { n_w2++; n_used += v0 + v1; }
+                const f2_t alq2 = f2_pack(v0 ? al0 : 0.0f, v1 ? al1 : 0.0f);
+                const f2_t Gq2 = f2_pack((v0 && !cl0) ? G0 : 0.0f, (v1 && !cl1) ? G1 : 0.0f);
+                const f2_t om2 = f2_sub(one2, alq2);   // 1 - alpha lies in [0.01, 1]
+                const f2_t inv2 = f2_pack(fast_rcp(f2_lo(om2)), fast_rcp(f2_hi(om2)));
+                const f2_t Ti2 = f2_mul(pT2, inv2);
+                const f2_t w2 = f2_mul(alq2, Ti2);
+                const ulonglong2 p3 = sb.P3[jj];
+                const f2_t cg2 = f2_fma(sb.P4[jj], g2_2, f2_fma(p3.y, g1_2, f2_mul(p3.x, g0_2)));
+                const f2_t dL2 = f2_sub(f2_mul(Ti2, cg2), f2_mul(S2, inv2));
+                S2 = f2_fma(w2, cg2, S2);
+                pT2 = f2_pack(v0 ? f2_lo(Ti2) : f2_lo(pT2), v1 ? f2_hi(Ti2) : f2_hi(pT2));
+                const f2_t t2 = f2_mul(Gq2, dL2);      // dL/do contributions
+                const f2_t dp2 = f2_mul(p2.y, t2);     // dL/dpower
+                const f2_t My2 = f2_mul(dp2, dy2), Myy2 = f2_mul(dp2, yy2);
+                const f2_t c0 = f2_mul(w2, g0_2), c1 = f2_mul(w2, g1_2), c2 = f2_mul(w2, g2_2);
+                const float dx = f2_lo(dx2), D = f2_lo(dp2) + f2_hi(dp2), My = f2_lo(My2) + f2_hi(My2);
+                r[0] = dx * D;                          // sum dp dx
+                r[1] = My;                              // sum dp dy
+                r[2] = f2_lo(dxx2) * D;                 // sum dp dx^2
+                r[3] = dx * My;                         // sum dp dx dy
+                r[4] = f2_lo(Myy2) + f2_hi(Myy2);       // sum dp dy^2
+                r[5] = f2_lo(t2) + f2_hi(t2);
+                r[6] = f2_lo(c0) + f2_hi(c0);
+                r[7] = f2_lo(c1) + f2_hi(c1);
+                r[8] = f2_lo(c2) + f2_hi(c2);
+            } else {
+                const float4 a = sb_A(sb, jj);
+                const float2 h = sb.H[jj];
+                const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy[0], a.y);
+                bool u = fabsf(dx) <= h.x && fabsf(dy) <= h.y && pos < plast[0];
+                if (CNT) n_eval += u;
+                if (!__any_sync(0xffffffffu, u)) continue;
+                if (CNT) n_w1++;
+                const float4 b = sb_B(sb, jj);
+                const float dxx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy);
+                const float pw = __fmaf_rn(a.w, __fmul_rn(dx, dy), __fmaf_rn(b.x, yy, __fmul_rn(a.z, dxx)));
+                const float G = fast_exp2(pw);
+                const float ar = __fmul_rn(b.y, G);
+                const bool cl = ar > amax;
+                const float al = cl ? amax : ar;
+                u = u && !(pw > 0.0f) && al >= amin;
+                if (!__any_sync(0xffffffffu, u)) continue;
+                if (CNT) { n_w2++; n_used += u; }
+                const float alq = u ? al : 0.0f;
+                const float Gq = (u && !cl) ? G : 0.0f;
                 const float inv = fast_rcp(1.0f - alq);    // 1 - alpha lies in [0.01, 1]
-                const float Ti = pT[q] * inv;
+                const float Ti = pT[0] * inv;
                 const float w = alq * Ti;
-                r[6] = fmaf(w, pg0[q], r[6]);
-                r[7] = fmaf(w, pg1[q], r[7]);
-                r[8] = fmaf(w, pg2[q], r[8]);
-                const float cg = fmaf(cb, pg2[q], fmaf(b.w, pg1[q], b.z * pg0[q]));
-                const float dL = fmaf(Ti, cg, -(psg[q] * inv));
-                psg[q] = fmaf(w, cg, psg[q]);
-                pT[q] = u[q] ? Ti : pT[q];
-                const float t = Gq * dL;            // dL/do contribution
-                r[5] += t;
-                const float dp = b.y * t;           // dL/dpower
-                D += dp;
-                My = fmaf(dp, dy[q], My);
-                Myy = fmaf(dp, yy[q], Myy);
+                const float cg = fmaf(sb_Cb(sb, jj), pg2[0], fmaf(b.w, pg1[0], b.z * pg0[0]));
+                const float dL = fmaf(Ti, cg, -(psg[0] * inv));
+                psg[0] = fmaf(w, cg, psg[0]);
+                pT[0] = u ? Ti : pT[0];
+                const float t = Gq * dL;                   // dL/do contribution
+                const float dp = b.y * t;                  // dL/dpower
+                r[0] = dx * dp;
+                r[1] = dp * dy;
+                r[2] = dxx * dp;
+                r[3] = dx * r[1];
+                r[4] = dp * yy;
+                r[5] = t;
+                r[6] = w * pg0[0];
+                r[7] = w * pg1[0];
+                r[8] = w * pg2[0];
             }
-            r[0] = dx * D;      // sum dp dx
-            r[1] = My;          // sum dp dy
-            r[2] = dxx * D;     // sum dp dx^2
-            r[3] = dx * My;     // sum dp dx dy
-            r[4] = Myy;         // sum dp dy^2
             // transposed reduce-scatter of r[0..7]: afterwards lane L (L % 4 == 0)
             // holds the warp sum of component comp(L)
 #pragma unroll
@@ -938,7 +1066,8 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         // dpower/d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2))
         for (int j = threadIdx.x; j < cnt; j += NT) {
             const float* acc = s_acc + j * 9;
-            const float ca = sb.A[j].z * GS_IKA, cb_ = sb.A[j].w * GS_IKB, cc = sb.B[j].x * GS_IKA;
+            const float ca = f2_lo(sb.P0[j].y) * GS_IKA, cb_ = f2_lo(sb.P1[j].y) * GS_IKB,
+                        cc = f2_lo(sb.P2[j].x) * GS_IKA;
             const float Mx = acc[0], My = acc[1];
             const float4 ga = make_float4(fmaf(ca, Mx, cb_ * My), fmaf(cb_, Mx, cc * My), -0.5f * acc[2], -acc[3]);
             const float4 gb = make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]);
