@@ -2,13 +2,15 @@
 // reverse-replay backward (the prior art's gradients w.r.t. the 2D splat
 // parameters, the inputs of the pose chain rule of Sec. 3.2).
 //
-// One CTA per 16x16 tile, one pixel per thread.  The tile's depth-sorted list
-// is consumed in batches of 256 splats staged in shared memory; each thread
-// walks the batch for its pixel.  The forward stops a pixel before the splat
-// that would bring its transmittance below t_min and the CTA leaves once every
-// pixel has stopped.  The backward walks the same lists back to front from
-// each pixel's last blended entry, rebuilding T by division, and reduces every
-// splat's nine 2D gradients over the warp before one vector atomic per warp.
+// One CTA per 16x16 tile.  The forward consumes the tile's depth-sorted list
+// in batches of 128 splats staged in shared memory; each warp compacts a batch
+// to the entries that can reach its pixel block and walks them in lock step,
+// a pixel stopping before the splat that would bring its transmittance below
+// t_min, and the CTA leaves once every pixel has stopped.  The backward walks
+// the same lists back to front from each pixel's last blended entry,
+// rebuilding T by division; with two pixels per thread each warp stages its
+// own 32-entry chunks (no block barrier), and every splat's nine 2D gradients
+// are reduced over the warp before one set of vector atomics per warp.
 #include <cuda_runtime.h>
 
 #include "gs_block_sort.cuh"
@@ -75,6 +77,18 @@ struct SplatBatch {
     float Qt[BATCH];   // widened bound on the conic's quadratic form at such pixels (INFINITY: no bound)
 };
 
+// Per-warp chunk of WCH staged entries (the records as in SplatBatch) and the
+// warp's accumulator slots, nine per entry, of the backward.
+#define WCH 32
+struct WarpChunk {
+    ulonglong2 P0[WCH];
+    ulonglong2 P1[WCH];
+    ulonglong2 P2[WCH];
+    ulonglong2 P3[WCH];
+    f2_t P4[WCH];
+    float acc[WCH * 9];
+};
+
 // Entry j as the scalar records A = (mu.x, mu.y, a', b'), B = (c', o, r, g)
 // and blue.
 __device__ __forceinline__ float4 sb_A(const SplatBatch& sb, int j) {
@@ -131,17 +145,36 @@ __device__ __forceinline__ float ellipse_bound(const float4 a, const float4 b, f
 #define GS_IKA (-1.38629436111989061f)  // 1 / GS_KA = -2 ln 2
 #define GS_IKB (-0.69314718055994531f)  // 1 / GS_KB = -ln 2
 
-// Stages batch entry j: splat records a = (mu.x, mu.y, a, b), b = (c, o, r, g),
-// cb = blue; the culling bounds from the unscaled conic, then the scaled one.
-__device__ __forceinline__ void stage_entry(SplatBatch& sb, int j, float4 a, float4 b, float cb, float amin) {
-    sb.H[j] = alpha_box(a, b, amin);
-    sb.Qt[j] = GS_KA * ellipse_bound(a, b, amin);   // -INFINITY: no bound
-    const float ca = a.z * GS_KA, cbb = a.w * GS_KB, cc = b.x * GS_KA;
-    sb.P0[j] = make_ulonglong2(f2_pack(a.x, a.x), f2_pack(ca, ca));
-    sb.P1[j] = make_ulonglong2(f2_pack(a.y, a.y), f2_pack(cbb, cbb));
-    sb.P2[j] = make_ulonglong2(f2_pack(cc, cc), f2_pack(b.y, b.y));
+// Culling bounds of a splat record a = (mu.x, mu.y, a, b), b = (c, o, r, g)
+// from its conic, which is then scaled in place (a.z, a.w, b.x).
+__device__ __forceinline__ void stage_prepare(float4& a, float4& b, float amin, float2& h, float& qt) {
+    h = alpha_box(a, b, amin);
+    qt = GS_KA * ellipse_bound(a, b, amin);   // -INFINITY: no bound
+    a.z *= GS_KA;
+    a.w *= GS_KB;
+    b.x *= GS_KA;
+}
+
+// Stores the prepared record (scaled conic) as entry j of a batch in pairs;
+// cb = blue.
+template <class Batch>
+__device__ __forceinline__ void stage_store(Batch& sb, int j, const float4 a, const float4 b, float cb) {
+    sb.P0[j] = make_ulonglong2(f2_pack(a.x, a.x), f2_pack(a.z, a.z));
+    sb.P1[j] = make_ulonglong2(f2_pack(a.y, a.y), f2_pack(a.w, a.w));
+    sb.P2[j] = make_ulonglong2(f2_pack(b.x, b.x), f2_pack(b.y, b.y));
     sb.P3[j] = make_ulonglong2(f2_pack(b.z, b.z), f2_pack(b.w, b.w));
     sb.P4[j] = f2_pack(cb, cb);
+}
+
+// Stages batch entry j: culling bounds from the unscaled conic, then the
+// scaled record.
+__device__ __forceinline__ void stage_entry(SplatBatch& sb, int j, float4 a, float4 b, float cb, float amin) {
+    float2 h;
+    float qt;
+    stage_prepare(a, b, amin, h, qt);
+    sb.H[j] = h;
+    sb.Qt[j] = qt;
+    stage_store(sb, j, a, b, cb);
 }
 
 // Splat record A of entry k with its projected mean moved to the tile origin
@@ -177,47 +210,48 @@ __device__ __forceinline__ float warp_y0(int tid) { return (float)((tid >> 6) * 
 // alone reaches the footprint: about a fifth of the box hits for the
 // rotated, elongated splats of real scenes.
 // Returns the number of entries written to wl.
+// Footprint test of one staged entry: a = (mu.x, mu.y, a', b') and c' the
+// scaled conic, h its alpha box, qt its scaled ellipse bound (-INFINITY: none).
+__device__ __forceinline__ bool footprint_hit(const float4 a, float cc, const float2 h, float qt, float fx0, float fy0,
+                                              int fh) {
+    const float fx1 = fx0 + (float)(WARP_W - 1), fy1 = fy0 + (float)(fh - 1);
+    bool hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx1) && (a.y + h.y + 0.01f >= fy0) &&
+               (a.y - h.y - 0.01f <= fy1);
+    if (hit && qt > -INFINITY) {
+        // Maximum of the scaled exponent p(d) = a' dx^2 + b' dx dy + c' dy^2
+        // (d = p - mu; -L/2 times the quadratic form q) over the
+        // footprint.  With the centre outside, a concave p is largest on
+        // an edge whose outside holds the centre: on such an edge the
+        // other offset is the 1D maximiser clamped to the edge.
+        const float dxl = fx0 - a.x, dxr = fx1 - a.x, dyl = fy0 - a.y, dyr = fy1 - a.y;
+        float best = 0.0f;
+        const bool ox = dxl > 0.0f || dxr < 0.0f, oy = dyl > 0.0f || dyr < 0.0f;
+        if (ox || oy) best = -INFINITY;
+        // (the 1D maximiser needs no exact quotient: an error e in it
+        // lowers p by only |c'| e^2, far inside the bound's 2% margin,
+        // and the p evaluated is that of a point of the edge either way)
+        if (ox) {
+            const float dx = dxl > 0.0f ? dxl : dxr;
+            const float dy = fminf(fmaxf(__fdividef(-0.5f * a.w * dx, cc), dyl), dyr);
+            best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
+        }
+        if (oy) {
+            const float dy = dyl > 0.0f ? dyl : dyr;
+            const float dx = fminf(fmaxf(__fdividef(-0.5f * a.w * dy, a.z), dxl), dxr);
+            best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
+        }
+        hit = best >= qt;
+    }
+    return hit;
+}
+
 __device__ __forceinline__ int warp_compact(const SplatBatch& sb, int cnt, float fx0, float fy0,
                                             unsigned char* wl, int fh = WARP_H) {
     const int lane = threadIdx.x & 31;
     int n = 0;
     for (int r = 0; r < cnt; r += 32) {
         const int e = r + lane;
-        bool hit = false;
-        if (e < cnt) {
-            const float4 a = sb_A(sb, e);
-            const float2 h = sb.H[e];
-            const float fx1 = fx0 + (float)(WARP_W - 1), fy1 = fy0 + (float)(fh - 1);
-            hit = (a.x + h.x + 0.01f >= fx0) && (a.x - h.x - 0.01f <= fx1) &&
-                  (a.y + h.y + 0.01f >= fy0) && (a.y - h.y - 0.01f <= fy1);
-            const float qt = sb.Qt[e];
-            if (hit && qt > -INFINITY) {
-                // Maximum of the scaled exponent p(d) = a' dx^2 + b' dx dy + c' dy^2
-                // (d = p - mu; -L/2 times the quadratic form q) over the
-                // footprint.  With the centre outside, a concave p is largest on
-                // an edge whose outside holds the centre: on such an edge the
-                // other offset is the 1D maximiser clamped to the edge.
-                const float cc = f2_lo(sb.P2[e].x);
-                const float dxl = fx0 - a.x, dxr = fx1 - a.x, dyl = fy0 - a.y, dyr = fy1 - a.y;
-                float best = 0.0f;
-                const bool ox = dxl > 0.0f || dxr < 0.0f, oy = dyl > 0.0f || dyr < 0.0f;
-                if (ox || oy) best = -INFINITY;
-                // (the 1D maximiser needs no exact quotient: an error e in it
-                // lowers p by only |c'| e^2, far inside the bound's 2% margin,
-                // and the p evaluated is that of a point of the edge either way)
-                if (ox) {
-                    const float dx = dxl > 0.0f ? dxl : dxr;
-                    const float dy = fminf(fmaxf(__fdividef(-0.5f * a.w * dx, cc), dyl), dyr);
-                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
-                }
-                if (oy) {
-                    const float dy = dyl > 0.0f ? dyl : dyr;
-                    const float dx = fminf(fmaxf(__fdividef(-0.5f * a.w * dy, a.z), dxl), dxr);
-                    best = fmaxf(best, fmaf(a.z * dx, dx, fmaf(a.w * dx, dy, cc * dy * dy)));
-                }
-                hit = best >= qt;
-            }
-        }
+        const bool hit = e < cnt && footprint_hit(sb_A(sb, e), f2_lo(sb.P2[e].x), sb.H[e], sb.Qt[e], fx0, fy0, fh);
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) wl[n + __popc(m & ((1u << lane) - 1u))] = (unsigned char)e;
         n += __popc(m);
@@ -796,18 +830,61 @@ struct BwdPixel {
     bool inside;
 };
 
-// PX pixels per thread (1 or 2): each warp covers an 8 x (4 PX) pixel block,
-// 8 / PX warps a tile.  With two pixels a lane sums both pixels' contributions
-// before the warp reduction, so one reduction serves 64 pixels.
-template <int PX, bool CNT>
-__global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd(
+// Per-pixel setup of the backward blend: T_final, n_contrib and dL/dC at
+// pixel (px, py) of view vd (a given dL/dC, the L1 term of Eq. 16 or its
+// confidence-masked form of Eq. 20-21), with the pixel's L1 sum added to l1.
+__device__ __forceinline__ BwdPixel bwd_pixel(const ViewDev& vd, int px, int py, const RenderParams& rp,
+                                              const float* __restrict__ image, const float* __restrict__ T_final,
+                                              const uint32_t* __restrict__ n_contrib, int loss_kind, float w_l1,
+                                              float l1_mask_t, const float* __restrict__ target,
+                                              const float* __restrict__ dldc, float& l1) {
+    BwdPixel P;
+    const int W = vd.W, H = vd.H;
+    P.inside = px < W && py < H;
+    P.T = 1.0f; P.g0 = P.g1 = P.g2 = 0.0f; P.last = 0;
+    if (P.inside) {
+        const size_t p = (size_t)py * W + px;
+        const size_t np = (size_t)W * H;
+        P.T = T_final[vd.pix_off + p];
+        P.last = n_contrib[vd.pix_off + p];
+        const float* img = image + vd.img_off;
+        if (loss_kind == GS_LOSS_DLDC || loss_kind == GS_LOSS_L1_DSSIM) {
+            const float* d = dldc + vd.img_off;
+            P.g0 = d[p]; P.g1 = d[np + p]; P.g2 = d[2 * np + p];
+        }
+        // L1 term (Eq. 16), or its confidence-masked form (Eq. 20-21): pixels
+        // whose accumulated alpha 1 - T is not above the mask threshold
+        // contribute nothing
+        if ((loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM || loss_kind == GS_LOSS_L1_MASKED) &&
+            P.T < l1_mask_t) {
+            const float* tg = target + vd.img_off;
+            const float sc = w_l1 * vd.inv_npix3;
+            const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
+            P.g0 += d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+            P.g1 += d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+            P.g2 += d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+            l1 += fabsf(d0) + fabsf(d1) + fabsf(d2);
+        }
+    }
+    // dL/dC . (colour accumulated behind the current splat), starting with
+    // the background: sg = sum_{behind} w_j (c_j . g) + T_final (bg . g)
+    P.sg = P.T * (rp.bg[0] * P.g0 + rp.bg[1] * P.g1 + rp.bg[2] * P.g2);
+    if (!(P.inside && ((P.g0 != 0.f) | (P.g1 != 0.f) | (P.g2 != 0.f)))) P.last = 0;  // takes no part
+    return P;
+}
+
+// One pixel per thread in block-wide batches: 8 warps per tile, each an 8 x 4
+// pixel block (the two-pixel form is k_blend_bwd_warp).
+template <bool CNT>
+__global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
     const float* __restrict__ image, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
     int loss_kind, float w_l1, float l1_mask_t, const float* __restrict__ target, const float* __restrict__ dldc,
     Grad2DArrays g2d, float* __restrict__ tile_loss, unsigned long long* __restrict__ counters) {
-    constexpr int NT = GS_TILE_PIX / PX;   // threads
-    constexpr int NW = NT / 32;            // warps
+    constexpr int PX = 1;
+    constexpr int NT = GS_TILE_PIX;   // threads
+    constexpr int NW = NT / 32;       // warps
     __shared__ SplatBatch sb;
     __shared__ uint32_t s_idx[BATCH];
     __shared__ uint32_t s_max[NW];
@@ -816,7 +893,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
     const int t = blockIdx.x;
     const int v = view_of_tile(tile_base, n_views, t);
     const ViewDev& vd = views[v];
-    const int W = vd.W, H = vd.H, gw = vd.gw;
+    const int gw = vd.gw;
     const int lt = t - vd.tile_base;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // warp footprint origin and this lane's first pixel (tile-relative)
@@ -833,40 +910,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
     BwdPixel pix[PX];
     float l1 = 0.0f;
 #pragma unroll
-    for (int q = 0; q < PX; q++) {
-        BwdPixel& P = pix[q];
-        const int px = tx0 + lx, py = ty0 + ly + WARP_H * q;
-        P.inside = px < W && py < H;
-        P.T = 1.0f; P.g0 = P.g1 = P.g2 = 0.0f; P.last = 0;
-        if (P.inside) {
-            const size_t p = (size_t)py * W + px;
-            const size_t np = (size_t)W * H;
-            P.T = T_final[vd.pix_off + p];
-            P.last = n_contrib[vd.pix_off + p];
-            const float* img = image + vd.img_off;
-            if (loss_kind == GS_LOSS_DLDC || loss_kind == GS_LOSS_L1_DSSIM) {
-                const float* d = dldc + vd.img_off;
-                P.g0 = d[p]; P.g1 = d[np + p]; P.g2 = d[2 * np + p];
-            }
-            // L1 term (Eq. 16), or its confidence-masked form (Eq. 20-21): pixels
-            // whose accumulated alpha 1 - T is not above the mask threshold
-            // contribute nothing
-            if ((loss_kind == GS_LOSS_L1 || loss_kind == GS_LOSS_L1_DSSIM || loss_kind == GS_LOSS_L1_MASKED) &&
-                P.T < l1_mask_t) {
-                const float* tg = target + vd.img_off;
-                const float sc = w_l1 * vd.inv_npix3;
-                const float d0 = img[p] - tg[p], d1 = img[np + p] - tg[np + p], d2 = img[2 * np + p] - tg[2 * np + p];
-                P.g0 += d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
-                P.g1 += d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
-                P.g2 += d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
-                l1 += fabsf(d0) + fabsf(d1) + fabsf(d2);
-            }
-        }
-        // dL/dC . (colour accumulated behind the current splat), starting with
-        // the background: sg = sum_{behind} w_j (c_j . g) + T_final (bg . g)
-        P.sg = P.T * (rp.bg[0] * P.g0 + rp.bg[1] * P.g1 + rp.bg[2] * P.g2);
-        if (!(P.inside && ((P.g0 != 0.f) | (P.g1 != 0.f) | (P.g2 != 0.f)))) P.last = 0;  // takes no part
-    }
+    for (int q = 0; q < PX; q++)
+        pix[q] = bwd_pixel(vd, tx0 + lx, ty0 + ly + WARP_H * q, rp, image, T_final, n_contrib, loss_kind, w_l1,
+                           l1_mask_t, target, dldc, l1);
     if (tile_loss) {
         float r = l1;
 #pragma unroll
@@ -909,12 +955,6 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
         fpy[q] = (float)(ly + WARP_H * q);
     }
     const float amin = rp.alpha_min, amax = rp.alpha_max;
-    // two-pixel state in pairs (used when PX == 2)
-    const f2_t fpx2 = f2_pack(fpx, fpx), fpy2 = f2_pack(fpy[0], fpy[PX - 1]);
-    const f2_t one2 = f2_pack(1.0f, 1.0f);
-    const f2_t g0_2 = f2_pack(pg0[0], pg0[PX - 1]), g1_2 = f2_pack(pg1[0], pg1[PX - 1]),
-               g2_2 = f2_pack(pg2[0], pg2[PX - 1]);
-    f2_t pT2 = f2_pack(pT[0], pT[PX - 1]), S2 = f2_pack(psg[0], psg[PX - 1]);
     for (int bend = (int)tile_last; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
@@ -940,59 +980,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
             // Myy = sum dp dy^2 (its pixels share dx); the conic and mean
             // gradients are linear in the moments and formed once per splat.
             float r[9];
-            if constexpr (PX == 2) {
-                const bool u0 = pos < plast[0], u1 = pos < plast[1];
-                if (!__any_sync(0xffffffffu, u0 || u1)) continue;
-                // alpha of both pixels (Eq. 3) with pair_alpha's operation
-                // sequence, paired: the lanes of each pair share dx
-                const ulonglong2 p0 = sb.P0[jj], p1 = sb.P1[jj], p2 = sb.P2[jj];
-                const f2_t dx2 = f2_sub(fpx2, p0.x), dy2 = f2_sub(fpy2, p1.x);
-                const f2_t dxx2 = f2_mul(dx2, dx2), yy2 = f2_mul(dy2, dy2);
-                const f2_t pw2 = f2_fma(p1.y, f2_mul(dx2, dy2), f2_fma(p2.x, yy2, f2_mul(p0.y, dxx2)));
-                const float pw0 = f2_lo(pw2), pw1 = f2_hi(pw2);
-                const float G0 = fast_exp2(pw0), G1 = fast_exp2(pw1);
-                const f2_t ar2 = f2_mul(p2.y, f2_pack(G0, G1));
-                const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
-                const bool cl0 = ar0 > amax, cl1 = ar1 > amax;
-                const float al0 = cl0 ? amax : ar0, al1 = cl1 ? amax : ar1;
-                const bool v0 = u0 && !(pw0 > 0.0f) && al0 >= amin;
-                const bool v1 = u1 && !(pw1 > 0.0f) && al1 >= amin;
-                if (CNT) {
-                    const float2 h = sb.H[jj];
-                    const bool inx = fabsf(f2_lo(dx2)) <= h.x;
-                    const bool b0 = u0 && inx && fabsf(f2_lo(dy2)) <= h.y;
-                    const bool b1 = u1 && inx && fabsf(f2_hi(dy2)) <= h.y;
-                    n_eval += b0 + b1;
-                    n_w1 += __any_sync(0xffffffffu, b0 || b1) ? 1u : 0u;
-                }
-                if (!__any_sync(0xffffffffu, v0 || v1)) continue;
-                if (CNT) { n_w2++; n_used += v0 + v1; }
-                const f2_t alq2 = f2_pack(v0 ? al0 : 0.0f, v1 ? al1 : 0.0f);
-                const f2_t Gq2 = f2_pack((v0 && !cl0) ? G0 : 0.0f, (v1 && !cl1) ? G1 : 0.0f);
-                const f2_t om2 = f2_sub(one2, alq2);   // 1 - alpha lies in [0.01, 1]
-                const f2_t inv2 = f2_pack(fast_rcp(f2_lo(om2)), fast_rcp(f2_hi(om2)));
-                const f2_t Ti2 = f2_mul(pT2, inv2);
-                const f2_t w2 = f2_mul(alq2, Ti2);
-                const ulonglong2 p3 = sb.P3[jj];
-                const f2_t cg2 = f2_fma(sb.P4[jj], g2_2, f2_fma(p3.y, g1_2, f2_mul(p3.x, g0_2)));
-                const f2_t dL2 = f2_sub(f2_mul(Ti2, cg2), f2_mul(S2, inv2));
-                S2 = f2_fma(w2, cg2, S2);
-                pT2 = f2_pack(v0 ? f2_lo(Ti2) : f2_lo(pT2), v1 ? f2_hi(Ti2) : f2_hi(pT2));
-                const f2_t t2 = f2_mul(Gq2, dL2);      // dL/do contributions
-                const f2_t dp2 = f2_mul(p2.y, t2);     // dL/dpower
-                const f2_t My2 = f2_mul(dp2, dy2), Myy2 = f2_mul(dp2, yy2);
-                const f2_t c0 = f2_mul(w2, g0_2), c1 = f2_mul(w2, g1_2), c2 = f2_mul(w2, g2_2);
-                const float dx = f2_lo(dx2), D = f2_lo(dp2) + f2_hi(dp2), My = f2_lo(My2) + f2_hi(My2);
-                r[0] = dx * D;                          // sum dp dx
-                r[1] = My;                              // sum dp dy
-                r[2] = f2_lo(dxx2) * D;                 // sum dp dx^2
-                r[3] = dx * My;                         // sum dp dx dy
-                r[4] = f2_lo(Myy2) + f2_hi(Myy2);       // sum dp dy^2
-                r[5] = f2_lo(t2) + f2_hi(t2);
-                r[6] = f2_lo(c0) + f2_hi(c0);
-                r[7] = f2_lo(c1) + f2_hi(c1);
-                r[8] = f2_lo(c2) + f2_hi(c2);
-            } else {
+            {
                 const float4 a = sb_A(sb, jj);
                 const float2 h = sb.H[jj];
                 const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy[0], a.y);
@@ -1097,22 +1085,244 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 6 : 9) k_blend_bwd
     }
 }
 
+// Backward blend in per-warp chunks (two pixels per thread, 4 warps per
+// tile, each warp an 8 x 8 pixel block).  Every warp walks the tile's list
+// back to front from the longest prefix its own pixels use, in chunks of 32
+// entries that it stages itself: lane l stages entry l of the chunk and tests
+// it against the warp's footprint from the values it staged, so no entry list
+// and no block barrier is needed and the warps of a tile never wait for one
+// another.  A warp's nine reduced sums of an entry go to its own accumulator
+// slots; the lanes then flush the chunk's entries in parallel, one set of
+// vector atomics per (warp, splat).
+template <bool CNT>
+__global__ void __launch_bounds__(GS_TILE_PIX / 2, 9) k_blend_bwd_warp(
+    int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
+    int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
+    const float* __restrict__ image, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+    int loss_kind, float w_l1, float l1_mask_t, const float* __restrict__ target, const float* __restrict__ dldc,
+    Grad2DArrays g2d, float* __restrict__ tile_loss, unsigned long long* __restrict__ counters) {
+    constexpr int NT = GS_TILE_PIX / 2;   // threads
+    constexpr int NW = NT / 32;           // warps
+    __shared__ WarpChunk s_wc[NW];
+    __shared__ uint32_t s_red[NW];
+    const int t = blockIdx.x;
+    const int v = view_of_tile(tile_base, n_views, t);
+    const ViewDev& vd = views[v];
+    const int gw = vd.gw;
+    const int lt = t - vd.tile_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // warp footprint origin and this lane's first pixel (tile-relative)
+    const int wx0 = (wid & 1) * WARP_W, wy0 = (wid >> 1) * (WARP_H * 2);
+    const int lx = wx0 + (lane & (WARP_W - 1)), ly = wy0 + (lane >> 3);
+    const int tx0 = (lt % gw) * GS_TILE, ty0 = (lt / gw) * GS_TILE;
+    // tile-relative pixel coordinates (the staged means are moved to the same origin)
+    const float ox = (float)tx0, oy = (float)ty0;
+    uint32_t s = starts[t], e = starts[t + 1];
+    if (s > cap) s = cap;
+    if (e > cap) e = cap;
+    const size_t vbase = (size_t)v * n;
+    float l1 = 0.0f;
+    const BwdPixel P0 = bwd_pixel(vd, tx0 + lx, ty0 + ly, rp, image, T_final, n_contrib, loss_kind, w_l1, l1_mask_t,
+                                  target, dldc, l1);
+    const BwdPixel P1 = bwd_pixel(vd, tx0 + lx, ty0 + ly + WARP_H, rp, image, T_final, n_contrib, loss_kind, w_l1,
+                                  l1_mask_t, target, dldc, l1);
+    if (tile_loss) {
+        const float r = warp_sum(l1);
+        if (lane == 0) s_red[wid] = __float_as_uint(r);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.0f;
+            for (int w = 0; w < NW; w++) acc += __uint_as_float(s_red[w]);
+            tile_loss[t] = acc;
+        }
+        __syncthreads();
+    }
+    // longest list prefix used by a pixel of this warp
+    uint32_t wlast = max(P0.last, P1.last);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    if (wlast > e - s) wlast = e - s;
+    if (CNT) {
+        // list entries the tile reads: the longest of its warps' prefixes
+        if (lane == 0) s_red[wid] = wlast;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t m = 0;
+            for (int w = 0; w < NW; w++) m = max(m, s_red[w]);
+            atomicAdd(counters + 4, (unsigned long long)m);
+        }
+    }
+    uint32_t n_eval = 0, n_used = 0, n_w1 = 0, n_w2 = 0;
+    // component held by this lane after the transposed reduction
+    const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    const float amin = rp.alpha_min, amax = rp.alpha_max;
+    const float fx0 = (float)wx0, fy0 = (float)wy0;
+    // per-pixel state in pairs, walked in lock step: a pixel that takes no
+    // part in an entry gets alpha 0, so its state is unchanged and its share of
+    // every sum is 0
+    const f2_t fpx2 = f2_pack((float)lx, (float)lx), fpy2 = f2_pack((float)ly, (float)(ly + WARP_H));
+    const f2_t one2 = f2_pack(1.0f, 1.0f);
+    const f2_t g0_2 = f2_pack(P0.g0, P1.g0), g1_2 = f2_pack(P0.g1, P1.g1), g2_2 = f2_pack(P0.g2, P1.g2);
+    f2_t pT2 = f2_pack(P0.T, P1.T), S2 = f2_pack(P0.sg, P1.sg);
+    const uint32_t plast0 = P0.last, plast1 = P1.last;
+    WarpChunk& wc = s_wc[wid];
+    for (int cend = (int)wlast; cend > 0; cend -= WCH) {
+        const int cstart = max(0, cend - WCH);
+        __syncwarp();   // the previous chunk's flush has read the slots
+        // lane l stages entry cstart + l and tests it against the footprint
+        bool hit = false;
+        uint32_t id = 0;
+        if (cstart + lane < cend) {
+            id = sorted_idx[s + cstart + lane];
+            const size_t k = vbase + id;
+            float4 a = stage_mean(sp, k, ox, oy);
+            float4 b = sp.B[k];
+            float2 h;
+            float qt;
+            stage_prepare(a, b, amin, h, qt);
+            stage_store(wc, lane, a, b, sp.Cb[k]);
+            hit = footprint_hit(a, b.x, h, qt, fx0, fy0, WARP_H * 2);
+        }
+        unsigned mm = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
+        unsigned pm = 0;   // entries with a contributing pixel
+        while (mm) {
+            const int jj = 31 - __clz(mm);
+            mm &= ~(1u << jj);
+            const uint32_t pos = (uint32_t)(cstart + jj);
+            const bool u0 = pos < plast0, u1 = pos < plast1;
+            if (!__any_sync(0xffffffffu, u0 || u1)) continue;
+            // alpha of both pixels (Eq. 3) with pair_alpha's operation
+            // sequence, paired: the lanes of each pair share dx
+            const ulonglong2 p0 = wc.P0[jj], p1 = wc.P1[jj], p2 = wc.P2[jj];
+            const f2_t dx2 = f2_sub(fpx2, p0.x), dy2 = f2_sub(fpy2, p1.x);
+            const f2_t dxx2 = f2_mul(dx2, dx2), yy2 = f2_mul(dy2, dy2);
+            const f2_t pw2 = f2_fma(p1.y, f2_mul(dx2, dy2), f2_fma(p2.x, yy2, f2_mul(p0.y, dxx2)));
+            const float pw0 = f2_lo(pw2), pw1 = f2_hi(pw2);
+            const float G0 = fast_exp2(pw0), G1 = fast_exp2(pw1);
+            const f2_t ar2 = f2_mul(p2.y, f2_pack(G0, G1));
+            const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
+            const bool cl0 = ar0 > amax, cl1 = ar1 > amax;
+            const float al0 = cl0 ? amax : ar0, al1 = cl1 ? amax : ar1;
+            const bool v0 = u0 && !(pw0 > 0.0f) && al0 >= amin;
+            const bool v1 = u1 && !(pw1 > 0.0f) && al1 >= amin;
+            if (CNT) {
+                // pixels inside the splat's alpha box (recomputed from the record)
+                const float4 a = make_float4(f2_lo(p0.x), f2_lo(p1.x), f2_lo(p0.y) * GS_IKA, f2_lo(p1.y) * GS_IKB);
+                const float4 b = make_float4(f2_lo(p2.x) * GS_IKA, f2_lo(p2.y), 0.0f, 0.0f);
+                const float2 h = alpha_box(a, b, amin);
+                const bool inx = fabsf(f2_lo(dx2)) <= h.x;
+                const bool b0 = u0 && inx && fabsf(f2_lo(dy2)) <= h.y;
+                const bool b1 = u1 && inx && fabsf(f2_hi(dy2)) <= h.y;
+                n_eval += b0 + b1;
+                n_w1 += __any_sync(0xffffffffu, b0 || b1) ? 1u : 0u;
+            }
+            if (!__any_sync(0xffffffffu, v0 || v1)) continue;
+            if (CNT) { n_w2++; n_used += v0 + v1; }
+            pm |= 1u << jj;
+            const f2_t alq2 = f2_pack(v0 ? al0 : 0.0f, v1 ? al1 : 0.0f);
+            const f2_t Gq2 = f2_pack((v0 && !cl0) ? G0 : 0.0f, (v1 && !cl1) ? G1 : 0.0f);
+            const f2_t om2 = f2_sub(one2, alq2);   // 1 - alpha lies in [0.01, 1]
+            const f2_t inv2 = f2_pack(fast_rcp(f2_lo(om2)), fast_rcp(f2_hi(om2)));
+            const f2_t Ti2 = f2_mul(pT2, inv2);
+            const f2_t w2 = f2_mul(alq2, Ti2);
+            const ulonglong2 p3 = wc.P3[jj];
+            const f2_t cg2 = f2_fma(wc.P4[jj], g2_2, f2_fma(p3.y, g1_2, f2_mul(p3.x, g0_2)));
+            const f2_t dL2 = f2_sub(f2_mul(Ti2, cg2), f2_mul(S2, inv2));
+            S2 = f2_fma(w2, cg2, S2);
+            pT2 = f2_pack(v0 ? f2_lo(Ti2) : f2_lo(pT2), v1 ? f2_hi(Ti2) : f2_hi(pT2));
+            const f2_t t2 = f2_mul(Gq2, dL2);      // dL/do contributions
+            const f2_t dp2 = f2_mul(p2.y, t2);     // dL/dpower
+            const f2_t My2 = f2_mul(dp2, dy2), Myy2 = f2_mul(dp2, yy2);
+            const f2_t c0 = f2_mul(w2, g0_2), c1 = f2_mul(w2, g1_2), c2 = f2_mul(w2, g2_2);
+            const float dx = f2_lo(dx2), D = f2_lo(dp2) + f2_hi(dp2), My = f2_lo(My2) + f2_hi(My2);
+            float r[9];
+            r[0] = dx * D;                          // sum dp dx
+            r[1] = My;                              // sum dp dy
+            r[2] = f2_lo(dxx2) * D;                 // sum dp dx^2
+            r[3] = dx * My;                         // sum dp dx dy
+            r[4] = f2_lo(Myy2) + f2_hi(Myy2);       // sum dp dy^2
+            r[5] = f2_lo(t2) + f2_hi(t2);
+            r[6] = f2_lo(c0) + f2_hi(c0);
+            r[7] = f2_lo(c1) + f2_hi(c1);
+            r[8] = f2_lo(c2) + f2_hi(c2);
+            // transposed reduce-scatter of r[0..7]: afterwards lane L (L % 4 == 0)
+            // holds the warp sum of component comp(L)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const bool hi = lane & 16;
+                const float send = hi ? r[k] : r[k + 4];
+                const float keep = hi ? r[k + 4] : r[k];
+                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const bool hi = lane & 8;
+                const float send = hi ? r[k] : r[k + 2];
+                const float keep = hi ? r[k + 2] : r[k];
+                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            {
+                const bool hi = lane & 4;
+                const float send = hi ? r[0] : r[1];
+                const float keep = hi ? r[1] : r[0];
+                r[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            r[0] += __shfl_xor_sync(0xffffffffu, r[0], 2);
+            r[0] += __shfl_xor_sync(0xffffffffu, r[0], 1);
+            const float r8 = warp_sum(r[8]);
+            if ((lane & 3) == 0) wc.acc[jj * 9 + comp] = r[0];
+            if (lane == 1) wc.acc[jj * 9 + 8] = r8;
+        }
+        __syncwarp();
+        // lane l flushes entry l: the conic and mean gradients from the moments
+        // (power = -1/2 (a dx^2 + c dy^2) - b dx dy, d = p - mu:
+        // dpower/dmu = (a dx + b dy, b dx + c dy), dpower/d(a, b, c) =
+        // (-dx^2 / 2, -dx dy, -dy^2 / 2))
+        if ((pm >> lane) & 1u) {
+            const float* acc = wc.acc + lane * 9;
+            const float ca = f2_lo(wc.P0[lane].y) * GS_IKA, cb_ = f2_lo(wc.P1[lane].y) * GS_IKB,
+                        cc = f2_lo(wc.P2[lane].x) * GS_IKA;
+            const float Mx = acc[0], My = acc[1];
+            const float4 ga = make_float4(fmaf(ca, Mx, cb_ * My), fmaf(cb_, Mx, cc * My), -0.5f * acc[2], -acc[3]);
+            const float4 gb = make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]);
+            const size_t k = vbase + id;
+            atomicAdd(g2d.gA + k, ga);
+            atomicAdd(g2d.gB + k, gb);
+            atomicAdd(g2d.gC + k, acc[8]);
+        }
+    }
+    if (CNT) {
+        unsigned long long ce = n_eval, cu = n_used;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ce += __shfl_xor_sync(0xffffffffu, ce, o);
+            cu += __shfl_xor_sync(0xffffffffu, cu, o);
+        }
+        if (lane == 0) {
+            atomicAdd(counters, ce);
+            atomicAdd(counters + 1, cu);
+            atomicAdd(counters + 7, (unsigned long long)n_w1);   // warp-entries with a pixel in the box
+            atomicAdd(counters + 8, (unsigned long long)n_w2);   // warp-entries with a contributing pixel
+        }
+    }
+}
+
 void launch_blend_bwd(int n_tiles, int n_views, const int* tile_base, const ViewDev* views, const RenderParams& rp,
                       SplatArrays sp, int n, const uint32_t* starts, const uint32_t* sorted_idx, uint32_t cap,
                       const float* image, const float* T_final, const uint32_t* n_contrib, int loss_kind, float w_l1,
                       float l1_mask_t, const float* target, const float* dldc, Grad2DArrays g2d, float* tile_loss,
                       unsigned long long* counters, int px_per_thread, cudaStream_t s) {
     if (n_tiles <= 0) return;
-#define GS_BWD_LAUNCH(PX, CNT)                                                                                     \
-    k_blend_bwd<PX, CNT><<<n_tiles, GS_TILE_PIX / PX, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts,         \
-                                                              sorted_idx, cap, image, T_final, n_contrib, loss_kind, \
-                                                              w_l1, l1_mask_t, target, dldc, g2d, tile_loss, counters)
+#define GS_BWD_LAUNCH(KERNEL, NT)                                                                                   \
+    KERNEL<<<n_tiles, NT, 0, s>>>(n_views, tile_base, views, rp, sp, n, starts, sorted_idx, cap, image, T_final,     \
+                                  n_contrib, loss_kind, w_l1, l1_mask_t, target, dldc, g2d, tile_loss, counters)
     if (px_per_thread == 2) {
-        if (counters) GS_BWD_LAUNCH(2, true);
-        else GS_BWD_LAUNCH(2, false);
+        if (counters) GS_BWD_LAUNCH(k_blend_bwd_warp<true>, GS_TILE_PIX / 2);
+        else GS_BWD_LAUNCH(k_blend_bwd_warp<false>, GS_TILE_PIX / 2);
     } else {
-        if (counters) GS_BWD_LAUNCH(1, true);
-        else GS_BWD_LAUNCH(1, false);
+        if (counters) GS_BWD_LAUNCH(k_blend_bwd<true>, GS_TILE_PIX);
+        else GS_BWD_LAUNCH(k_blend_bwd<false>, GS_TILE_PIX);
     }
 #undef GS_BWD_LAUNCH
 }
