@@ -152,6 +152,65 @@ __device__ __forceinline__ void rect_of(const uint2 r, int& x0, int& y0, int& x1
 // is used, so that the loads overlap.
 #define CS_PREFETCH 4
 
+// Warp-cooperative key scatter.  The 32 lanes of a warp hold consecutive
+// Gaussians (Morton-ordered, so their rectangles cluster).  When the union of
+// the warp's rectangles spans at most GS_BIN_BOX tiles, the warp walks that
+// box: per tile, a ballot of the lanes whose rectangle covers it, and one
+// slot atomic by the first of them for all (instead of one returning atomic
+// per key, which the atomic unit serialises when lanes share a tile).  A wider
+// union falls back to each lane walking its own rectangle, whose per-tile
+// ballots would cost more than the atomics they save.  (The count pass keeps
+// one atomic per key: without a return value they are cheap.)
+#define GS_BIN_BOX 16
+
+// Union box of the valid rectangles of the warp; returns false when none.
+__device__ __forceinline__ bool warp_box(bool valid, int x0, int y0, int x1, int y1, int& bx0, int& by0, int& bx1,
+                                         int& by1) {
+    if (!__any_sync(0xffffffffu, valid)) return false;
+    bx0 = (int)__reduce_min_sync(0xffffffffu, valid ? (unsigned)x0 : 0xffffffffu);
+    by0 = (int)__reduce_min_sync(0xffffffffu, valid ? (unsigned)y0 : 0xffffffffu);
+    bx1 = (int)__reduce_max_sync(0xffffffffu, valid ? (unsigned)x1 : 0u);
+    by1 = (int)__reduce_max_sync(0xffffffffu, valid ? (unsigned)y1 : 0u);
+    return true;
+}
+
+// Scatters the lane's key to every tile of its rectangle at the slots that
+// hist (tile -> next global position) hands out; every lane of the warp
+// calls it.  over is set when a position reaches cap.
+__device__ __forceinline__ void warp_scatter(int x0, int y0, int x1, int y1, int gw, uint32_t* hist,
+                                             unsigned long long key, unsigned long long* __restrict__ keys,
+                                             uint32_t cap, bool& over) {
+    const bool valid = x1 > x0 && y1 > y0;
+    int bx0, by0, bx1, by1;
+    if (!warp_box(valid, x0, y0, x1, y1, bx0, by0, bx1, by1)) return;
+    if ((bx1 - bx0) * (by1 - by0) <= GS_BIN_BOX) {
+        const int lane = threadIdx.x & 31;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int ty = by0; ty < by1; ty++) {
+            const bool iny = valid && y0 <= ty && ty < y1;
+            for (int tx = bx0; tx < bx1; tx++) {
+                const bool cov = iny && x0 <= tx && tx < x1;
+                const unsigned m = __ballot_sync(0xffffffffu, cov);
+                if (!m) continue;
+                const int leader = __ffs(m) - 1;
+                uint32_t base = 0u;
+                if (lane == leader) base = atomicAdd(hist + ty * gw + tx, (uint32_t)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (cov) {
+                    const uint32_t pos = base + (uint32_t)__popc(m & lt);
+                    if (pos < cap) keys[pos] = key; else over = true;
+                }
+            }
+        }
+    } else {
+        for (int ty = y0; ty < y1; ty++)
+            for (int tx = x0; tx < x1; tx++) {
+                const uint32_t pos = atomicAdd(hist + ty * gw + tx, 1u);
+                if (pos < cap) keys[pos] = key; else over = true;
+            }
+    }
+}
+
 // Adds every key of this thread's entries of [i0, i1) to the shared histogram.
 __device__ __forceinline__ void chunk_histogram(const uint2* __restrict__ rect, size_t vb, int i0, int i1, int gw,
                                                 uint32_t* hist) {
@@ -266,7 +325,12 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, 
         }
     }
     __syncthreads();
-    for (int i = i0 + threadIdx.x; i < i1; i += CS_THREADS * CS_PREFETCH) {
+    bool over = false;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform bases (lane i = base + lane), so that every lane takes part
+    // in the warp's ballots; entries past the chunk get an empty rectangle
+    for (int ib = i0 + (int)(threadIdx.x & ~31u); ib < i1; ib += CS_THREADS * CS_PREFETCH) {
+        const int i = ib + lane;
         uint2 r[CS_PREFETCH];
         float dz[CS_PREFETCH];
 #pragma unroll
@@ -281,13 +345,10 @@ __global__ void __launch_bounds__(CS_THREADS) k_scatter_tiles(int n, int chunk, 
             rect_of(r[u], x0, y0, x1, y1);
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(dz[u]) << 32) | (uint32_t)(i + u * CS_THREADS);
-            for (int ty = y0; ty < y1; ty++)
-                for (int tx = x0; tx < x1; tx++) {
-                    const uint32_t pos = atomicAdd(hist + ty * gw + tx, 1u);
-                    if (pos < cap) keys[pos] = key; else s_over = 1;
-                }
+            warp_scatter(x0, y0, x1, y1, gw, hist, key, keys, cap, over);
         }
     }
+    if (over) s_over = 1;
     __syncthreads();
     if (threadIdx.x == 0 && s_over) gs_set_status(status, GS_DEV_OVERFLOW);
 }
