@@ -739,12 +739,11 @@ static void launch_lazy_cnt(int n_tiles, int n_views, const int* tile_base, cons
                             uint32_t* sorted_count, uint32_t cap, float* image, float* T_final, uint32_t* n_contrib,
                             const float* target, float* tile_loss, unsigned long long* counters, cudaStream_t s) {
     constexpr int NT = GS_TILE_PIX / PX;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [](int) {
         cudaFuncSetAttribute(k_blend_fwd_lazy<CAP, PX, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(LazySmem<CAP, NT>));
-        attr = true;
-    }
+    });
     k_blend_fwd_lazy<CAP, PX, CNT><<<n_tiles, NT, sizeof(LazySmem<CAP, NT>), s>>>(
         n_views, tile_base, views, rp, sp, n, starts, keys, tmp, sorted_idx, sorted_count, cap, image, T_final,
         n_contrib, target, tile_loss, counters);

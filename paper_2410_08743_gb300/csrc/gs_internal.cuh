@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "gsplat.h"
 
 #define GS_TILE 16
@@ -110,6 +112,20 @@ __device__ __forceinline__ float fast_rcp(float x) {
 // ------------------------------------------------------------ kernel entry
 // Host-side launchers (defined in the .cu files).
 namespace gs {
+
+// Runs set() the first time it is reached on the current device (kernel
+// attributes such as the dynamic shared-memory limit are per device); safe to
+// reach from several threads, where set() may run more than once (it only
+// sets the same values).
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long>& done, F set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    set(dev);
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 void launch_setup_views(const gs_view* dummy, int n_views, const double* poses, ViewDev* views_dev,
                         const RenderParams& rp, cudaStream_t s);

@@ -312,24 +312,48 @@ __device__ __forceinline__ void project_ff(float xh, float xl, float zh, float z
 }
 
 // ------------------------------------------------------------ forward
+// 16-byte shared-memory read that the compiler keeps where it is written
+// (inside the view loop, not hoisted into 48 live registers).
+__device__ __forceinline__ float4 lds_f4(const float4* p) {
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
 // Gaussians [i_begin, i_end) of the scene (a launch may cover a slice, so that
-// the slices can start while later ones are still being uploaded).
+// the slices can start while later ones are still being uploaded), one per
+// thread, looping over the views (in shared memory); the thread's SH
+// coefficients are staged in shared memory once and read per view, which keeps
+// the kernel near 60 registers instead of 124.
 template <int D>
 __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int i_begin, int i_end, int n_views,
                                                         const ViewDev* __restrict__ views, RenderParams rp,
                                                         SplatArrays sp, uint32_t* __restrict__ tile_counts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ViewDev* sv = reinterpret_cast<ViewDev*>(smem_raw);
+    constexpr int NC = (D + 1) * (D + 1);
+    // the block's SH coefficients in groups of four, [group][thread]: the
+    // 16-byte reads of consecutive lanes are consecutive
+    constexpr int NG = (NC * 3 + 3) / 4;
+    float4* ssh = reinterpret_cast<float4*>(smem_raw + sizeof(ViewDev) * n_views);
     {
         const int words = n_views * (int)(sizeof(ViewDev) / 4);
         const int* src = reinterpret_cast<const int*>(views);
         int* dst = reinterpret_cast<int*>(sv);
         for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+        const int g0 = i_begin + blockIdx.x * blockDim.x;
+        const int ng = min((int)blockDim.x, i_end - g0);
+        const float4* shb = reinterpret_cast<const float4*>(sc.sh + (size_t)g0 * 48);
+        for (int w = threadIdx.x; w < ng * 12; w += blockDim.x) {
+            const int g = w / 12, k4 = w - g * 12;
+            if (k4 < NG) ssh[k4 * blockDim.x + g] = shb[w];
+        }
     }
     __syncthreads();
     const int i = i_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= i_end) return;
-    constexpr int NC = (D + 1) * (D + 1);
+    const float4* frow = ssh + threadIdx.x;
     float mu[3], s[3], q[4];
 #pragma unroll
     for (int k = 0; k < 3; k++) { mu[k] = sc.means[3 * i + k]; s[k] = sc.scales[3 * i + k]; }
@@ -338,10 +362,6 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int i_begin
         q[0] = qq.x; q[1] = qq.y; q[2] = qq.z; q[3] = qq.w;
     }
     const float op = sc.opac[i];
-    float f[NC * 3];
-    const float* fs = sc.sh + (size_t)i * 48;
-#pragma unroll
-    for (int k = 0; k < NC * 3; k++) f[k] = fs[k];
     float S[6];
     key_sigma(q, s, S);
     for (int v = 0; v < n_views; v++) {
@@ -362,14 +382,22 @@ __global__ void __launch_bounds__(256) k_preprocess_fwd(SceneDev sc, int i_begin
         dx *= il; dy *= il; dz *= il;
         float Y[16];
         sh_basis<D>(dx, dy, dz, Y);
-        float col[3];
+        // colour = sum_b f[b][ch] Y[b] + 1/2 per channel, in b order, the
+        // coefficients read from the shared row for each view (not kept live
+        // across the view loop)
+        float col[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float acc = 0.5f;
+        for (int k4 = 0; k4 < NG; k4++) {
+            const float4 v4 = lds_f4(frow + k4 * blockDim.x);
+            const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-            for (int b = 0; b < NC; b++) acc = fmaf(f[b * 3 + ch], Y[b], acc);
-            col[ch] = fmaxf(acc, 0.0f);
+            for (int e = 0; e < 4; e++) {
+                const int idx = 4 * k4 + e;
+                if (idx < NC * 3) col[idx % 3] = fmaf(vv[e], Y[idx / 3], col[idx % 3]);
+            }
         }
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) col[ch] = fmaxf(col[ch], 0.0f);
         {
             float xh, xl, yh, yl, zh, zl, mxh, mxl, myh, myl;
             cam_coord_ff(vd, 0, mu, xh, xl);
@@ -400,7 +428,16 @@ void launch_preprocess_fwd(const SceneDev& sc, int threads, int n_views, const V
     if (i_end <= i_begin || n_views <= 0) return;
     const int T = threads == 128 ? 128 : 256;
     const int grid = (i_end - i_begin + T - 1) / T;
-    const size_t sm = sizeof(ViewDev) * (size_t)n_views;
+    const int deg = sc.sh_degree < 3 ? sc.sh_degree : 3;
+    const size_t sm = sizeof(ViewDev) * (size_t)n_views + sizeof(float4) * ((3 * (deg + 1) * (deg + 1) + 3) / 4) * T;
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [](int) {
+        const int mx = 200 * 1024;
+        cudaFuncSetAttribute(k_preprocess_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_preprocess_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    });
 #define GS_PRE_FWD(D) k_preprocess_fwd<D><<<grid, T, sm, s>>>(sc, i_begin, i_end, n_views, views, rp, sp, tile_counts)
     switch (sc.sh_degree) {
         case 0: GS_PRE_FWD(0); break;
@@ -797,8 +834,8 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
     const int nc3 = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
     const size_t sm = ((sizeof(ViewDev) * n_views + 15) & ~(size_t)15) + sizeof(double) * (T / 32) * n_views * 6 +
                       sizeof(float) * nc3 * (T + 1) + 16 + (size_t)PB_STAGES * T * (16 + 16 + 4);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [](int) {
         const int mx = 200 * 1024;
         cudaFuncSetAttribute(k_preprocess_bwd<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_preprocess_bwd<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -808,8 +845,7 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
         cudaFuncSetAttribute(k_preprocess_bwd<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_preprocess_bwd<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_preprocess_bwd<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr = true;
-    }
+    });
     const bool po = !grads.means && !grads.scales && !grads.quats && !grads.opacities && !grads.sh;
 #define GS_PRE_BWD(D)                                                                                          \
     if (po)                                                                                                    \

@@ -509,29 +509,31 @@ __global__ void __launch_bounds__(LARGE_T) k_segsort_large(int n_tiles, const ui
     }
 }
 
-static int g_num_sms = 0;
 
 void launch_segment_sort(int n_tiles, const uint32_t* starts, unsigned long long* keys, unsigned long long* tmp_keys,
                          uint32_t* sorted_idx, uint32_t cap, uint32_t* lists, uint32_t* counters, cudaStream_t s) {
     if (n_tiles <= 0) return;
-    static bool attr_done = false;
+    static std::atomic<unsigned long long> attr_done{0};
+    static std::atomic<int> num_sms[64];   // SM count per device
     const size_t sm_small = 2 * sizeof(unsigned long long) * SMALL_CAP + sizeof(uint32_t) * (SMALL_T / 32) * 256;
     const size_t sm_med = 2 * sizeof(unsigned long long) * MED_CAP + sizeof(uint32_t) * (MED_T / 32) * 256;
     const size_t sm_large = 2 * sizeof(unsigned long long) * MED_CAP + sizeof(uint32_t) * (LARGE_T / 32) * 256;
-    if (!attr_done) {
+    once_per_device(attr_done, [&](int dev) {
         cudaFuncSetAttribute(k_segsort_list<SMALL_T, SMALL_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm_small);
         cudaFuncSetAttribute(k_segsort_list<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_med);
         cudaFuncSetAttribute(k_segsort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_large);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        attr_done = true;
-    }
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        num_sms[dev & 63].store(sms);
+    });
+    int dev = 0;
+    cudaGetDevice(&dev);
     // counters: [0..2] list lengths, [3..5] work cursors
     cudaMemsetAsync(counters, 0, 6 * sizeof(uint32_t), s);
     k_classify_tiles<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_tiles, starts, cap, keys, sorted_idx, lists, counters);
-    const int sms = g_num_sms > 0 ? g_num_sms : 152;
+    const int sms_seen = num_sms[dev & 63].load();
+    const int sms = sms_seen > 0 ? sms_seen : 152;
     k_segsort_large<<<sms * 2, LARGE_T, sm_large, s>>>(n_tiles, starts, cap, keys, tmp_keys, sorted_idx,
                                                        lists + 2 * (size_t)n_tiles, counters + 2, counters + 5);
     k_segsort_list<MED_T, MED_CAP><<<sms * 2, MED_T, sm_med, s>>>(n_tiles, starts, cap, keys, sorted_idx,
