@@ -493,7 +493,6 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
             if (CNT) n_went += (uint32_t)nw;
             if constexpr (PX == 2) {
                 for (int qq = 0; qq < nw; qq++) {
-                    if (__all_sync(0xffffffffu, done[0] && done[1])) break;
                     const int jj = wl[qq];
                     const uint32_t pos1 = base + (uint32_t)jj + 1u;
                     const ulonglong2 p0 = sm.u.sb.P0[jj], p1 = sm.u.sb.P1[jj], p2 = sm.u.sb.P2[jj];
@@ -505,16 +504,22 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
                     const float pw0 = f2_lo(pw2), pw1 = f2_hi(pw2);
                     const f2_t ar2 = f2_mul(p2.y, f2_pack(fast_exp2(pw0), fast_exp2(pw1)));
                     const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
-                    const float al0 = ar0 > amax ? amax : ar0, al1 = ar1 > amax ? amax : ar1;
-                    const bool ok0 = !done[0] && !(pw0 > 0.0f) && al0 >= amin;
-                    const bool ok1 = !done[1] && !(pw1 > 0.0f) && al1 >= amin;
+                    // the decisions of pair_alpha (alpha >= alpha_min iff the
+                    // unclamped ar is, as alpha_max >= alpha_min; a NaN skips)
+                    const bool ok0 = !done[0] && !(pw0 > 0.0f) && ar0 >= amin;
+                    const bool ok1 = !done[1] && !(pw1 > 0.0f) && ar1 >= amin;
+                    const float al0 = fminf(ar0, amax), al1 = fminf(ar1, amax);
                     if (CNT) {
                         const float2 h = sm.u.sb.H[jj];
                         const bool inx = fabsf(f2_lo(dx2)) <= h.x;
                         n_eval += (!done[0] && inx && fabsf(f2_lo(dy2)) <= h.y) +
                                   (!done[1] && inx && fabsf(f2_hi(dy2)) <= h.y);
                     }
-                    if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
+                    if (!__any_sync(0xffffffffu, ok0 || ok1)) {
+                        // no pixel blends: the warp leaves once all have stopped
+                        if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+                        continue;
+                    }
                     // Eq. 4 front to back; stop before the splat that would take
                     // the transmittance below t_min
                     const f2_t Tn2 = f2_mul(pT2, f2_sub(one2, f2_pack(al0, al1)));
