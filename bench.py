@@ -506,8 +506,9 @@ def run_gpu(args):
             rk = roofline_for(k, v[0] / max(1, v[1]), v[1] // max(1, K), counters, n, V, n_keys, sc["sh_degree"],
                               peaks, alu, sm_mhz_run)
             kernels[k]["roofline"] = {x: rk[x] for x in ("bound", "achieved", "unit", "frac") if x in rk}
-            if "mufu_frac" in rk:
-                kernels[k]["roofline"]["mufu_frac"] = rk["mufu_frac"]
+            for x in ("mufu_frac", "atomic_frac"):
+                if x in rk:
+                    kernels[k]["roofline"][x] = rk[x]
 
     serving = None
     if not args.no_serve:
@@ -904,9 +905,17 @@ def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys
         a = ops / t / 1e12
         mufu = (counters[2] + counters[3]) / lps / t / 1e12
         tr = TRAFFIC_PER_UNIT.get("blend_bwd")
-        return {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
-                "frac": a / alu_peak, "mufu_frac": mufu / mufu_peak,
-                "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None, "peak_source": alu_src}
+        out = {"kernel": kname, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s",
+               "frac": a / alu_peak, "mufu_frac": mufu / mufu_peak,
+               "traffic": (tr[0] * counters[tr[1]] / lps) if tr else None, "peak_source": alu_src}
+        # gradient atomics: two float4 adds and one float add per (warp, splat)
+        # entry with a contributing pixel (the two-pixel kernel's flush);
+        # atomic_frac = the share of the probe's atomic rates they take
+        if alu.get("red_f32x4_per_s") and alu.get("red_f32_per_s"):
+            n_ent = counters[9] / lps
+            out["atomics_per_s"] = 3.0 * n_ent / t
+            out["atomic_frac"] = (2.0 * n_ent / t) / alu["red_f32x4_per_s"] + (n_ent / t) / alu["red_f32_per_s"]
+        return out
     if kname == "preprocess_fwd":
         # parameters once per launch; 60 B per visible pair, the 16 B culled
         # marker (rect, depth, radius) per culled pair

@@ -502,22 +502,30 @@ int gs_ctx_profile(gs_ctx* ctx, int max_kinds, char (*names)[32], double* total_
 
 /* Measured arithmetic rates of a device, the peaks of the "alu" roofline of
  * the blending kernels (which are bound by FP32 and MUFU issue; the paper has
- * no counterpart, it reports no kernel rates).  Runs three probe kernels of
- * one wave of resident blocks each on `device` (synchronous, a few ms, uses
- * the legacy default stream and allocates a few MB that it frees):
+ * no counterpart, it reports no kernel rates), and of the atomic adds the
+ * backward blend ends with.  Runs four probe kernels of one wave of resident
+ * blocks each and two atomic probes on `device` (synchronous, some tens of ms,
+ * uses the legacy default stream and allocates about 20 MB that it frees):
  *   sm_count               multiprocessors of the device;
  *   probe_sm_mhz           SM clock seen by the probes (clock64 cycles over
  *                          CUDA-event time); the GPU's clocks are not touched;
  *   fp32_fma_per_sm_clk    FP32 FMA lane operations per SM per cycle (FFMA);
  *   fp32x2_fma_per_sm_clk  the same with paired fma.rn.f32x2 (both halves);
  *   ex2_per_sm_clk         MUFU ex2 lane operations per SM per cycle;
- *   *_per_s                the same rates per second at the probe's clock.
+ *   fp64_fma_per_sm_clk    FP64 FMA lane operations per SM per cycle (DFMA);
+ *   *_per_s                the same rates per second at the probe's clock;
+ *   red_f32_per_s          global atomic float adds without a return value,
+ *                          every thread its own address (16 MB of addresses
+ *                          that stay in L2), per second;
+ *   red_f32x4_per_s        the same with 16-byte vector adds (float4).
  * Returns GS_EINVAL for a NULL out, GS_ECUDA / GS_ENOMEM on a CUDA error. */
 typedef struct gs_alu_peaks {
     int sm_count;
     double probe_sm_mhz;
     double fp32_fma_per_sm_clk, fp32x2_fma_per_sm_clk, ex2_per_sm_clk;
     double fp32_fma_per_s, fp32x2_fma_per_s, ex2_per_s;
+    double fp64_fma_per_sm_clk, fp64_fma_per_s;
+    double red_f32_per_s, red_f32x4_per_s;
 } gs_alu_peaks;
 int gs_measure_alu_peaks(int device, gs_alu_peaks* out);
 

@@ -100,7 +100,9 @@ class gs_solve_result(C.Structure):
 class gs_alu_peaks(C.Structure):
     _fields_ = [("sm_count", C.c_int), ("probe_sm_mhz", C.c_double), ("fp32_fma_per_sm_clk", C.c_double),
                 ("fp32x2_fma_per_sm_clk", C.c_double), ("ex2_per_sm_clk", C.c_double),
-                ("fp32_fma_per_s", C.c_double), ("fp32x2_fma_per_s", C.c_double), ("ex2_per_s", C.c_double)]
+                ("fp32_fma_per_s", C.c_double), ("fp32x2_fma_per_s", C.c_double), ("ex2_per_s", C.c_double),
+                ("fp64_fma_per_sm_clk", C.c_double), ("fp64_fma_per_s", C.c_double),
+                ("red_f32_per_s", C.c_double), ("red_f32x4_per_s", C.c_double)]
 
 
 class gs_server_stats(C.Structure):

@@ -36,13 +36,14 @@ def test_reference_arm_prints_one_contract_line():
 
 
 ALU = {"sm_count": 152, "probe_sm_mhz": 1900.0, "fp32_fma_per_sm_clk": 120.0, "fp32x2_fma_per_sm_clk": 121.0,
-       "ex2_per_sm_clk": 30.0, "fp32_fma_per_s": 0.0, "fp32x2_fma_per_s": 0.0, "ex2_per_s": 0.0}
+       "ex2_per_sm_clk": 30.0, "fp32_fma_per_s": 0.0, "fp32x2_fma_per_s": 0.0, "ex2_per_s": 0.0,
+       "fp64_fma_per_sm_clk": 2.0, "fp64_fma_per_s": 0.0, "red_f32_per_s": 4e10, "red_f32x4_per_s": 2e10}
 
 
 def test_roofline_arithmetic():
     # blend_bwd: (16 eval + 33 contributing) lane-ops per pair over the launch
     # time, against the measured FFMA rate x SM count x the run's SM clock
-    c = [0, 0, 1_000_000, 500_000, 0, 2_000, 0, 0, 0, 0, 0]
+    c = [0, 0, 1_000_000, 500_000, 0, 2_000, 0, 0, 0, 40_000, 0]
     r = bench.roofline_for("blend_bwd", 1.0, 1, c, 10, 2, 100, 3, {"hbm_gbs": 5000.0}, ALU, 2000.0)
     ops = 16 * 1_000_000 + 33 * 500_000
     assert r["bound"] == "alu"
@@ -53,6 +54,9 @@ def test_roofline_arithmetic():
     # traffic: DRAM bytes per unit from a capture of the kernel as it stands, else null
     assert r["traffic"] == (pytest.approx(tr[0] * c[tr[1]]) if tr else None)
     assert "2000 MHz" in r["peak_source"] and "of measured" in r["peak_source"]
+    # gradient atomics: two float4 adds and one float add per used warp entry
+    assert r["atomics_per_s"] == pytest.approx(3 * 40_000 / 1e-3)
+    assert r["atomic_frac"] == pytest.approx(2 * 40_000 / 1e-3 / 2e10 + 40_000 / 1e-3 / 4e10)
     # HBM kernels: algorithmic bytes (visible pairs counted apart) over time
     n, V, n_vis = 1000, 4, 1500
     c[10] = n_vis

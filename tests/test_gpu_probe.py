@@ -22,3 +22,12 @@ def test_alu_peak_probe():
     assert 500.0 <= a["probe_sm_mhz"] <= 3000.0, a
     per_s = a["fp32_fma_per_sm_clk"] * a["sm_count"] * a["probe_sm_mhz"] * 1e6
     assert 0.7 * per_s <= a["fp32_fma_per_s"] <= 1.3 * per_s, a
+    # FP64: at most the FP32 rate (GB300's FP64 is far below it)
+    assert 0.0 < a["fp64_fma_per_sm_clk"] <= a["fp32_fma_per_sm_clk"], a
+    per_s64 = a["fp64_fma_per_sm_clk"] * a["sm_count"] * a["probe_sm_mhz"] * 1e6
+    assert 0.7 * per_s64 <= a["fp64_fma_per_s"] <= 1.3 * per_s64, a
+    # global atomic adds to distinct L2-resident addresses: between 1e9/s and
+    # one per SM-lane per cycle
+    lanes_per_s = 128.0 * a["sm_count"] * a["probe_sm_mhz"] * 1e6
+    for k in ("red_f32_per_s", "red_f32x4_per_s"):
+        assert 1e9 <= a[k] <= lanes_per_s, (k, a)
