@@ -3,8 +3,8 @@
 // caller's).  Adam keeps its moments in the tangent space of each view's
 // current pose; the SE(3) step is applied on the left, T <- Exp(delta) T,
 // matching the left-perturbation pose gradient; the T x SO(3) step moves the
-// camera centre and the rotation separately (Sec. 4.2).  FP64 throughout (one
-// thread per view).
+// camera centre and the rotation separately (Sec. 4.2).  FP64 throughout (a
+// group of eight lanes per view).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -53,21 +53,18 @@ __device__ void se3_exp(const double tau[6], double E[9], double te[3]) {
 // A step (d_o, d_phi) equals the left step (rho, phi) = (-R d_o, d_phi) to
 // first order, so its gradient is (g_o, g_phi) = (-R^T g_rho, g_phi); the
 // moments live in those coordinates.
-__device__ void pose_adam_one(double* P, double* m, double* v, const double* g_in, double lr, double b1, double b2,
-                              double eps, double c1, double c2, int param) {
-    double g[6];
-    for (int k = 0; k < 6; k++) g[k] = g_in[k];
-    if (param == GS_POSE_TXSO3) {
-        for (int a = 0; a < 3; a++) g[a] = -(P[0 * 3 + a] * g_in[0] + P[1 * 3 + a] * g_in[1] + P[2 * 3 + a] * g_in[2]);
-    }
-    double d[6];
-    for (int k = 0; k < 6; k++) {
-        const double mk = b1 * m[k] + (1.0 - b1) * g[k];
-        const double vk = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
-        m[k] = mk;
-        v[k] = vk;
-        d[k] = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
-    }
+//
+// The step is taken by a group of POSE_LANES consecutive lanes per pose (GB300
+// runs FP64 at a small fraction of the FP32 rate, so the length of the
+// dependent FP64 chain sets the time): lane k < 6 of the group updates the
+// moments of tangent component k and its step, lanes 6 and 7 the two bias
+// corrections where they are per pose, and the group's first lane applies the
+// step to the pose.  The operations per component are those of a one-thread
+// step.  Every lane of the warp calls it (ok false: a lane group with no pose).
+#define POSE_LANES 8
+
+// Applies the tangent step d to pose P (first lane of the group).
+__device__ void pose_apply(double* P, const double d[6], int param) {
     double E[9], te[3], R[9], t[3];
     if (param == GS_POSE_TXSO3) {
         double o[3];
@@ -89,19 +86,51 @@ __device__ void pose_adam_one(double* P, double* m, double* v, const double* g_i
     for (int k = 0; k < 3; k++) P[9 + k] = t[k];
 }
 
+// step > 0: bias corrections 1 - b^step computed in the group (lanes 6, 7);
+// step <= 0: c1, c2 as given.
+__device__ void pose_adam_group(bool ok, double* P, double* m, double* v, const double* g_in, double lr, double b1,
+                                double b2, double eps, double c1, double c2, int step, int param) {
+    const int k = threadIdx.x & (POSE_LANES - 1);
+    if (step > 0) {
+        double c = 0.0;
+        if (k == 6) c = 1.0 - pow(b1, (double)step);
+        if (k == 7) c = 1.0 - pow(b2, (double)step);
+        c1 = __shfl_sync(0xffffffffu, c, 6, POSE_LANES);
+        c2 = __shfl_sync(0xffffffffu, c, 7, POSE_LANES);
+    }
+    double dk = 0.0;
+    if (ok && k < 6) {
+        double gk = g_in[k];
+        if (param == GS_POSE_TXSO3 && k < 3)
+            gk = -(P[0 * 3 + k] * g_in[0] + P[1 * 3 + k] * g_in[1] + P[2 * 3 + k] * g_in[2]);
+        const double mk = b1 * m[k] + (1.0 - b1) * gk;
+        const double vk = b2 * v[k] + (1.0 - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        dk = -lr * (mk / c1) / (sqrt(vk / c2) + eps);
+    }
+    double d[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) d[j] = __shfl_sync(0xffffffffu, dk, j, POSE_LANES);
+    if (ok && k == 0) pose_apply(P, d, param);
+}
+
+// POSE_LANES lanes per view (pose_adam_group)
 __global__ void k_pose_adam(int n_views, double* __restrict__ poses, double* __restrict__ m, double* __restrict__ v,
                             const double* __restrict__ g, double lr, double b1, double b2, double eps, double c1,
                             double c2, int param) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_views) return;
-    pose_adam_one(poses + 12 * i, m + 6 * i, v + 6 * i, g + 6 * i, lr, b1, b2, eps, c1, c2, param);
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / POSE_LANES;
+    const bool ok = i < n_views;
+    const int j = ok ? i : 0;
+    pose_adam_group(ok, poses + 12 * j, m + 6 * j, v + 6 * j, g + 6 * j, lr, b1, b2, eps, c1, c2, 0, param);
 }
 
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr, double b1,
                       double b2, double eps, int step, int param, cudaStream_t s) {
     if (n_views <= 0) return;
     const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    k_pose_adam<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, lr, b1, b2, eps, c1, c2, param);
+    k_pose_adam<<<(n_views + 7) / 8, 8 * POSE_LANES, 0, s>>>(n_views, poses, m, v, grad, lr, b1, b2, eps, c1, c2,
+                                                            param);
 }
 
 // Per-view variant: every view has its own step count (1-based, <= 0 means
@@ -110,18 +139,18 @@ void launch_pose_adam(int n_views, double* poses, double* m, double* v, const do
 __global__ void k_pose_adam_multi(int n_views, double* __restrict__ poses, double* __restrict__ m,
                                   double* __restrict__ v, const double* __restrict__ g, const int* __restrict__ steps,
                                   const double* __restrict__ lrs, double b1, double b2, double eps, int param) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_views) return;
-    const int step = steps[i];
-    if (step <= 0) return;
-    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    pose_adam_one(poses + 12 * i, m + 6 * i, v + 6 * i, g + 6 * i, lrs[i], b1, b2, eps, c1, c2, param);
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / POSE_LANES;
+    const int j = i < n_views ? i : 0;
+    const int step = i < n_views ? steps[j] : 0;
+    pose_adam_group(step > 0, poses + 12 * j, m + 6 * j, v + 6 * j, g + 6 * j, lrs[j], b1, b2, eps, 1.0, 1.0,
+                    step > 0 ? step : 1, param);
 }
 
 void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
                             const double* lrs, double b1, double b2, double eps, int param, cudaStream_t s) {
     if (n_views <= 0) return;
-    k_pose_adam_multi<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2, eps, param);
+    k_pose_adam_multi<<<(n_views + 7) / 8, 8 * POSE_LANES, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2,
+                                                                  eps, param);
 }
 
 // Slot-indexed variants for a batch of independent solves whose state lives
@@ -137,14 +166,12 @@ __global__ void k_pose_adam_slots(int n, const int* __restrict__ slot_of, double
                                   double* __restrict__ m, double* __restrict__ v, const double* __restrict__ g,
                                   const int* __restrict__ steps, const double* __restrict__ lrs, double b1, double b2,
                                   double eps, int param) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    const int kv = (blockIdx.x * blockDim.x + threadIdx.x) / POSE_LANES;
+    const int k = kv < n ? kv : 0;
     const int i = slot_of[k];
-    const int step = steps[k];
-    if (step <= 0) return;
-    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    pose_adam_one(poses + 12 * (size_t)i, m + 6 * (size_t)i, v + 6 * (size_t)i, g + 6 * k, lrs[k], b1, b2, eps, c1,
-                  c2, param);
+    const int step = kv < n ? steps[k] : 0;
+    pose_adam_group(step > 0, poses + 12 * (size_t)i, m + 6 * (size_t)i, v + 6 * (size_t)i, g + 6 * k, lrs[k], b1, b2,
+                    eps, 1.0, 1.0, step > 0 ? step : 1, param);
 }
 
 void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s) {
@@ -156,7 +183,8 @@ void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m,
                             const int* steps, const double* lrs, double b1, double b2, double eps, int param,
                             cudaStream_t s) {
     if (n <= 0) return;
-    k_pose_adam_slots<<<(n + 63) / 64, 64, 0, s>>>(n, slot_of, poses, m, v, grad, steps, lrs, b1, b2, eps, param);
+    k_pose_adam_slots<<<(n + 7) / 8, 8 * POSE_LANES, 0, s>>>(n, slot_of, poses, m, v, grad, steps, lrs, b1, b2, eps,
+                                                            param);
 }
 
 // ------------------------------------------------------------ Gaussian Adam
