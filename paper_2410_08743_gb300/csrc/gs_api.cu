@@ -786,7 +786,10 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
     }
     const int nblk = gs::preprocess_bwd_blocks(n);
     const int nchunks = (n_views + kViewChunk - 1) / kViewChunk;
-    if ((rc = fr->pose_partials.ensure((size_t)std::max(nblk, 1) * n_views * 6 + 6, grow, "pose partials"))) return rc;
+    // the block partials of a view chunk, then the reduction's group sums
+    const size_t part_n = (size_t)std::max(nblk, 1) * std::min(n_views, kViewChunk) * 6 + 6;
+    const size_t red_n = (size_t)gs::pose_reduce_groups(nblk) * std::min(n_views, kViewChunk) * 6;
+    if ((rc = fr->pose_partials.ensure(part_n + red_n, grow, "pose partials"))) return rc;
     const RenderParams rp = make_params(opts);
     const float* dldc = loss->dl_dimage;
     const bool l1_loss = loss->loss && l1_kind;
@@ -870,8 +873,8 @@ int gs::render_backward_impl(gs_ctx* ctx, const gs_scene* scene, int n_views, co
         }
         CK_LAUNCH();
         if (pose_grad) {
-            PROF(PK_POSE_REDUCE, 1);
-            gs::launch_pose_reduce(nv, nblk, part, pose_grad + 6 * v0, s);
+            PROF(PK_POSE_REDUCE, 2);
+            gs::launch_pose_reduce(nv, nblk, part, part + part_n, pose_grad + 6 * v0, s);
             CK_LAUNCH();
         }
     }

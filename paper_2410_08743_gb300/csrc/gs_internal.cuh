@@ -183,7 +183,10 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
                            int n_blocks, cudaStream_t s, int i_begin = 0, int i_end = -1);
 int preprocess_bwd_blocks(int n);
 
-void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* pose_grad, cudaStream_t s);
+// scratch: pose_reduce_groups(n_blocks) * n_views * 6 doubles
+int pose_reduce_groups(int n_blocks);
+void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* scratch, double* pose_grad,
+                        cudaStream_t s);
 
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr,
                       double b1, double b2, double eps, int step, int param, cudaStream_t s);

@@ -863,32 +863,73 @@ void launch_preprocess_bwd(const SceneDev& sc, int n_views, const ViewDev* views
 #undef GS_PRE_BWD
 }
 
-// Deterministic sum of the block partials: one block per view, a fixed
-// strided split over blocks and a fixed-order tree.
-__global__ void k_pose_reduce(int n_views, int n_blocks, const double* __restrict__ partials, double* __restrict__ out) {
-    __shared__ double sm[256 * 6];
-    const int v = blockIdx.x;
+// Deterministic sum of the block partials in two passes (FP64 runs at a small
+// fraction of the FP32 rate on this GPU, so the sum is spread over many SMs
+// instead of one block per view): pass 1, block (g, v) sums the partials of
+// blocks [g PRD_CHUNK, (g + 1) PRD_CHUNK) of view v (thread-strided, then a
+// butterfly over the warp, then the warps in order) into scratch[v][g]; pass
+// 2, one warp per view sums scratch[v][0 .. G) the same way.  The split and
+// every order are fixed, so the result is bit-reproducible.
+#define PRD_T 128
+#define PRD_CHUNK 256
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);   // a + b = b + a: all lanes agree
+    return x;
+}
+
+__global__ void __launch_bounds__(PRD_T) k_pose_reduce_part(int n_views, int n_blocks,
+                                                            const double* __restrict__ partials,
+                                                            double* __restrict__ scratch) {
+    __shared__ double sm[PRD_T / 32][6];
+    const int g = blockIdx.x, v = blockIdx.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int b0 = g * PRD_CHUNK, b1 = min(n_blocks, b0 + PRD_CHUNK);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) {
+    for (int b = b0 + threadIdx.x; b < b1; b += PRD_T) {
         const double* p = partials + ((size_t)b * n_views + v) * 6;
 #pragma unroll
         for (int c = 0; c < 6; c++) acc[c] += p[c];
     }
 #pragma unroll
-    for (int c = 0; c < 6; c++) sm[threadIdx.x * 6 + c] = acc[c];
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if ((int)threadIdx.x < st)
+    for (int c = 0; c < 6; c++) acc[c] = warp_sum_d(acc[c]);
+    if (lane == 0)
 #pragma unroll
-            for (int c = 0; c < 6; c++) sm[threadIdx.x * 6 + c] += sm[(threadIdx.x + st) * 6 + c];
-        __syncthreads();
+        for (int c = 0; c < 6; c++) sm[wid][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int w = 0; w < PRD_T / 32; w++) t += sm[w][threadIdx.x];
+        scratch[((size_t)v * gridDim.x + g) * 6 + threadIdx.x] = t;
     }
-    if (threadIdx.x < 6) out[v * 6 + threadIdx.x] = sm[threadIdx.x];
 }
 
-void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* pose_grad, cudaStream_t s) {
+__global__ void k_pose_reduce_final(int n_groups, const double* __restrict__ scratch, double* __restrict__ out) {
+    const int v = blockIdx.x, lane = threadIdx.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int g = lane; g < n_groups; g += 32) {
+        const double* p = scratch + ((size_t)v * n_groups + g) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[c] += p[c];
+    }
+    double r = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        const double t = warp_sum_d(acc[c]);
+        if (lane == c) r = t;
+    }
+    if (lane < 6) out[v * 6 + lane] = r;
+}
+
+int pose_reduce_groups(int n_blocks) { return (std::max(n_blocks, 1) + PRD_CHUNK - 1) / PRD_CHUNK; }
+
+void launch_pose_reduce(int n_views, int n_blocks, const double* partials, double* scratch, double* pose_grad,
+                        cudaStream_t s) {
     if (n_views <= 0) return;
-    k_pose_reduce<<<n_views, 256, 0, s>>>(n_views, n_blocks, partials, pose_grad);
+    const int G = pose_reduce_groups(n_blocks);
+    k_pose_reduce_part<<<dim3(G, n_views), PRD_T, 0, s>>>(n_views, n_blocks, partials, scratch);
+    k_pose_reduce_final<<<n_views, 32, 0, s>>>(G, scratch, pose_grad);
 }
 
 }  // namespace gs
