@@ -391,13 +391,18 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
 // runs of consecutive buckets of at most LZ_CAP keys are sorted and blended one
 // after another until every pixel has stopped.  The concatenation of the
 // sorted runs is exactly the (depth, index) order, so the image equals the one
-// of a fully sorted list.  The sorted prefix and its length go to sorted_idx /
-// sorted_count for the backward pass, which never reads past it.
+// of a fully sorted list.  A run is gathered grouped by bucket and each bucket
+// is sorted on its own (buckets hold a few keys each), with a radix sort of
+// the whole run where a bucket is large.  The sorted prefix and its length go
+// to sorted_idx / sorted_count for the backward pass, which never reads past
+// it.
 #define LZ_NB_BITS 10
 #define LZ_NB (1 << LZ_NB_BITS)
 // the first run of buckets is cut at LZ_FIRST keys: most tiles stop within
 // a few hundred entries, so a short first run sorts little that is not used
 #define LZ_FIRST 512
+// buckets of at most LZ_SMALL keys are insertion-sorted by one thread
+#define LZ_SMALL 32
 #define LZ_T GS_TILE_PIX
 
 template <int LZ_CAP, int NT>
@@ -577,6 +582,38 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
         for (int j = threadIdx.x; j < m; j += NT) sorted_idx[s + c0 + j] = (uint32_t)(r[j] & 0xffffffffull);
         __syncthreads();
     };
+    // Sorts the run [c0, c0 + m) of buckets [cb, cb1) held in b0 grouped by
+    // bucket (bucket b at [bstart[b] - c0, bstart[b + 1] - c0)): the buckets
+    // are depth intervals in order, so sorting each bucket on its own sorts the
+    // run; a thread insertion-sorts a bucket of at most LZ_SMALL keys.  A run
+    // with a larger bucket is radix-sorted whole instead.  Either way b0 ends
+    // in the exact (depth, index) order.
+    auto sort_buckets_write = [&](int cb, int cb1, uint32_t c0, int m) {
+        bool big = false;
+        unsigned long long* k0 = sm.u.srt.b0;
+        for (int b = cb + (int)threadIdx.x; b < cb1; b += NT) {
+            const uint32_t bl = sm.bstart[b] - c0, bh = sm.bstart[b + 1] - c0;
+            if (bh - bl > LZ_SMALL) {
+                big = true;
+                continue;
+            }
+            for (uint32_t i = bl + 1; i < bh; i++) {
+                const unsigned long long x = k0[i];
+                uint32_t j = i;
+                while (j > bl && k0[j - 1] > x) {
+                    k0[j] = k0[j - 1];
+                    j--;
+                }
+                k0[j] = x;
+            }
+        }
+        if (__syncthreads_or(big)) {
+            sort_write(k0, sm.u.srt.b1, c0, m);
+            return;
+        }
+        for (int j = threadIdx.x; j < m; j += NT) sorted_idx[s + c0 + j] = (uint32_t)(k0[j] & 0xffffffffull);
+        __syncthreads();
+    };
 
     if (n_list <= LZ_CAP) {
         for (uint32_t j = threadIdx.x; j < n_list; j += NT) sm.u.srt.b0[j] = keys[s + j];
@@ -657,19 +694,21 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
                 if (m > LZ_CAP) {
                     sort_write(tmp + s + c0, keys + s + c0, c0, m);  // one oversized bucket
                 } else if (scattered) {
+                    // the scattered copy is grouped by bucket already
                     for (int j = threadIdx.x; j < m; j += NT) sm.u.srt.b0[j] = tmp[s + c0 + j];
                     __syncthreads();
-                    sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
+                    sort_buckets_write(cb, cb1, c0, m);
                 } else {
-                    if (threadIdx.x == 0) s_mm[0] = 0u;
+                    // gathered into b0 grouped by bucket (a cursor per bucket)
+                    for (int b = cb + (int)threadIdx.x; b < cb1; b += NT) sm.hist[b] = sm.bstart[b] - c0;
                     __syncthreads();
                     for (uint32_t j = threadIdx.x; j < n_list; j += NT) {
                         const unsigned long long x = keys[s + j];
                         const int b = (int)(((uint32_t)(x >> 32) - lo) >> shift);
-                        if (b >= cb && b < cb1) sm.u.srt.b0[atomicAdd(&s_mm[0], 1u)] = x;
+                        if (b >= cb && b < cb1) sm.u.srt.b0[atomicAdd(&sm.hist[b], 1u)] = x;
                     }
                     __syncthreads();
-                    sort_write(sm.u.srt.b0, sm.u.srt.b1, c0, m);
+                    sort_buckets_write(cb, cb1, c0, m);
                 }
                 n_sorted = c0 + (uint32_t)m;
                 run++;
