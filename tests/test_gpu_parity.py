@@ -83,6 +83,21 @@ def _needle_case(n=6000, seed=33):
     return sc, views, poses
 
 
+def _layered_case(n=40000, seed=35):
+    """Long tile lists (about 10k keys) over a wide depth range at low
+    opacity, so the lazy sort consumes several runs: most Gaussians spread in
+    depth (a few keys per depth bucket: the bucket-by-bucket sort), 2,400 on
+    three thin depth layers (a few hundred keys in one bucket: the radix sort
+    of the whole run)."""
+    rng = np.random.default_rng(seed)
+    sc = synth.make_scene_box(seed, n, sh_degree=0, lo=(-1.0, -0.8, 2.5), hi=(1.0, 0.8, 6.0))
+    layer = np.arange(n) < 2400
+    sc["means"][layer, 2] = (np.repeat([3.0, 4.0, 5.0], 800) + rng.uniform(0.0, 2e-4, 2400)).astype(np.float32)
+    sc["opac"][:] = rng.uniform(0.02, 0.06, n).astype(np.float32)
+    views = [dict(fx=40.0, fy=40.0, cx=24.0, cy=20.0, width=48, height=40)]
+    return sc, views, synth.pose_from_center(np.eye(3), np.zeros(3))[None]
+
+
 def _wide_view_case(n=6000, seed=34):
     """A view with more than the 8192 tiles the shared-memory tile histograms
     hold (2050 x 1090: 129 x 69 tiles, ragged on both edges), which takes the
@@ -106,6 +121,7 @@ CASES = {
     "same_depth": lambda: _same_depth_case(),
     "needles": lambda: _needle_case(),
     "wide_view": lambda: _wide_view_case(),
+    "layered": lambda: _layered_case(),
 }
 GRAD_CASES = ["tiny", "ragged_sh3", "ragged_sh1", "dense_medium", "wide_view"]
 
