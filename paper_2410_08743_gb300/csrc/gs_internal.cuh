@@ -191,8 +191,6 @@ void launch_pose_reduce(int n_views, int n_blocks, const double* partials, doubl
 void launch_pose_adam(int n_views, double* poses, double* m, double* v, const double* grad, double lr,
                       double b1, double b2, double eps, int step, int param, cudaStream_t s);
 
-void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
-                            const double* lrs, double b1, double b2, double eps, int param, cudaStream_t s);
 
 void launch_gather_poses(int n, const int* slot_of, const double* slot_poses, double* packed, cudaStream_t s);
 void launch_pose_adam_slots(int n, const int* slot_of, double* poses, double* m, double* v, const double* grad,

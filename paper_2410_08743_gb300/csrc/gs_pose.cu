@@ -133,28 +133,10 @@ void launch_pose_adam(int n_views, double* poses, double* m, double* v, const do
                                                             param);
 }
 
-// Per-view variant: every view has its own step count (1-based, <= 0 means
-// "leave this view alone") and learning rate, as in a batch of independent
-// pose solves that started at different times.
-__global__ void k_pose_adam_multi(int n_views, double* __restrict__ poses, double* __restrict__ m,
-                                  double* __restrict__ v, const double* __restrict__ g, const int* __restrict__ steps,
-                                  const double* __restrict__ lrs, double b1, double b2, double eps, int param) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / POSE_LANES;
-    const int j = i < n_views ? i : 0;
-    const int step = i < n_views ? steps[j] : 0;
-    pose_adam_group(step > 0, poses + 12 * j, m + 6 * j, v + 6 * j, g + 6 * j, lrs[j], b1, b2, eps, 1.0, 1.0,
-                    step > 0 ? step : 1, param);
-}
-
-void launch_pose_adam_multi(int n_views, double* poses, double* m, double* v, const double* grad, const int* steps,
-                            const double* lrs, double b1, double b2, double eps, int param, cudaStream_t s) {
-    if (n_views <= 0) return;
-    k_pose_adam_multi<<<(n_views + 7) / 8, 8 * POSE_LANES, 0, s>>>(n_views, poses, m, v, grad, steps, lrs, b1, b2,
-                                                                  eps, param);
-}
-
 // Slot-indexed variants for a batch of independent solves whose state lives
-// in fixed slots: view k of the batch is slot slot_of[k].
+// in fixed slots: view k of the batch is slot slot_of[k], with its own step
+// count (1-based; <= 0 leaves the slot alone) and learning rate, as the solves
+// started at different times.
 __global__ void k_gather_poses(int n, const int* __restrict__ slot_of, const double* __restrict__ slot_poses,
                                double* __restrict__ packed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
