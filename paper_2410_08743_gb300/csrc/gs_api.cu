@@ -268,7 +268,7 @@ struct gs_frames {
 };
 
 static const int kViewChunk = 64;  // views per preprocess launch (bounds shared memory)
-static const size_t kHostSlices = 4;  // Gaussian slices of a gs_step with host buffers (at most GS_MAX_SLICES)
+static const size_t kHostSlices = 8;  // Gaussian slices of a gs_step with host buffers (at most GS_MAX_SLICES)
 
 // ------------------------------------------------------------ helpers
 static int check_scene(const gs_scene* sc) {
