@@ -4,14 +4,19 @@
 // Layout: every (view, Gaussian) splat with tile rectangle R emits one key per
 // tile of R.  Tiles of all views of a launch share one global numbering, so a
 // single pass serves a whole batch of views.
-//   1. the preprocess counts keys per tile (atomics on tile_counts);
+//   1. count: a CTA takes a chunk of Gaussians of one view, counts their keys
+//      per tile in shared memory and reserves its range in each touched tile
+//      with one global atomic, recording (tile, offset) for step 3;
 //   2. an exclusive scan of the counts gives each tile's [start, end);
 //   3. scatter: each splat writes (depth bits << 32 | Gaussian index) into
-//      its tiles' ranges (arbitrary order within a tile);
-//   4. per-tile LSD radix sort of those 64-bit keys in shared memory.  Keys
-//      within a tile are unique (one Gaussian appears once per tile), so the
-//      result is the unique (depth, index) order: ties in depth go to the
-//      lower index, independent of the scatter's order.
+//      its tiles' ranges at the CTA's reserved slots (arbitrary order within
+//      a tile);
+//   4. sort: normally lazily inside the forward blend (gs_blend.cu), which
+//      sorts only the list prefixes it consumes; with GS_F_FULL_SORT the
+//      segmented sorts below sort every tile's whole list.  Keys within a tile
+//      are unique (one Gaussian appears once per tile), so either gives the
+//      unique (depth, index) order: ties in depth go to the lower index,
+//      independent of the scatter's order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
