@@ -479,14 +479,23 @@ __global__ void __launch_bounds__(GS_TILE_PIX / PX, PX == 1 ? 4 : 8) k_blend_fwd
     // Blends list positions [p0, p1) read from sorted_idx; returns true when
     // every pixel of the tile has stopped.
     auto blend_range = [&](uint32_t p0, uint32_t p1) -> bool {
+        static_assert(NT >= BATCH, "one staged entry per thread");
         for (uint32_t base = p0; base < p1; base += BATCH) {
-            if (__syncthreads_count(all_done()) == NT) return true;
-            n_read += (threadIdx.x == 0) ? min((uint32_t)BATCH, p1 - base) : 0u;
             const int cnt = (int)min((uint32_t)BATCH, p1 - base);
-            for (int j = threadIdx.x; j < cnt; j += NT) {
-                const size_t k = vbase + sorted_idx[s + base + j];
-                stage_entry(sm.u.sb, j, stage_mean(sp, k, ox, oy), sp.B[k], sp.Cb[k], rp.alpha_min);
+            // the entry's records are loaded before the barrier (their latency
+            // overlaps the wait) and staged after it
+            const bool have = (int)threadIdx.x < cnt;
+            float4 ra = make_float4(0.0f, 0.0f, 0.0f, 0.0f), rb = ra;
+            float rc = 0.0f;
+            if (have) {
+                const size_t k = vbase + sorted_idx[s + base + threadIdx.x];
+                ra = stage_mean(sp, k, ox, oy);
+                rb = sp.B[k];
+                rc = sp.Cb[k];
             }
+            if (__syncthreads_count(all_done()) == NT) return true;
+            n_read += (threadIdx.x == 0) ? (uint32_t)cnt : 0u;
+            if (have) stage_entry(sm.u.sb, threadIdx.x, ra, rb, rc, rp.alpha_min);
             __syncthreads();
             unsigned char* wl = sm.wl[wid];
             // a warp whose pixels have all stopped skips the batch
