@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX) k_blend_fwd(int n_views, const in
 // the whole run where a bucket is large.  The sorted prefix and its length go
 // to sorted_idx / sorted_count for the backward pass, which never reads past
 // it.
-#define LZ_NB_BITS 10
+#define LZ_NB_BITS 9
 #define LZ_NB (1 << LZ_NB_BITS)
 // the first run of buckets is cut at LZ_FIRST keys: most tiles stop within
 // a few hundred entries, so a short first run sorts little that is not used
