@@ -1242,8 +1242,9 @@ __global__ void __launch_bounds__(GS_TILE_PIX / 2, 9) k_blend_bwd_warp(
             const int jj = 31 - __clz(mm);
             mm &= ~(1u << jj);
             const uint32_t pos = (uint32_t)(cstart + jj);
+            // (the warp walks only positions below its longest prefix, so some
+            // lane's pixel always takes part here)
             const bool u0 = pos < plast0, u1 = pos < plast1;
-            if (!__any_sync(0xffffffffu, u0 || u1)) continue;
             // alpha of both pixels (Eq. 3) with pair_alpha's operation
             // sequence, paired: the lanes of each pair share dx
             const ulonglong2 p0 = wc.P0[jj], p1 = wc.P1[jj], p2 = wc.P2[jj];
