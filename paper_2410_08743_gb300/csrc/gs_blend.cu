@@ -1147,7 +1147,7 @@ __global__ void __launch_bounds__(GS_TILE_PIX, 6) k_blend_bwd(
 // slots; the lanes then flush the chunk's entries in parallel, one set of
 // vector atomics per (warp, splat).
 template <bool CNT>
-__global__ void __launch_bounds__(GS_TILE_PIX / 2, 9) k_blend_bwd_warp(
+__global__ void __launch_bounds__(GS_TILE_PIX / 2, 8) k_blend_bwd_warp(
     int n_views, const int* __restrict__ tile_base, const ViewDev* __restrict__ views, RenderParams rp, SplatArrays sp,
     int n, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ sorted_idx, uint32_t cap,
     const float* __restrict__ image, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
