@@ -24,7 +24,9 @@ def workload_key(gpu_name: str, views, n_gaussians: int) -> str:
     px = sum(int(v["width"]) * int(v["height"]) for v in views)
     res_class = f"views{len(views)}-px2^{int(round(math.log2(max(px, 1))))}"
     n_class = f"n2^{int(round(math.log2(max(n_gaussians, 1))))}"
-    return f"t3|{gpu_name}|{res_class}|{n_class}"   # t3: the knob set with the blends' pixel counts
+    # the version prefix changes when the kernels' timing changes enough for a
+    # cached choice to go stale (t4: paired-arithmetic and per-warp blends)
+    return f"t4|{gpu_name}|{res_class}|{n_class}"
 
 
 def autotune(renderer, params: dict, views, poses, image, loss, grads=None, pose_grad=None, repeats: int = 2,

@@ -92,3 +92,15 @@ def test_clock_rows_before_the_timed_region_are_dropped(tmp_path):
     out = cs.stop()
     assert out["samples"] == 2 and out["sm_mhz"] == 2070.0 and out["reasons"] == []
     assert not path.exists()
+
+
+def test_tuning_cache_key_classes():
+    """The autotuner caches per GPU, view-count/resolution class and
+    Gaussian-count class (powers of two), under a version prefix."""
+    from paper_2410_08743_gb300 import tune
+    v = [dict(width=1008, height=756), dict(width=256, height=192)]
+    k = tune.workload_key("GPU X", v, 1_000_000)
+    assert k.startswith("t4|GPU X|views2-px2^20|") and k.endswith("|n2^20")
+    assert tune.workload_key("GPU X", v, 1_100_000) == k            # same class
+    assert tune.workload_key("GPU X", v, 3_000_000) != k            # another Gaussian-count class
+    assert tune.workload_key("GPU X", v[:1], 1_000_000) != k        # another view count
