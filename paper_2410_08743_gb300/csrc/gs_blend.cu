@@ -1255,10 +1255,12 @@ __global__ void __launch_bounds__(GS_TILE_PIX / 2, 8) k_blend_bwd_warp(
             const float G0 = fast_exp2(pw0), G1 = fast_exp2(pw1);
             const f2_t ar2 = f2_mul(p2.y, f2_pack(G0, G1));
             const float ar0 = f2_lo(ar2), ar1 = f2_hi(ar2);
+            // the decisions of pair_alpha (alpha >= alpha_min iff the unclamped ar
+            // is, as alpha_max >= alpha_min; a NaN skips)
             const bool cl0 = ar0 > amax, cl1 = ar1 > amax;
-            const float al0 = cl0 ? amax : ar0, al1 = cl1 ? amax : ar1;
-            const bool v0 = u0 && !(pw0 > 0.0f) && al0 >= amin;
-            const bool v1 = u1 && !(pw1 > 0.0f) && al1 >= amin;
+            const float al0 = fminf(ar0, amax), al1 = fminf(ar1, amax);
+            const bool v0 = u0 && !(pw0 > 0.0f) && ar0 >= amin;
+            const bool v1 = u1 && !(pw1 > 0.0f) && ar1 >= amin;
             if (CNT) {
                 // pixels inside the splat's alpha box (recomputed from the record)
                 const float4 a = make_float4(f2_lo(p0.x), f2_lo(p1.x), f2_lo(p0.y) * GS_IKA, f2_lo(p1.y) * GS_IKB);
