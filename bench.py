@@ -870,8 +870,8 @@ OPS_BWD_EVAL, OPS_BWD_GRAD = 16, 33
 # kernel -> (DRAM bytes, read + write, per unit; counter index of the unit) from one
 # ncu capture of the current kernel on the 16-view case, scaled to a launch by the
 # run's units; re-measure when the kernel changes.
-# k_blend_bwd_warp<0>: 218.0 MB for 4,860,434 list entries read, 16 views at 1M Gaussians.
-TRAFFIC_PER_UNIT = {"blend_bwd": (44.86, 5)}
+# k_blend_bwd_warp<0>: 217.7 MB for 4,860,434 list entries read, 16 views at 1M Gaussians.
+TRAFFIC_PER_UNIT = {"blend_bwd": (44.79, 5)}
 
 
 def roofline_for(kname, per_launch_ms, launches_per_step, counters, n, V, n_keys, sh_degree, peaks, alu, sm_mhz):
